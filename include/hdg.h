@@ -1,0 +1,198 @@
+/*
+ * hdg.h -- C ABI of the GB300 library for the statically condensed HDG trace
+ * operator of -div(kappa grad u) = f (u = 0 on the boundary) on a uniform
+ * Cartesian quad mesh, and the nested p/h geometric multigrid built on it.
+ *
+ * Method: Fabien, Knepley, Mills, Riviere, "Manycore parallel computing for a
+ * hybridizable discontinuous Galerkin nested multigrid method" (arXiv
+ * 1705.09907). Section, equation and algorithm numbers below refer to it.
+ *
+ * Conventions shared by every call
+ *  - Mesh: nx x ny rectangles on [x0,x1] x [y0,y1]; element e = i + nx*j.
+ *    Edges: vertical ones first, id = i + (nx+1)*j (i in [0,nx], j in [0,ny));
+ *    then horizontal ones, id = (nx+1)*ny + i + nx*j (i in [0,nx), j in [0,ny]).
+ *    Local faces of an element: 0 = W, 1 = E, 2 = S, 3 = N.
+ *  - Trace vectors ("x", "y", "b", "lambda"): [n_edges][k+1] values at the k+1
+ *    Gauss-Legendre nodes of each edge, ordered by increasing coordinate;
+ *    dof = edge*(k+1) + a. With nrhs > 1 the layout is [n_edges*(k+1)][nrhs]
+ *    (right-hand side fastest). Entries on boundary edges are outputs of 0 and
+ *    are ignored on input (the trace is P_h g_D = 0 there).
+ *  - Source samples f_q: [nel][k+2][k+2], f at the (k+2)^2 Gauss-Legendre points
+ *    of each element, index [e][jy][ix] (x fastest).
+ *  - Volume output u: [nel][(k+1)^2], q: [nel][2][(k+1)^2] -- values at the
+ *    tensor Gauss-Lobatto nodes, index i + (k+1)*j (i along x); k = 0: the
+ *    element constant.
+ *  - All vector arguments are DEVICE pointers owned by the caller, unless a
+ *    name says host. The context owns everything it allocates.
+ *  - `stream` is a cudaStream_t passed as void* (0 = legacy default stream).
+ *    Calls are asynchronous on that stream unless they return host-visible
+ *    results (hdg_setup, hdg_solve, hdg_adjoint_grad, hdg_get_*), which
+ *    synchronise it.
+ *  - Every call returns an hdg_status. On an error nothing is written to the
+ *    outputs that later calls depend on; the context stays usable unless the
+ *    status is HDG_ERR_CUDA (a sticky CUDA error).
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_ERR_INVALID_ARG = 1,   /* bad size, degree, pointer or option          */
+  HDG_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed  */
+  HDG_ERR_OOM = 3,           /* device allocation failed                     */
+  HDG_ERR_NOT_CONVERGED = 4, /* iteration limit reached before the tolerance */
+  HDG_ERR_BREAKDOWN = 5,     /* CG breakdown: p^T A p <= 0 or not finite     */
+  HDG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                */
+  HDG_ERR_UNSUPPORTED = 7    /* valid request this build does not provide    */
+} hdg_status;
+
+/* Storage / arithmetic precision of an operator apply or V-cycle.
+ *  FP64: blocks and vectors in double, double accumulation.
+ *  FP32: blocks and vectors in float, float accumulation.
+ *  BF16: blocks in bfloat16, vectors in float, float accumulation. */
+typedef enum { HDG_PREC_FP64 = 0, HDG_PREC_FP32 = 1, HDG_PREC_BF16 = 2 } hdg_prec;
+
+typedef struct {
+  int nx, ny;                 /* elements per direction, >= 1                */
+  double x0, y0, x1, y1;      /* domain corners, x1 > x0, y1 > y0            */
+} hdg_mesh;
+
+typedef struct {
+  int nu1, nu2;               /* pre/post smoothing steps (2, 2), Algs. 1-2  */
+  int coarse_n;               /* coarsen the Q1 meshes while both sizes are even
+                                 and halving keeps them >= coarse_n (2)       */
+  double tau;                 /* HDG stabilisation on every facet (1.0)      */
+  int cheb_degree;            /* Chebyshev degree per h-level smoothing step (2) */
+  int mixed;                  /* also build FP32 and BF16 copies of the level
+                                 blocks for mixed-precision V-cycles (1)      */
+  int use_graphs;             /* capture V-cycles in CUDA graphs (1)         */
+} hdg_options;
+
+typedef struct {
+  int nel, n_edges, ndof;     /* ndof = n_edges * (k+1)                      */
+  int k, n_plevels, n_hlevels;/* p-levels k..0 and Q1 h-levels (finest first) */
+  int coarse_dim;             /* unknowns of the coarsest (direct) solve     */
+  size_t device_bytes;        /* device memory held by the context           */
+  double setup_ms;            /* wall time of hdg_setup                      */
+} hdg_info;
+
+typedef struct {
+  int iterations;             /* CG iterations taken                         */
+  double relres;              /* final |b - A x|_2 / |b|_2 (FP64 residual)    */
+  double relres_history[256]; /* per iteration, [0] = 1                       */
+  double solve_ms;            /* wall time of the call                       */
+} hdg_solve_info;
+
+/* Fill `opt` with the defaults listed above. */
+void hdg_default_options(hdg_options* opt);
+
+/* Human-readable text for a status code (static storage). */
+const char* hdg_error_string(int status);
+
+/*
+ * Build the solver for degree k (0 <= k <= 7) and per-element coefficient
+ * kappa (device, [nel] doubles, each > 0 and finite; K = kappa*I, piecewise
+ * constant as in Sec. 2). Performs procedure (i) of Sec. 3 -- the local
+ * solvers of Eq. shur0 and the condensed blocks S_K of Eq. shur1 on every
+ * element -- then the multigrid hierarchy of Sec. 6: Galerkin p-levels k-1..0,
+ * Schwarz blocks, the conforming Q1 h-levels with Galerkin coarsening, the
+ * Chebyshev bounds, and the FP64 Cholesky factor of the coarsest operator.
+ * `opt` may be NULL (defaults). On success *out owns all device data; release
+ * it with hdg_destroy. Errors: INVALID_ARG (sizes, k, kappa <= 0 or NaN, bad
+ * options), OOM, CUDA.
+ */
+int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_options* opt,
+              void* stream, void** out_ctx);
+
+/* Sizes and setup statistics (host struct). */
+int hdg_get_info(void* ctx, hdg_info* info);
+
+/*
+ * Index maps (device outputs, int32): elem_to_edge [nel][4] (faces W,E,S,N),
+ * edge_to_elem [n_edges][2] (low-side, high-side element; -1 off the domain),
+ * edge_local_face [n_edges][2] (face of the edge in those elements; -1).
+ * These are the maps Map0..Map3 of Alg. 3. Any output may be NULL.
+ */
+int hdg_get_maps(void* ctx, int32_t* elem_to_edge, int32_t* edge_to_elem,
+                 int32_t* edge_local_face, void* stream);
+
+/*
+ * Condensed right-hand side (Sec. 3 step (ii); the volume-to-surface
+ * projection of Sec. 8.3): b = sum_K A_K^T b_K, b_K(mu) = (f, u_mu)_K.
+ * f_q: device [nrhs][nel][k+2][k+2] doubles; b: device [ndof][nrhs] doubles
+ * (nrhs = 1: [ndof]). Boundary entries of b are written as 0.
+ */
+int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* stream);
+
+/*
+ * Assembly-free apply of the condensed trace operator (Alg. 3):
+ * y_e = sum over the two elements K of edge e of S_K[e rows, :] x_K on every
+ * interior edge, y = 0 on boundary edges. Each face is written once, by one
+ * thread, with no atomics. x, y: device [ndof][nrhs] in the type `prec`
+ * selects (double for FP64, float for FP32 and BF16); x and y must not overlap.
+ * Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED (BF16/FP32 when the
+ * context was built with mixed = 0).
+ */
+int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
+
+/*
+ * One nested V-cycle z = V r (Algs. 2 then 1, zero initial guess): p-levels
+ * k..1 with nu1/nu2 weighted additive Schwarz steps (Sec. 6.4.2), restriction
+ * R = P^T and prolongation P per edge (Eqs. eq_mg_pro, eq_mg_res), the p = 0
+ * level and the Q1 levels with Chebyshev steps, P_J / P_J^T between p = 0 and
+ * Q1 (Eq. eq_h_mg_pro), bilinear transfers, and an FP64 Cholesky solve on the
+ * coarsest mesh. r, z: device [ndof][nrhs] (double for FP64, float otherwise).
+ * The operator is symmetric positive definite, so CG may use it.
+ */
+int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* stream);
+
+/*
+ * Solve A lambda = b (Sec. 3 step (iii)) with conjugate gradients
+ * preconditioned by one V-cycle per iteration, to |b - A lambda|_2 <= rtol |b|_2.
+ * b, lambda: device [ndof] doubles (nrhs must be 1). The residual, the CG
+ * vectors and the update are FP64; `inner` selects the V-cycle precision
+ * (FP64, or FP32/BF16 blocks with FP32 accumulation -- then CG uses the
+ * flexible Polak-Ribiere beta). info (host, may be NULL) receives the
+ * iteration count and residual history. Errors: NOT_CONVERGED (lambda holds
+ * the last iterate), BREAKDOWN, TIMEOUT, CUDA.
+ */
+int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol, int maxit,
+              int inner, hdg_solve_info* info, void* stream);
+
+/*
+ * Surface-to-volume reconstruction (Sec. 3 step (iv), Eq. shur0, Sec. 8.3):
+ * from the trace lambda [ndof] and sources f_q [nel][k+2][k+2] compute
+ * u [nel][(k+1)^2] and q [nel][2][(k+1)^2] (device doubles; either may be NULL).
+ */
+int hdg_recover_local(void* ctx, const double* lambda, const double* f_q, double* u, double* q,
+                      void* stream);
+
+/*
+ * Adjoint gradient of J = 1/2 |lambda - lambda_obs|_2^2 (interior dofs) where
+ * lambda solves A(kappa) lambda = b(kappa, f). Solves A psi = lambda - lambda_obs
+ * with the same multigrid-preconditioned CG (A is symmetric) to rtol, then an
+ * element-local kernel gives
+ *   dJ/dlog(kappa_K) = -(kappa^-1 q_K(lambda, f), q_K(psi, 0))_K
+ *   dJ/df at the sample points = w_q |J_K| u_K(psi, 0)(x_q)
+ * with (q, u) from the local solver of Eq. shur0.
+ * f_q, lambda, lambda_obs: device inputs; dJ_dlogk [nel], dJ_df [nel][k+2][k+2],
+ * J (one double), psi [ndof]: device outputs, each may be NULL.
+ */
+int hdg_adjoint_grad(void* ctx, const double* f_q, const double* lambda, const double* lambda_obs,
+                     double rtol, int maxit, double* dJ_dlogk, double* dJ_df, double* J,
+                     double* psi, void* stream);
+
+/* Release everything the context owns. NULL is ignored. */
+void hdg_destroy(void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_H */

@@ -1,0 +1,157 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <string>
+
+#include "../../include/hdg.h"
+
+namespace hdg {
+
+constexpr int kMaxDegree = 7;
+constexpr int kSeg = 16;          // elements per record segment (x direction)
+
+// ---------------------------------------------------------------------------
+// Host reference tables for one degree p on an hx x hy rectangle.
+// Volume basis: Lagrange at the (p+1)^2 tensor Gauss-Lobatto nodes (p >= 1) or
+// the constant (p = 0); trace basis: Lagrange at the p+1 Gauss-Legendre nodes.
+// All matrices are row-major doubles.
+struct RefTables {
+  int p = 0, n1 = 1, n = 1, m = 4, nf = 4;  // nf = (p+2)^2 source samples
+  double hx = 1, hy = 1;
+  // Local solver pieces (Eq. shur0 after eliminating q):
+  //   A_u = kappa*P + tau*Mb   [n x n]
+  //   W   = kappa*Z + tau*Eb   [n x m]
+  //   S   = kappa*Y + tau*diag(Ml) - W^T A_u^-1 W   [m x m]
+  std::vector<double> P, Mb, Z, Eb, Y, Ml;
+  std::vector<double> M;                    // volume mass [n x n]
+  // Recovery of q: q_c = kappa * (MiBt_c U - MiC_c lambda), c = x, y
+  std::vector<double> MiBt, MiC;            // [2][n x n], [2][n x m]
+  // Source load F = Vf^T (wJf .* f_q)
+  std::vector<double> Vf, wJf;              // [nf x n], [nf]
+};
+
+void build_ref_tables(int p, double hx, double hy, RefTables& t);
+// Per-edge embedding degree p -> p+1: Pp[(p+2) x (p+1)], Pp[a'][a] = mu_a(x_a')
+void p_prolongation_1d(int p, std::vector<double>& Pp);
+// 1-D Gauss-Legendre and Gauss-Lobatto rules (ascending nodes)
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w);
+void gauss_lobatto(int q, std::vector<double>& x, std::vector<double>& w);
+
+// ---------------------------------------------------------------------------
+// Device data of one p-level. Blocks are kept in the "owner record" layout:
+// segment s = row j, elements i0..i0+15 of that row; each element holds the row
+// blocks needed to compute its W and S faces:
+//   slot 0: S_K[W rows, :]        slot 1: S_{K-1}[E rows, :]   (west neighbour)
+//   slot 2: S_K[S rows, :]        slot 3: S_{K-nx}[N rows, :]  (south neighbour)
+// entry r = (slot*(p+1) + a)*m + c, stored at [(seg*R + r)*16 + lane].
+struct PLevel {
+  int p = 0, n1 = 1, m = 4, R = 16;
+  int nseg = 0;
+  size_t rec_entries = 0;                   // nseg * R * 16
+  double* S64 = nullptr; float* S32 = nullptr; __nv_bfloat16* S16 = nullptr;
+  double* M64 = nullptr; float* M32 = nullptr; __nv_bfloat16* M16 = nullptr;
+  double* Sdense = nullptr;                 // [nel][m][m] FP64 element blocks
+  double* Pp = nullptr;                     // prolongation from p-1 [(p+1) x p] (device)
+  // V-cycle work vectors, [ndof] each, per precision (d = double, f = float)
+  double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
+  float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;
+  // p = 0 only: inverse diagonal of the assembled operator (Chebyshev/Jacobi)
+  double* dinv64 = nullptr; float* dinv32 = nullptr;
+  double lmax = 0.0;
+};
+
+// One Q1 level (interior vertices (nx-1) x (ny-1)); 9-point stencils stored as
+// [9][nv] with offsets (dx, dy) in {-1,0,1}^2, index (dy+1)*3 + (dx+1).
+struct HLevel {
+  int nx = 0, ny = 0, nv = 0;
+  double* st64 = nullptr; float* st32 = nullptr;
+  double* dinv64 = nullptr; float* dinv32 = nullptr;
+  double lmax = 0.0;
+  double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
+  float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;
+};
+
+struct Context {
+  hdg_mesh mesh{};
+  hdg_options opt{};
+  int k = 0, nel = 0, n_edges = 0, ndof = 0;
+  int dev = 0, num_sms = 0;
+  double hx = 0, hy = 0;
+  double* kappa = nullptr;                  // [nel] (copy)
+  int32_t* e2e = nullptr;                   // [nel][4]
+  int32_t* edge_elem = nullptr;             // [n_edges][2]
+  int32_t* edge_face = nullptr;             // [n_edges][2]
+  RefTables ref;                            // finest degree
+  double* d_ref = nullptr;                  // device copy of the finest tables
+  size_t off_P = 0, off_Mb = 0, off_Z = 0, off_Eb = 0, off_Y = 0, off_Ml = 0,
+         off_MiBt = 0, off_MiC = 0, off_Vf = 0, off_wJf = 0, off_M = 0;
+  double* elem_scratch = nullptr;           // [nel][m] per-element partial results
+  // finest-level local factors: Cholesky L of A_u (packed lower) and V = L^-1 W
+  double* Lfac = nullptr;                   // [nel][n(n+1)/2]
+  double* Vfac = nullptr;                   // [nel][n][m]
+  std::vector<PLevel> plev;                 // index p = 0..k
+  std::vector<HLevel> hlev;                 // finest Q1 first
+  double* coarse_L = nullptr;               // dense FP64 Cholesky factor [nc][nc]
+  int coarse_dim = 0;
+  double* coarse_rhs = nullptr;             // [nc] FP64 scratch
+  // CG / reduction scratch
+  double* red = nullptr;                    // partial sums
+  double* scal = nullptr;                   // device scalars
+  double* h_scal = nullptr;                 // pinned host mirror
+  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_zold = nullptr;
+  float* cg_r32 = nullptr;
+  float* cg_z32 = nullptr;
+  int* err_flag = nullptr;                  // device error flag (timeouts)
+  size_t bytes = 0;
+  double setup_ms = 0.0;
+  std::vector<void*> allocs;
+  // CUDA graphs of the V-cycle body, per precision, keyed by stream
+  cudaGraphExec_t vc_graph[3] = {nullptr, nullptr, nullptr};
+  cudaStream_t vc_graph_stream[3] = {nullptr, nullptr, nullptr};
+};
+
+// allocation helper: records the pointer for hdg_destroy
+cudaError_t ctx_alloc(Context* c, void** p, size_t bytes);
+
+// ---------------------------------------------------------------------------
+// Kernel entry points (implemented in the .cu files)
+cudaError_t launch_local_setup(Context* c, cudaStream_t s);
+cudaError_t launch_galerkin_coarsen(Context* c, int p_fine, cudaStream_t s);
+cudaError_t launch_build_records(Context* c, int p, cudaStream_t s);
+cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s);
+cudaError_t launch_p0_diag(Context* c, cudaStream_t s);
+
+// Trace-operator apply on the record layout of level p:
+//   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)
+// vectors in double (prec FP64) or float (FP32/BF16); cvec may be null.
+cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, const void* cvec,
+                         void* y, double alpha, double beta, int nrhs, cudaStream_t s);
+
+// Multigrid pieces (hdg_mg.cu)
+cudaError_t build_hierarchy(Context* c, cudaStream_t s);
+cudaError_t vcycle(Context* c, int prec, const void* r, void* z, cudaStream_t s);
+int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, int inner,
+              hdg_solve_info* info, cudaStream_t s);
+
+// Vector helpers (hdg_apply.cu)
+cudaError_t vec_dot(Context* c, const double* a, const double* b, int n, double* out_dev, cudaStream_t s);
+cudaError_t vec_fill(void* p, int prec, size_t n, cudaStream_t s);
+
+// Local element operations (hdg_local.cu)
+cudaError_t launch_condense(Context* c, const double* f_q, double* b, int nrhs, cudaStream_t s);
+cudaError_t launch_recover(Context* c, const double* lam, const double* f_q, double* u, double* q,
+                           cudaStream_t s);
+cudaError_t launch_adjoint(Context* c, const double* f_q, const double* lam, const double* psi,
+                           double* dJ_dlogk, double* dJ_df, cudaStream_t s);
+
+}  // namespace hdg
+
+#define HDG_CUDA_TRY(expr)                                  \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return _e;                       \
+  } while (0)

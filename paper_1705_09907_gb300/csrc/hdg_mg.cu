@@ -1,0 +1,823 @@
+// Nested p/h multigrid (Sec. 6, Algs. 1 and 2) and multigrid-preconditioned CG.
+//
+// p-levels k..1 : element-block operators (records), weighted additive Schwarz
+//                 smoothing, per-edge transfers P (Eq. eq_mg_pro), R = P^T.
+// p = 0         : top of the h-hierarchy; Jacobi-preconditioned Chebyshev.
+// Q1 levels     : interior vertices of nested N, N/2, ... meshes; 9-point
+//                 stencils (conforming Q1 stiffness on the finest mesh, Galerkin
+//                 triple products below), Chebyshev smoothing, bilinear P and
+//                 R = P^T; P_J / P_J^T (edge means, Eq. eq_h_mg_pro) between the
+//                 finest Q1 level and p = 0; FP64 Cholesky on the coarsest mesh.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "hdg_internal.h"
+
+namespace hdg {
+
+constexpr int kRedBlocks = 304;   // fixed reduction grid (deterministic sums)
+
+// ---------------------------------------------------------------------------
+// Deterministic dot products: fixed grid of partial sums, then one block sums
+// the partials in a fixed order.
+template <typename T>
+__global__ void dots_kernel(size_t n, const T* __restrict__ a0, const T* __restrict__ b0,
+                            const T* __restrict__ a1, const T* __restrict__ b1, const T* __restrict__ a2,
+                            const T* __restrict__ b2, double* __restrict__ part) {
+  __shared__ double sh[3][256];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    s0 += (double)a0[t] * (double)b0[t];
+    if (a1) s1 += (double)a1[t] * (double)b1[t];
+    if (a2) s2 += (double)a2[t] * (double)b2[t];
+  }
+  sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1; sh[2][threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 3; ++q) part[q * kRedBlocks + blockIdx.x] = sh[q][0];
+}
+
+__global__ void dots_finalize_kernel(const double* __restrict__ part, int nd, double* __restrict__ out) {
+  __shared__ double sh[3][512];
+  for (int q = 0; q < 3; ++q) {
+    double v = 0.0;
+    for (int t = threadIdx.x; t < kRedBlocks; t += 512) v += part[q * kRedBlocks + t];
+    sh[q][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int w = 256; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 3; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < nd; ++q) out[q] = sh[q][0];
+}
+
+template <typename T>
+static cudaError_t dots(Context* c, size_t n, const T* a0, const T* b0, const T* a1, const T* b1, const T* a2,
+                        const T* b2, double* out, cudaStream_t s) {
+  dots_kernel<T><<<kRedBlocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, c->red);
+  HDG_CUDA_TRY(cudaGetLastError());
+  const int nd = a2 ? 3 : (a1 ? 2 : 1);
+  dots_finalize_kernel<<<1, 512, 0, s>>>(c->red, nd, out);
+  return cudaGetLastError();
+}
+
+cudaError_t vec_dot(Context* c, const double* a, const double* b, int n, double* out_dev, cudaStream_t s) {
+  return dots<double>(c, (size_t)n, a, b, nullptr, nullptr, nullptr, nullptr, out_dev, s);
+}
+
+// ---------------------------------------------------------------------------
+// Elementwise helpers
+template <typename T>
+__global__ void scale_kernel(size_t n, T* __restrict__ x, const double* __restrict__ sc, double mult) {
+  const double f = mult / sc[0];
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    x[t] = (T)((double)x[t] * f);
+}
+
+template <typename T>
+__global__ void mul_kernel(size_t n, const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ y) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = a[t] * b[t];
+}
+
+template <typename TI, typename TO>
+__global__ void copy_convert_kernel(size_t n, const TI* __restrict__ a, TO* __restrict__ b) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    b[t] = (TO)a[t];
+}
+
+static int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  if (b > 2048) b = 2048;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// Chebyshev steps: first step from x = 0 (x = d = c0 * dinv .* f), first step
+// with x given (d = c0 * dinv .* t; x += d), later steps (d = a1 d + a2 dinv .* t;
+// x += d).
+template <typename T>
+__global__ void cheb_first_zero_kernel(size_t n, const T* __restrict__ dinv, const T* __restrict__ f,
+                                       T* __restrict__ x, T* __restrict__ d, T c0) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const T v = c0 * dinv[t] * f[t];
+    x[t] = v;
+    d[t] = v;
+  }
+}
+template <typename T>
+__global__ void cheb_step_kernel(size_t n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ x,
+                                 T* __restrict__ d, T a1, T a2) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const T v = a1 * d[t] + a2 * dinv[t] * r[t];
+    d[t] = v;
+    x[t] += v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// p-transfers per edge. P is [(pc+2) x (pc+1)] row-major: fine node a', coarse a.
+template <typename T>
+__global__ void restrict_p_kernel(int n_edges, int n1c, const double* __restrict__ P,
+                                  const T* __restrict__ rf, T* __restrict__ rc) {
+  const int n1f = n1c + 1;
+  const size_t total = (size_t)n_edges * n1c;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = t / n1c;
+    const int a = (int)(t % n1c);
+    T s = 0;
+    for (int b = 0; b < n1f; ++b) s += (T)P[b * n1c + a] * rf[e * n1f + b];
+    rc[t] = s;
+  }
+}
+template <typename T>
+__global__ void prolong_p_add_kernel(int n_edges, int n1c, const double* __restrict__ P,
+                                     const T* __restrict__ xc, T* __restrict__ xf) {
+  const int n1f = n1c + 1;
+  const size_t total = (size_t)n_edges * n1f;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = t / n1f;
+    const int a = (int)(t % n1f);
+    T s = 0;
+    for (int b = 0; b < n1c; ++b) s += (T)P[a * n1c + b] * xc[e * n1c + b];
+    xf[t] += s;
+  }
+}
+
+// P_J^T: interior vertex (I, J) gets half the sum of its 4 edges' residuals.
+template <typename T>
+__global__ void restrict_J_kernel(int nx, int ny, const T* __restrict__ r0, T* __restrict__ rq) {
+  const int nvx = nx - 1, nvert = (nx - 1) * (ny - 1);
+  const int nv = (nx + 1) * ny;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    const int I = t % nvx + 1, J = t / nvx + 1;
+    const T s = r0[I + (nx + 1) * (J - 1)] + r0[I + (nx + 1) * J] + r0[nv + (I - 1) + nx * J] + r0[nv + I + nx * J];
+    rq[t] = T(0.5) * s;
+  }
+}
+// P_J: every edge gets the mean of its two end vertices (boundary vertices 0);
+// boundary edges stay 0.
+template <typename T>
+__global__ void prolong_J_add_kernel(int nx, int ny, const T* __restrict__ xq, T* __restrict__ x0) {
+  const int nvx = nx - 1;
+  const int nv = (nx + 1) * ny, ne = nv + nx * (ny + 1);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne; t += gridDim.x * blockDim.x) {
+    int I0, J0, I1, J1;
+    bool interior;
+    if (t < nv) {
+      const int i = t % (nx + 1), j = t / (nx + 1);
+      I0 = i; J0 = j; I1 = i; J1 = j + 1;
+      interior = (i > 0 && i < nx);
+    } else {
+      const int u = t - nv, i = u % nx, j = u / nx;
+      I0 = i; J0 = j; I1 = i + 1; J1 = j;
+      interior = (j > 0 && j < ny);
+    }
+    if (!interior) continue;
+    T s = 0;
+    if (I0 > 0 && I0 < nx && J0 > 0 && J0 < ny) s += xq[(I0 - 1) + nvx * (J0 - 1)];
+    if (I1 > 0 && I1 < nx && J1 > 0 && J1 < ny) s += xq[(I1 - 1) + nvx * (J1 - 1)];
+    x0[t] += T(0.5) * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Q1 stencil levels. Stencil [9][nv], offset o = (dy+1)*3 + (dx+1).
+template <typename T>
+__global__ void stencil_apply_kernel(int nx, int ny, const T* __restrict__ st, const T* __restrict__ x,
+                                     const T* __restrict__ c, T* __restrict__ y, T alpha, T beta) {
+  const int nvx = nx - 1, nvy = ny - 1, nvert = nvx * nvy;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    const int I = t % nvx, J = t / nvx;
+    T s = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int I2 = I + dx, J2 = J + dy;
+        if (I2 < 0 || J2 < 0 || I2 >= nvx || J2 >= nvy) continue;
+        s += st[((dy + 1) * 3 + dx + 1) * (size_t)nvert + t] * x[I2 + nvx * J2];
+      }
+    T v = alpha * s;
+    if (c) v += beta * c[t];
+    y[t] = v;
+  }
+}
+
+// full weighting R = P^T of bilinear interpolation
+template <typename T>
+__global__ void restrict_q_kernel(int nxc, int nyc, const T* __restrict__ rf, T* __restrict__ rc) {
+  const int nxf = 2 * nxc, nyf = 2 * nyc;
+  const int nvxc = nxc - 1, nvert = (nxc - 1) * (nyc - 1), nvxf = nxf - 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    const int I = t % nvxc + 1, J = t / nvxc + 1;
+    T s = 0;
+    for (int b = -1; b <= 1; ++b)
+      for (int a = -1; a <= 1; ++a) {
+        const int i = 2 * I + a, j = 2 * J + b;
+        if (i <= 0 || j <= 0 || i >= nxf || j >= nyf) continue;
+        const T w = (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5));
+        s += w * rf[(i - 1) + nvxf * (j - 1)];
+      }
+    rc[t] = s;
+  }
+}
+
+template <typename T>
+__global__ void prolong_q_add_kernel(int nxc, int nyc, const T* __restrict__ xc, T* __restrict__ xf) {
+  const int nxf = 2 * nxc, nyf = 2 * nyc;
+  const int nvxf = nxf - 1, nvert = (nxf - 1) * (nyf - 1), nvxc = nxc - 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    const int i = t % nvxf + 1, j = t / nvxf + 1;
+    const int i0 = i / 2, j0 = j / 2;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
+    const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
+    T s = 0;
+    for (int b = 0; b < nj; ++b)
+      for (int a = 0; a < ni; ++a) {
+        const int I = i0 + a, J = j0 + b;
+        if (I <= 0 || J <= 0 || I >= nxc || J >= nyc) continue;
+        s += wx * wy * xc[(I - 1) + nvxc * (J - 1)];
+      }
+    xf[t] += s;
+  }
+}
+
+// conforming Q1 stiffness (kappa grad u, grad v) on the finest mesh:
+// element matrix kappa * ((hy/hx) Kx + (hx/hy) Ky) with the bilinear patterns
+// Kx = 1/6 [[2,-2,1,-1],[-2,2,-1,1],[1,-1,2,-2],[-1,1,-2,2]] (vertex order
+// (0,0), (1,0), (0,1), (1,1)) and Ky its x/y transpose.
+__global__ void q1_stencil_kernel(int nx, int ny, double hx, double hy, const double* __restrict__ kappa,
+                                  double* __restrict__ st) {
+  const int nvx = nx - 1, nvert = (nx - 1) * (ny - 1);
+  const double ax = hy / hx / 6.0, ay = hx / hy / 6.0;
+  const double Kx[4][4] = {{2, -2, 1, -1}, {-2, 2, -1, 1}, {1, -1, 2, -2}, {-1, 1, -2, 2}};
+  const double Ky[4][4] = {{2, 1, -2, -1}, {1, 2, -1, -2}, {-2, -1, 2, 1}, {-1, -2, 1, 2}};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    const int I = t % nvx + 1, J = t / nvx + 1;
+    double acc[9];
+    for (int o = 0; o < 9; ++o) acc[o] = 0.0;
+    for (int ej = J - 1; ej <= J; ++ej)
+      for (int ei = I - 1; ei <= I; ++ei) {
+        const double kap = kappa[ei + nx * ej];
+        const int la = (I - ei) + 2 * (J - ej);          // local index of (I, J)
+        for (int lb = 0; lb < 4; ++lb) {
+          const int I2 = ei + (lb & 1), J2 = ej + (lb >> 1);
+          if (I2 <= 0 || J2 <= 0 || I2 >= nx || J2 >= ny) continue;
+          const int o = (J2 - J + 1) * 3 + (I2 - I + 1);
+          acc[o] += kap * (ax * Kx[la][lb] + ay * Ky[la][lb]);
+        }
+      }
+    for (int o = 0; o < 9; ++o) st[o * (size_t)nvert + t] = acc[o];
+  }
+}
+
+// Galerkin coarse stencil A_c = P^T A_f P for bilinear P.
+__global__ void galerkin_stencil_kernel(int nxc, int nyc, const double* __restrict__ stf,
+                                        double* __restrict__ stc) {
+  const int nxf = 2 * nxc, nyf = 2 * nyc;
+  const int nvxc = nxc - 1, nvertc = (nxc - 1) * (nyc - 1);
+  const int nvxf = nxf - 1, nvertf = (nxf - 1) * (nyf - 1);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvertc * 9; t += gridDim.x * blockDim.x) {
+    const int v = t % nvertc, o = t / nvertc;
+    const int I = v % nvxc + 1, J = v / nvxc + 1;
+    const int dx = o % 3 - 1, dy = o / 3 - 1;
+    const int I2 = I + dx, J2 = J + dy;
+    double s = 0.0;
+    if (I2 > 0 && J2 > 0 && I2 < nxc && J2 < nyc) {
+      for (int b = -1; b <= 1; ++b)
+        for (int a = -1; a <= 1; ++a) {
+          const int ui = 2 * I + a, uj = 2 * J + b;
+          if (ui <= 0 || uj <= 0 || ui >= nxf || uj >= nyf) continue;
+          const double wu = (a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5);
+          for (int b2 = -1; b2 <= 1; ++b2)
+            for (int a2 = -1; a2 <= 1; ++a2) {
+              const int vi = 2 * I2 + a2, vj = 2 * J2 + b2;
+              if (vi <= 0 || vj <= 0 || vi >= nxf || vj >= nyf) continue;
+              const int ox = vi - ui, oy = vj - uj;
+              if (ox < -1 || ox > 1 || oy < -1 || oy > 1) continue;
+              const double wv = (a2 == 0 ? 1.0 : 0.5) * (b2 == 0 ? 1.0 : 0.5);
+              s += wu * wv * stf[((oy + 1) * 3 + ox + 1) * (size_t)nvertf + (ui - 1) + nvxf * (uj - 1)];
+            }
+        }
+    }
+    stc[o * (size_t)nvertc + v] = s;
+  }
+}
+
+__global__ void stencil_diag_kernel(int nvert, const double* __restrict__ st, double* __restrict__ dinv64,
+                                    float* __restrict__ dinv32) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    const double v = 1.0 / st[4 * (size_t)nvert + t];
+    dinv64[t] = v;
+    if (dinv32) dinv32[t] = (float)v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: dense FP64 matrix from the stencil, Cholesky (one block),
+// and the per-cycle triangular solves (one block).
+__global__ void dense_from_stencil_kernel(int nx, int ny, const double* __restrict__ st, double* __restrict__ A) {
+  const int nvx = nx - 1, n = (nx - 1) * (ny - 1);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * n; t += gridDim.x * blockDim.x) A[t] = 0.0;
+  __syncthreads();
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int I = t % nvx, J = t / nvx;
+    for (int o = 0; o < 9; ++o) {
+      const int I2 = I + o % 3 - 1, J2 = J + o / 3 - 1;
+      if (I2 < 0 || J2 < 0 || I2 >= nvx || J2 >= ny - 1) continue;
+      A[(size_t)t * n + I2 + nvx * J2] = st[o * (size_t)n + t];
+    }
+  }
+}
+
+__global__ void cholesky_block_kernel(int n, double* __restrict__ A, int* err) {
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    const double ajj = A[(size_t)j * n + j];
+    if (!(ajj > 0.0) && threadIdx.x == 0) atomicExch(err, 4);
+    const double d = sqrt(fmax(ajj, 1e-300));
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + j] /= d;
+    __syncthreads();
+    if (threadIdx.x == 0) A[(size_t)j * n + j] = d;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      const double lij = A[(size_t)i * n + j];
+      for (int l = j + 1; l <= i; ++l) A[(size_t)i * n + l] -= lij * A[(size_t)l * n + j];
+    }
+  }
+}
+
+template <typename T>
+__global__ void coarse_solve_kernel(int n, const double* __restrict__ L, const T* __restrict__ r,
+                                    T* __restrict__ x, double* __restrict__ w) {
+  // forward then backward substitution, columns in parallel over threads
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = (double)r[i];
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) w[j] /= L[(size_t)j * n + j];
+    __syncthreads();
+    const double wj = w[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) w[i] -= L[(size_t)i * n + j] * wj;
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) w[j] /= L[(size_t)j * n + j];
+    __syncthreads();
+    const double wj = w[j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) w[i] -= L[(size_t)j * n + i] * wj;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (T)w[i];
+}
+
+// ---------------------------------------------------------------------------
+// Power-iteration start vector s_i = ((7919 i) mod 1009) / 1009 - 1/2 over the
+// interior unknowns in increasing order (for p = 0: interior edges, vertical
+// ones before horizontal ones).
+__global__ void power_start_edges_kernel(int nx, int ny, double* __restrict__ x) {
+  const int nv = (nx + 1) * ny, ne = nv + nx * (ny + 1);
+  const int nvi = (nx - 1) * ny;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne; t += gridDim.x * blockDim.x) {
+    long idx = -1;
+    if (t < nv) {
+      const int i = t % (nx + 1), j = t / (nx + 1);
+      if (i > 0 && i < nx) idx = (long)j * (nx - 1) + (i - 1);
+    } else {
+      const int u = t - nv, i = u % nx, j = u / nx;
+      if (j > 0 && j < ny) idx = nvi + (long)(j - 1) * nx + i;
+    }
+    x[t] = idx < 0 ? 0.0 : (double)((7919L * idx) % 1009L) / 1009.0 - 0.5;
+  }
+}
+__global__ void power_start_verts_kernel(int n, double* __restrict__ x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+    x[t] = (double)((7919L * t) % 1009L) / 1009.0 - 0.5;
+}
+
+// ---------------------------------------------------------------------------
+// Level operators used by the V-cycle, generic over the vector type.
+static cudaError_t p0_apply(Context* c, int prec, const void* v, const void* cv, void* y, double al, double be,
+                            cudaStream_t s) {
+  return launch_apply(c, 0, 0, prec, v, cv, y, al, be, 1, s);
+}
+
+template <typename T>
+static cudaError_t q_apply(HLevel& H, const T* st, const T* x, const T* cv, T* y, double al, double be,
+                           cudaStream_t s) {
+  stencil_apply_kernel<T><<<grid_for(H.nv), 256, 0, s>>>(H.nx, H.ny, st, x, cv, y, (T)al, (T)be);
+  return cudaGetLastError();
+}
+
+struct ChebCoef {
+  double c0;
+  std::vector<double> a1, a2;
+};
+static ChebCoef cheb_coefficients(double lmax, int degree) {
+  const double a = 0.1 * lmax, b = 1.1 * lmax;
+  const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+  ChebCoef cc;
+  cc.c0 = 1.0 / theta;
+  double rho = 1.0 / sigma;
+  for (int i = 1; i < degree; ++i) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    cc.a1.push_back(rn * rho);
+    cc.a2.push_back(2.0 * rn / delta);
+    rho = rn;
+  }
+  return cc;
+}
+
+// nu Chebyshev smoothing steps on one h-level (the p = 0 level when H == nullptr).
+template <typename T>
+static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x, T* t, T* d, bool x_zero,
+                               int nu, cudaStream_t s) {
+  const bool p0 = (H == nullptr);
+  PLevel& L0 = c->plev[0];
+  const size_t n = p0 ? (size_t)c->n_edges : (size_t)H->nv;
+  const T* dinv = p0 ? (const T*)(prec == HDG_PREC_FP64 ? (const void*)L0.dinv64 : (const void*)L0.dinv32)
+                     : (const T*)(prec == HDG_PREC_FP64 ? (const void*)H->dinv64 : (const void*)H->dinv32);
+  const T* st = p0 ? nullptr : (const T*)(prec == HDG_PREC_FP64 ? (const void*)H->st64 : (const void*)H->st32);
+  const ChebCoef cc = cheb_coefficients(p0 ? L0.lmax : H->lmax, c->opt.cheb_degree);
+  auto A = [&](const T* v, const T* cv, T* y, double al, double be) -> cudaError_t {
+    if (p0) return p0_apply(c, prec, v, cv, y, al, be, s);
+    return q_apply<T>(*H, st, v, cv, y, al, be, s);
+  };
+  const int g = grid_for(n);
+  for (int step = 0; step < nu; ++step) {
+    const T* rsrc;
+    if (step == 0 && x_zero) {
+      cheb_first_zero_kernel<T><<<g, 256, 0, s>>>(n, dinv, f, x, d, (T)cc.c0);
+      HDG_CUDA_TRY(cudaGetLastError());
+      rsrc = f;
+    } else {
+      HDG_CUDA_TRY(A(x, f, t, -1.0, 1.0));                    // t = f - A x
+      cheb_step_kernel<T><<<g, 256, 0, s>>>(n, dinv, t, x, d, (T)0, (T)cc.c0);   // d = c0 D^-1 t
+      HDG_CUDA_TRY(cudaGetLastError());
+      rsrc = t;
+    }
+    for (size_t i = 0; i < cc.a1.size(); ++i) {
+      HDG_CUDA_TRY(A(d, rsrc, t, -1.0, 1.0));                 // t = r - A d
+      cheb_step_kernel<T><<<g, 256, 0, s>>>(n, dinv, t, x, d, (T)cc.a1[i], (T)cc.a2[i]);
+      HDG_CUDA_TRY(cudaGetLastError());
+      rsrc = t;
+    }
+  }
+  return cudaSuccess;
+}
+
+// Alg. 1 on the h-levels: level l = -1 is the p = 0 HDG space, l >= 0 the Q1
+// levels (finest first); the last Q1 level is solved directly.
+template <typename T>
+static cudaError_t hmg(Context* c, int prec, int l, const T* r, T* x, cudaStream_t s) {
+  const int nh = (int)c->hlev.size();
+  if (l == nh - 1) {
+    HLevel& H = c->hlev[l];
+    coarse_solve_kernel<T><<<1, 256, 0, s>>>(H.nv, c->coarse_L, r, x, c->coarse_rhs);
+    return cudaGetLastError();
+  }
+  const bool p0 = (l < 0);
+  HLevel* H = p0 ? nullptr : &c->hlev[l];
+  PLevel& L0 = c->plev[0];
+  T *t, *d;
+  if (p0) {
+    t = (T*)(prec == HDG_PREC_FP64 ? (void*)L0.t64 : (void*)L0.t32);
+    d = (T*)(prec == HDG_PREC_FP64 ? (void*)L0.d64 : (void*)L0.d32);
+  } else {
+    t = (T*)(prec == HDG_PREC_FP64 ? (void*)H->t64 : (void*)H->t32);
+    d = (T*)(prec == HDG_PREC_FP64 ? (void*)H->d64 : (void*)H->d32);
+  }
+  HDG_CUDA_TRY(cheb_smooth<T>(c, prec, H, r, x, t, d, true, c->opt.nu1, s));
+  // residual and restriction to the next (coarser) Q1 level
+  HLevel& Hc = c->hlev[l + 1];
+  T* rc = (T*)(prec == HDG_PREC_FP64 ? (void*)Hc.r64 : (void*)Hc.r32);
+  T* xc = (T*)(prec == HDG_PREC_FP64 ? (void*)Hc.x64 : (void*)Hc.x32);
+  if (p0) {
+    HDG_CUDA_TRY(p0_apply(c, prec, x, r, t, -1.0, 1.0, s));
+    restrict_J_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, t, rc);
+  } else {
+    const T* st = (const T*)(prec == HDG_PREC_FP64 ? (const void*)H->st64 : (const void*)H->st32);
+    HDG_CUDA_TRY(q_apply<T>(*H, st, x, r, t, -1.0, 1.0, s));
+    restrict_q_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(Hc.nx, Hc.ny, t, rc);
+  }
+  HDG_CUDA_TRY(cudaGetLastError());
+  HDG_CUDA_TRY(hmg<T>(c, prec, l + 1, rc, xc, s));
+  if (p0) prolong_J_add_kernel<T><<<grid_for(c->n_edges), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, xc, x);
+  else prolong_q_add_kernel<T><<<grid_for(H->nv), 256, 0, s>>>(Hc.nx, Hc.ny, xc, x);
+  HDG_CUDA_TRY(cudaGetLastError());
+  return cheb_smooth<T>(c, prec, H, r, x, t, d, false, c->opt.nu2, s);
+}
+
+// Alg. 2 on p-level p >= 1 (zero initial guess): r, x are level-p vectors.
+template <typename T>
+static cudaError_t pmg(Context* c, int prec, int p, const T* r, T* x, cudaStream_t s) {
+  PLevel& L = c->plev[p];
+  PLevel& Lc = c->plev[p - 1];
+  T* t = (T*)(prec == HDG_PREC_FP64 ? (void*)L.t64 : (void*)L.t32);
+  const int nu1 = c->opt.nu1, nu2 = c->opt.nu2;
+  // pre-smoothing: x = M r, then x += M (r - A x)
+  HDG_CUDA_TRY(launch_apply(c, p, 1, prec, r, nullptr, x, 1.0, 0.0, 1, s));
+  for (int i = 1; i < nu1; ++i) {
+    HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
+    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, 1, s));
+  }
+  // restricted residual
+  HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
+  T* rc = (T*)(prec == HDG_PREC_FP64 ? (void*)Lc.r64 : (void*)Lc.r32);
+  T* xc = (T*)(prec == HDG_PREC_FP64 ? (void*)Lc.x64 : (void*)Lc.x32);
+  restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1), 256, 0, s>>>(c->n_edges, Lc.n1, L.Pp, t, rc);
+  HDG_CUDA_TRY(cudaGetLastError());
+  if (p - 1 == 0) HDG_CUDA_TRY(hmg<T>(c, prec, -1, rc, xc, s));
+  else HDG_CUDA_TRY(pmg<T>(c, prec, p - 1, rc, xc, s));
+  prolong_p_add_kernel<T><<<grid_for((size_t)c->n_edges * L.n1), 256, 0, s>>>(c->n_edges, Lc.n1, L.Pp, xc, x);
+  HDG_CUDA_TRY(cudaGetLastError());
+  for (int i = 0; i < nu2; ++i) {
+    HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
+    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, 1, s));
+  }
+  return cudaSuccess;
+}
+
+// V-cycle body on the context's top-level buffers r -> x of level k.
+template <typename T>
+static cudaError_t vcycle_body(Context* c, int prec, cudaStream_t s) {
+  PLevel& L = c->plev[c->k];
+  const T* r = (const T*)(prec == HDG_PREC_FP64 ? (void*)L.r64 : (void*)L.r32);
+  T* x = (T*)(prec == HDG_PREC_FP64 ? (void*)L.x64 : (void*)L.x32);
+  if (c->k == 0) return hmg<T>(c, prec, -1, r, x, s);
+  return pmg<T>(c, prec, c->k, r, x, s);
+}
+
+static cudaError_t vcycle_body_any(Context* c, int prec, cudaStream_t s) {
+  if (prec == HDG_PREC_FP64) return vcycle_body<double>(c, prec, s);
+  return vcycle_body<float>(c, prec, s);
+}
+
+// z = V r. r and z are double for FP64, float otherwise (device, [ndof]).
+cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_double, cudaStream_t s) {
+  PLevel& L = c->plev[c->k];
+  const size_t n = (size_t)c->ndof;
+  const int g = grid_for(n);
+  if (prec == HDG_PREC_FP64) {
+    HDG_CUDA_TRY(cudaMemcpyAsync(L.r64, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else if (r_double) {
+    copy_convert_kernel<double, float><<<g, 256, 0, s>>>(n, (const double*)r, L.r32);
+    HDG_CUDA_TRY(cudaGetLastError());
+  } else {
+    HDG_CUDA_TRY(cudaMemcpyAsync(L.r32, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  const int gi = prec;
+  if (c->opt.use_graphs) {
+    if (c->vc_graph[gi] == nullptr || c->vc_graph_stream[gi] != s) {
+      if (c->vc_graph[gi]) { cudaGraphExecDestroy(c->vc_graph[gi]); c->vc_graph[gi] = nullptr; }
+      cudaStream_t cap = s;
+      bool own = false;
+      if (cap == 0) {  // the legacy stream cannot be captured: capture on a private stream
+        HDG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        own = true;
+      }
+      cudaGraph_t g0;
+      HDG_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+      cudaError_t eb = vcycle_body_any(c, prec, cap);
+      cudaError_t ee = cudaStreamEndCapture(cap, &g0);
+      if (own) cudaStreamDestroy(cap);
+      HDG_CUDA_TRY(eb);
+      HDG_CUDA_TRY(ee);
+      HDG_CUDA_TRY(cudaGraphInstantiate(&c->vc_graph[gi], g0, 0));
+      cudaGraphDestroy(g0);
+      c->vc_graph_stream[gi] = s;
+    }
+    HDG_CUDA_TRY(cudaGraphLaunch(c->vc_graph[gi], s));
+  } else {
+    HDG_CUDA_TRY(vcycle_body_any(c, prec, s));
+  }
+  if (prec == HDG_PREC_FP64) {
+    HDG_CUDA_TRY(cudaMemcpyAsync(z, L.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  } else if (r_double) {
+    copy_convert_kernel<float, double><<<g, 256, 0, s>>>(n, L.x32, (double*)z);
+    HDG_CUDA_TRY(cudaGetLastError());
+  } else {
+    HDG_CUDA_TRY(cudaMemcpyAsync(z, L.x32, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t vcycle(Context* c, int prec, const void* r, void* z, cudaStream_t s) {
+  return vcycle_typed(c, prec, r, z, false, s);
+}
+
+// ---------------------------------------------------------------------------
+// Hierarchy construction (after the p-level blocks exist).
+static cudaError_t alloc_vecs_d(Context* c, size_t n, std::initializer_list<double**> ps) {
+  for (double** p : ps) HDG_CUDA_TRY(ctx_alloc(c, (void**)p, n * sizeof(double)));
+  return cudaSuccess;
+}
+static cudaError_t alloc_vecs_f(Context* c, size_t n, std::initializer_list<float**> ps) {
+  for (float** p : ps) HDG_CUDA_TRY(ctx_alloc(c, (void**)p, n * sizeof(float)));
+  return cudaSuccess;
+}
+
+// lambda_max(D^-1 A) by 10 power iterations from the fixed pattern (FP64).
+static cudaError_t power_iteration(Context* c, HLevel* H, double* out, cudaStream_t s) {
+  const bool p0 = (H == nullptr);
+  const size_t n = p0 ? (size_t)c->n_edges : (size_t)H->nv;
+  double *x, *y;
+  HDG_CUDA_TRY(cudaMallocAsync((void**)&x, n * sizeof(double), s));
+  HDG_CUDA_TRY(cudaMallocAsync((void**)&y, n * sizeof(double), s));
+  const int g = grid_for(n);
+  if (p0) power_start_edges_kernel<<<g, 256, 0, s>>>(c->mesh.nx, c->mesh.ny, x);
+  else power_start_verts_kernel<<<g, 256, 0, s>>>((int)n, x);
+  HDG_CUDA_TRY(cudaGetLastError());
+  const double* dinv = p0 ? c->plev[0].dinv64 : H->dinv64;
+  double* sc = c->scal + 16;
+  HDG_CUDA_TRY(dots<double>(c, n, x, x, nullptr, nullptr, nullptr, nullptr, sc, s));
+  // x /= |x|: scale by 1/sqrt(sc[0]) -- done on the host-visible value below
+  double h_nrm2 = 0.0;
+  HDG_CUDA_TRY(cudaMemcpyAsync(&h_nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HDG_CUDA_TRY(cudaStreamSynchronize(s));
+  double* scale_dev = c->scal + 20;
+  double one_over = std::sqrt(h_nrm2);
+  HDG_CUDA_TRY(cudaMemcpyAsync(scale_dev, &one_over, sizeof(double), cudaMemcpyHostToDevice, s));
+  scale_kernel<double><<<g, 256, 0, s>>>(n, x, scale_dev, 1.0);
+  HDG_CUDA_TRY(cudaGetLastError());
+  double lam = 0.0;
+  for (int it = 0; it < 10; ++it) {
+    if (p0) HDG_CUDA_TRY(p0_apply(c, HDG_PREC_FP64, x, nullptr, y, 1.0, 0.0, s));
+    else HDG_CUDA_TRY(q_apply<double>(*H, H->st64, x, nullptr, y, 1.0, 0.0, s));
+    mul_kernel<double><<<g, 256, 0, s>>>(n, y, dinv, y);
+    HDG_CUDA_TRY(cudaGetLastError());
+    HDG_CUDA_TRY(dots<double>(c, n, y, y, nullptr, nullptr, nullptr, nullptr, sc, s));
+    HDG_CUDA_TRY(cudaMemcpyAsync(&h_nrm2, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HDG_CUDA_TRY(cudaStreamSynchronize(s));
+    lam = std::sqrt(h_nrm2);
+    HDG_CUDA_TRY(cudaMemcpyAsync(scale_dev, &lam, sizeof(double), cudaMemcpyHostToDevice, s));
+    scale_kernel<double><<<g, 256, 0, s>>>(n, y, scale_dev, 1.0);
+    HDG_CUDA_TRY(cudaGetLastError());
+    std::swap(x, y);
+  }
+  HDG_CUDA_TRY(cudaStreamSynchronize(s));
+  *out = lam;
+  HDG_CUDA_TRY(cudaFreeAsync(x, s));
+  HDG_CUDA_TRY(cudaFreeAsync(y, s));
+  return cudaSuccess;
+}
+
+cudaError_t build_hierarchy(Context* c, cudaStream_t s) {
+  const bool mixed = c->opt.mixed != 0;
+  const size_t ne = (size_t)c->n_edges;
+  // p-level vectors
+  for (int p = 0; p <= c->k; ++p) {
+    PLevel& L = c->plev[p];
+    const size_t n = ne * L.n1;
+    HDG_CUDA_TRY(alloc_vecs_d(c, n, {&L.r64, &L.x64, &L.t64}));
+    if (mixed) HDG_CUDA_TRY(alloc_vecs_f(c, n, {&L.r32, &L.x32, &L.t32}));
+  }
+  // p = 0 Jacobi diagonal and Chebyshev direction vector
+  PLevel& L0 = c->plev[0];
+  HDG_CUDA_TRY(alloc_vecs_d(c, ne, {&L0.d64}));
+  if (mixed) HDG_CUDA_TRY(alloc_vecs_f(c, ne, {&L0.d32}));
+  HDG_CUDA_TRY(ctx_alloc(c, (void**)&L0.dinv64, ne * sizeof(double)));
+  if (mixed) HDG_CUDA_TRY(ctx_alloc(c, (void**)&L0.dinv32, ne * sizeof(float)));
+  HDG_CUDA_TRY(launch_p0_diag(c, s));
+  // Q1 levels
+  int nx = c->mesh.nx, ny = c->mesh.ny;
+  c->hlev.clear();
+  if (nx < 2 || ny < 2) return cudaErrorInvalidValue;
+  {
+    HLevel H; H.nx = nx; H.ny = ny; H.nv = (nx - 1) * (ny - 1);
+    c->hlev.push_back(H);
+  }
+  const int cn = c->opt.coarse_n;
+  while (nx % 2 == 0 && ny % 2 == 0 && nx / 2 >= cn && ny / 2 >= cn && nx > cn && nx / 2 >= 2 && ny / 2 >= 2) {
+    nx /= 2; ny /= 2;
+    HLevel H; H.nx = nx; H.ny = ny; H.nv = (nx - 1) * (ny - 1);
+    c->hlev.push_back(H);
+  }
+  for (size_t l = 0; l < c->hlev.size(); ++l) {
+    HLevel& H = c->hlev[l];
+    const size_t n = (size_t)H.nv;
+    HDG_CUDA_TRY(ctx_alloc(c, (void**)&H.st64, 9 * n * sizeof(double)));
+    HDG_CUDA_TRY(alloc_vecs_d(c, n, {&H.dinv64, &H.r64, &H.x64, &H.t64, &H.d64}));
+    if (mixed) {
+      HDG_CUDA_TRY(ctx_alloc(c, (void**)&H.st32, 9 * n * sizeof(float)));
+      HDG_CUDA_TRY(alloc_vecs_f(c, n, {&H.dinv32, &H.r32, &H.x32, &H.t32, &H.d32}));
+    }
+    if (l == 0) {
+      q1_stencil_kernel<<<grid_for(n), 256, 0, s>>>(H.nx, H.ny, c->hx, c->hy, c->kappa, H.st64);
+    } else {
+      galerkin_stencil_kernel<<<grid_for(9 * n), 256, 0, s>>>(H.nx, H.ny, c->hlev[l - 1].st64, H.st64);
+    }
+    HDG_CUDA_TRY(cudaGetLastError());
+    stencil_diag_kernel<<<grid_for(n), 256, 0, s>>>((int)n, H.st64, H.dinv64, H.dinv32);
+    HDG_CUDA_TRY(cudaGetLastError());
+    if (mixed) {
+      copy_convert_kernel<double, float><<<grid_for(9 * n), 256, 0, s>>>(9 * n, H.st64, H.st32);
+      HDG_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  // Chebyshev bounds on the smoothed levels (p = 0 and every Q1 level but the last)
+  HDG_CUDA_TRY(power_iteration(c, nullptr, &L0.lmax, s));
+  for (size_t l = 0; l + 1 < c->hlev.size(); ++l) HDG_CUDA_TRY(power_iteration(c, &c->hlev[l], &c->hlev[l].lmax, s));
+  // coarsest dense Cholesky (FP64)
+  HLevel& Hc = c->hlev.back();
+  const int nc = Hc.nv;
+  c->coarse_dim = nc;
+  HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->coarse_L, (size_t)nc * nc * sizeof(double)));
+  HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->coarse_rhs, (size_t)nc * sizeof(double)));
+  dense_from_stencil_kernel<<<1, 256, 0, s>>>(Hc.nx, Hc.ny, Hc.st64, c->coarse_L);
+  HDG_CUDA_TRY(cudaGetLastError());
+  cholesky_block_kernel<<<1, 256, 0, s>>>(nc, c->coarse_L, c->err_flag);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Preconditioned CG on the FP64 trace system.
+// scal layout: 0 rz, 1 pq, 2 rr, 3 r.zold, 4 bb, 8.. scratch
+__global__ void cg_xr_kernel(size_t n, const double* __restrict__ scal, const double* __restrict__ p,
+                             const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
+  const double alpha = scal[0] / scal[1];
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    x[t] += alpha * p[t];
+    r[t] -= alpha * q[t];
+  }
+}
+// p = z + beta p, beta = (r.z_new - r.z_old [flexible]) / rz_old; then rz <- r.z_new
+__global__ void cg_p_kernel(size_t n, double* __restrict__ scal, const double* __restrict__ z,
+                            double* __restrict__ p, int flexible) {
+  const double rz_new = scal[8];
+  const double num = flexible ? rz_new - scal[9] : rz_new;
+  const double beta = num / scal[0];
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    p[t] = z[t] + beta * p[t];
+}
+__global__ void cg_commit_kernel(double* scal) { scal[0] = scal[8]; }
+
+int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, int inner, hdg_solve_info* info,
+              cudaStream_t s) {
+  const size_t n = (size_t)c->ndof;
+  const int g = grid_for(n);
+  double* r = c->cg_r;
+  double* z = c->cg_z;
+  double* p = c->cg_p;
+  double* q = c->cg_q;
+  double* zold = c->cg_zold;
+  double* sc = c->scal;
+  double* h = c->h_scal;
+  const bool flexible = inner != HDG_PREC_FP64;
+#define CK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return HDG_ERR_CUDA; } while (0)
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(dots<double>(c, n, b, b, nullptr, nullptr, nullptr, nullptr, sc + 4, s));
+  CK(cudaMemcpyAsync(h, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const double bn = std::sqrt(h[0]);
+  if (info) { info->iterations = 0; info->relres = 0.0; info->relres_history[0] = 1.0; }
+  if (!(bn > 0.0)) {
+    if (info) info->relres = 0.0;
+    return (bn == 0.0) ? HDG_OK : HDG_ERR_INVALID_ARG;
+  }
+  CK(vcycle_typed(c, inner, r, z, true, s));
+  CK(dots<double>(c, n, r, z, nullptr, nullptr, nullptr, nullptr, sc + 0, s));
+  CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int it = 0;
+  double rel = 1.0;
+  int status = HDG_ERR_NOT_CONVERGED;
+  for (it = 1; it <= maxit; ++it) {
+    CK(launch_apply(c, c->k, 0, HDG_PREC_FP64, p, nullptr, q, 1.0, 0.0, 1, s));
+    CK(dots<double>(c, n, p, q, nullptr, nullptr, nullptr, nullptr, sc + 1, s));
+    CK(cudaMemcpyAsync(h + 1, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    cg_xr_kernel<<<g, 256, 0, s>>>(n, sc, p, q, x, r);
+    CK(cudaGetLastError());
+    CK(dots<double>(c, n, r, r, nullptr, nullptr, nullptr, nullptr, sc + 2, s));
+    CK(cudaMemcpyAsync(h + 2, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(h[1] > 0.0) || !std::isfinite(h[1])) { status = HDG_ERR_BREAKDOWN; break; }
+    rel = std::sqrt(h[2]) / bn;
+    if (info && it < 256) info->relres_history[it] = rel;
+    if (!std::isfinite(rel)) { status = HDG_ERR_BREAKDOWN; break; }
+    if (rel <= rtol) { status = HDG_OK; break; }
+    if (flexible) CK(cudaMemcpyAsync(zold, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(vcycle_typed(c, inner, r, z, true, s));
+    if (flexible) CK(dots<double>(c, n, r, z, r, zold, nullptr, nullptr, sc + 8, s));
+    else CK(dots<double>(c, n, r, z, nullptr, nullptr, nullptr, nullptr, sc + 8, s));
+    cg_p_kernel<<<g, 256, 0, s>>>(n, sc, z, p, flexible ? 1 : 0);
+    CK(cudaGetLastError());
+    cg_commit_kernel<<<1, 1, 0, s>>>(sc);
+    CK(cudaGetLastError());
+  }
+#undef CK
+  if (it > maxit) it = maxit;
+  if (info) { info->iterations = it; info->relres = rel; }
+  return status;
+}
+
+}  // namespace hdg
