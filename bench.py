@@ -1,0 +1,367 @@
+"""Benchmark: HDG trace apply and nested-GMG solve on one GB300.
+
+Workload (the paper's headline configuration): 512 x 512 quads on the unit
+square, degree k = 4, per-element kappa = exp(g), g a seeded Gaussian field
+(variance 1, squared-exponential correlation length 0.05, seed 0), f = 1,
+element Schur blocks stored in FP64. One step is one pass of the hot path on
+one right-hand side: condensed right-hand side, multigrid-preconditioned CG
+with FP64 V-cycles to relative residual 1e-10, and local recovery of (u, q).
+The solver set-up (local solvers, hierarchy) runs once before timing and is
+reported separately.
+
+Printed JSON line (rank 0):
+  value          whole-job solves per second (all ranks, replicas)
+  ms_per_step    FP64 GMG-CG solve time to 1e-10 (incl. condense + recovery)
+  roofline       the trace-apply kernel (the dominant kernel of the step),
+                 timed alone with CUDA events over repeated launches
+  trace_apply    GB/s and fraction of the measured HBM copy peak per precision
+  mixed          the same solve with FP32 / BF16 V-cycles in FP64 flexible CG
+  e2e            the same step through the public API with the source samples
+                 copied host -> device and lambda, u copied back each step
+  cpu_baseline   the FP64 oracle (condense + sparse direct solve + recovery)
+                 on a bounded sub-mesh, one core, scaled per element
+
+--impl reference times that oracle alone (the reference arm of this repo).
+Multi-GPU: one replica per rank (the solve has no data-parallel split on one
+box); value sums the ranks' solves.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, K_DEFAULT, SEED = 512, 4, 0
+METRIC = "trace-apply GB/s and %HBM peak; GMG solve time to 1e-10 rel residual, mixed vs FP64 on GPU"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample of the workload
+def _oracle_sample(n_sub, N, k, seed):
+    from oracle import hdg as ohdg, mesh as omesh
+    from paper_1705_09907_gb300 import inputs
+    g = inputs.gaussian_field(N, seed).reshape(N, N)
+    kap = np.exp(g[:n_sub, :n_sub]).ravel()
+    h = 1.0 / N
+    m = omesh.Mesh(n_sub, n_sub, 0.0, 0.0, n_sub * h, n_sub * h)
+    fq = np.ones((m.nel, k + 2, k + 2))
+    t0 = time.perf_counter()
+    prob = ohdg.HDGProblem(m, k, kap)
+    b = prob.condense_rhs(fq)
+    lam = prob.solve_direct(b)
+    prob.recover(lam, fq)
+    return time.perf_counter() - t0, m.nel
+
+
+def cpu_baseline_worker(n_sub, N, k, seed, reps):
+    times = []
+    nel = None
+    for _ in range(reps):
+        t, nel = _oracle_sample(n_sub, N, k, seed)
+        times.append(t)
+    print(json.dumps({"times": times, "nel": nel}))
+
+
+def run_cpu_baseline(N, k, n_sub=48, reps=1):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, "-c",
+           "import bench; bench.cpu_baseline_worker(%d, %d, %d, %d, %d)" % (n_sub, N, k, SEED, reps)]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    t = statistics.median(out["times"])
+    per_elem = t / out["nel"]
+    full = per_elem * N * N
+    return {
+        "value": 1.0 / full, "unit": "solve/s", "cores": 1, "kind": "oracle",
+        "sample": "%dx%d sub-mesh of the %dx%d k=%d lognormal workload (same h and kappa), oracle condense + "
+                  "scipy SuperLU direct solve + recovery, %.2f s, scaled linearly by element count"
+                  % (n_sub, n_sub, N, N, k, t),
+        "sample_seconds": t,
+    }
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    def __init__(self, path, index):
+        self.path = path
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except Exception:
+            rows = []
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def timed_events(fn, reps, torch):
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1705_09907_gb300 import hdg, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    N, k = args.n, args.k
+    peaks = load_peaks()
+    kap = inputs.lognormal_kappa(N, SEED)
+    fq_h = inputs.constant_f(N, k)
+    kap_d = torch.as_tensor(kap, device="cuda")
+    fq_d = torch.as_tensor(fq_h, device="cuda")
+    solver = hdg.HDGSolver(N, N, k, kap_d)
+    info = solver.info
+    rtol = 1e-10
+    u = torch.empty((solver.nel, (k + 1) ** 2), dtype=torch.float64, device="cuda")
+    lam = torch.empty(solver.ndof, dtype=torch.float64, device="cuda")
+
+    last = {}
+
+    def step(inner="fp64"):
+        b = solver.condense_rhs(fq_d)
+        lam_, inf = solver.solve(b, rtol=rtol, maxit=200, inner=inner, out=lam)
+        uu, qq = solver.recover(lam_, fq_d)
+        last["info"] = inf
+        return uu
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if args.profile:
+        # short fixed sequence for profiler launch lists: one solve step, then
+        # three trace applies per precision; no other work
+        step()
+        x64 = torch.as_tensor(inputs.random_trace(solver.n_edges, k, seed=1), device="cuda")
+        x32 = x64.float()
+        # each precision's applies inside an NVTX range named apply_<prec>
+        # (profilers can select one with --nvtx-include "apply_<prec>/")
+        for p_, xx in (("fp64", x64), ("fp32", x32), ("bf16", x32), ("f32x2", x64)):
+            torch.cuda.nvtx.range_push("apply_" + p_)
+            for _ in range(3):
+                solver.apply(xx, p_)
+            torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "iterations": last["info"]["iterations"],
+                          "relres": last["info"]["relres"], "vcycle_kernels": solver.get_info()["vcycle_kernels"]}))
+        solver.close()
+        return
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_r%d.csv" % rank), local)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    with clocks:
+        torch.cuda.synchronize()
+        t_ms = timed_events(step, args.steps, torch)
+        its = last["info"]["iterations"]
+        relres = last["info"]["relres"]
+        # the dominant kernel: trace apply at level k, timed alone (inputs >> L2)
+        x64 = torch.as_tensor(inputs.random_trace(solver.n_edges, k, seed=1), device="cuda")
+        y64 = torch.empty_like(x64)
+        apply_ms = {}
+        apply_ms["fp64"] = timed_events(lambda: solver.apply(x64, "fp64", out=y64), args.apply_reps, torch)
+        x32 = x64.float()
+        y32 = torch.empty_like(x32)
+        apply_ms["fp32"] = timed_events(lambda: solver.apply(x32, "fp32", out=y32), args.apply_reps, torch)
+        apply_ms["bf16"] = timed_events(lambda: solver.apply(x32, "bf16", out=y32), args.apply_reps, torch)
+        apply_ms["f32x2"] = timed_events(lambda: solver.apply(x64, "f32x2", out=y64), args.apply_reps, torch)
+    clk = clocks.summary()
+    # mixed-precision solves on the same mesh (outside the clock window: reported, not the headline)
+    lam64 = lam.clone()
+    mixed = {}
+    for inner in ("fp32", "bf16", "f32x2"):
+        step(inner)
+        ms = timed_events(lambda: step(inner), max(1, args.steps // 2), torch)
+        inf = last["info"]
+        err = float(torch.linalg.norm(lam - lam64) / torch.linalg.norm(lam64))
+        mixed[inner] = {"ms_per_solve": ms, "iterations": inf["iterations"], "relres": inf["relres"],
+                        "rel_diff_vs_fp64_solution": err}
+    # end to end through the public API with host buffers
+    fq_pin = torch.as_tensor(fq_h).pin_memory()
+    lam_pin = torch.empty(solver.ndof, dtype=torch.float64).pin_memory()
+    u_pin = torch.empty(tuple(u.shape), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        fd = fq_pin.to("cuda", non_blocking=True)
+        b = solver.condense_rhs(fd)
+        lam_, _ = solver.solve(b, rtol=rtol, maxit=200, out=lam)
+        uu, _ = solver.recover(lam_, fd)
+        lam_pin.copy_(lam_, non_blocking=True)
+        u_pin.copy_(uu, non_blocking=True)
+
+    e2e_step()
+    e2e_ms = timed_events(e2e_step, max(1, args.steps // 2), torch)
+    # launches in the timed region: condense 2 + recover 1 + CG
+    vk = solver.get_info()["vcycle_kernels"]
+    # per CG iteration: apply, 2 dots kernels, x/r update, 2 dots, V-cycle, 2 dots, p update, commit;
+    # the last iteration stops after the convergence check (no V-cycle, dots, p, commit)
+    per_it = 1 + 2 + 1 + 2 + vk + 2 + 1 + 1
+    launches_per_step = 3 + (2 + vk + 2) + per_it * its - (vk + 4)
+    # timing max over ranks
+    t_all = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    t_ms = float(t_all.item())
+    if rank != 0:
+        solver.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    nel, ne, n1 = solver.nel, solver.n_edges, k + 1
+    bytes_S = {"fp64": 8, "fp32": 4, "bf16": 2, "f32x2": 8}
+    bytes_x = {"fp64": 8, "fp32": 4, "bf16": 4, "f32x2": 8}
+    tra = {}
+    for p_, ms in apply_ms.items():
+        algo = nel * 16 * n1 * n1 * bytes_S[p_] + 2 * ne * n1 * bytes_x[p_]
+        gbs = algo / (ms * 1e-3) / 1e9
+        tra[p_] = {"ms": ms, "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
+                   "flops": 2 * nel * 16 * n1 * n1}
+    fp = tra["fp64"]
+    tflops = fp["flops"] / (apply_ms["fp64"] * 1e-3) / 1e12
+    # FP64: 0.25 flop/byte needs more FP64 issue than the GPU has (1.25 TFLOP/s
+    # nominal), so the FP64 apply is bound by the FP64 pipe, not by HBM.
+    roof = {"kernel": "apply_kernel<5,double,double,double> (FP64 trace apply, level k)",
+            "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": tflops / 1.25,
+            "peak_source": "nominal FP64 rate of GB300 (recipe table); HBM fraction in trace_apply",
+            "traffic": None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu = run_cpu_baseline(N, k)
+        except Exception as ex:  # reported, not fatal
+            cpu = {"error": str(ex)[:300]}
+    line = {
+        "metric": METRIC, "value": world * 1000.0 / t_ms, "unit": "solve/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hdg_trace_gmg_pcg", "mesh": "%dx%d" % (N, N), "k": k,
+                   "kappa": "lognormal sigma^2=1 l=0.05 seed 0", "f": 1, "rtol": rtol,
+                   "ndof": solver.ndof, "cg_iterations": its, "final_relres": relres,
+                   "l2": "inputs larger than L2 (FP64 S + Schwarz blocks %.0f MB)" % (2 * nel * 16 * n1 * n1 * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
+        "roofline": roof, "trace_apply": tra, "mixed": mixed,
+        "e2e": {"value": 1000.0 / e2e_ms, "unit": "solve/s", "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(fq_h.nbytes), "d2h_bytes_per_step": int(solver.ndof * 8 + u.numel() * 8)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clk, "peaks": peaks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    N, k = args.n, args.k
+    n_sub = 32
+    for _ in range(args.warmup):
+        _oracle_sample(8, N, k, SEED)
+    times = []
+    nel = None
+    for _ in range(args.steps):
+        t, nel = _oracle_sample(n_sub, N, k, SEED)
+        times.append(t)
+    t = statistics.median(times)
+    per_solve = t / nel * N * N
+    value = 1.0 / per_solve
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solve/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1000.0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hdg_trace_gmg_pcg", "mesh": "%dx%d" % (N, N), "k": k},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "solve/s",
+                         "sample": "%dx%d sub-mesh per step (same h, kappa), oracle condense + SuperLU + recovery, "
+                                   "scaled linearly by element count" % (n_sub, n_sub)},
+        "e2e": {"value": value, "unit": "solve/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--k", type=int, default=K_DEFAULT)
+    ap.add_argument("--apply-reps", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="one solve step and 3 applies per precision, then exit")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -54,10 +54,16 @@ typedef enum {
 } hdg_status;
 
 /* Storage / arithmetic precision of an operator apply or V-cycle.
- *  FP64: blocks and vectors in double, double accumulation.
- *  FP32: blocks and vectors in float, float accumulation.
- *  BF16: blocks in bfloat16, vectors in float, float accumulation. */
-typedef enum { HDG_PREC_FP64 = 0, HDG_PREC_FP32 = 1, HDG_PREC_BF16 = 2 } hdg_prec;
+ *  FP64:  blocks and vectors in double, double accumulation.
+ *  FP32:  blocks and vectors in float, float accumulation.
+ *  BF16:  blocks in bfloat16, vectors in float, float accumulation.
+ *  F32X2: blocks as pairs of floats (hi + lo, about 48 significant bits),
+ *         vectors in double, products and sums in compensated ("double-float")
+ *         FP32 arithmetic: FP64-class results from the FP32 pipe, whose rate on
+ *         this GPU is about 60x the FP64 rate.
+ * FP32 and BF16 apply the condensed blocks to x minus its mean on each element
+ * (exact in exact arithmetic because every S_K has zero row sums). */
+typedef enum { HDG_PREC_FP64 = 0, HDG_PREC_FP32 = 1, HDG_PREC_BF16 = 2, HDG_PREC_F32X2 = 3 } hdg_prec;
 
 typedef struct {
   int nx, ny;                 /* elements per direction, >= 1                */
@@ -70,9 +76,12 @@ typedef struct {
                                  and halving keeps them >= coarse_n (2)       */
   double tau;                 /* HDG stabilisation on every facet (1.0)      */
   int cheb_degree;            /* Chebyshev degree per h-level smoothing step (2) */
-  int mixed;                  /* also build FP32 and BF16 copies of the level
-                                 blocks for mixed-precision V-cycles (1)      */
+  int mixed;                  /* also build FP32, BF16 and F32X2 copies of the
+                                 level blocks (1)                             */
   int use_graphs;             /* capture V-cycles in CUDA graphs (1)         */
+  int autotune;               /* time the apply kernels' launch shapes per
+                                 level and precision at set-up and keep the
+                                 fastest (1); shapes never change results      */
 } hdg_options;
 
 typedef struct {
@@ -81,6 +90,8 @@ typedef struct {
   int coarse_dim;             /* unknowns of the coarsest (direct) solve     */
   size_t device_bytes;        /* device memory held by the context           */
   double setup_ms;            /* wall time of hdg_setup                      */
+  int vcycle_kernels;         /* kernel launches in one V-cycle (0 until the
+                                 first V-cycle has been captured or run)     */
 } hdg_info;
 
 typedef struct {
@@ -136,9 +147,9 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
  * y_e = sum over the two elements K of edge e of S_K[e rows, :] x_K on every
  * interior edge, y = 0 on boundary edges. Each face is written once, by one
  * thread, with no atomics. x, y: device [ndof][nrhs] in the type `prec`
- * selects (double for FP64, float for FP32 and BF16); x and y must not overlap.
- * Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED (BF16/FP32 when the
- * context was built with mixed = 0).
+ * selects (double for FP64 and F32X2, float for FP32 and BF16); x and y must
+ * not overlap. Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED
+ * (FP32/BF16/F32X2 when the context was built with mixed = 0).
  */
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
 
@@ -148,7 +159,9 @@ int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void*
  * R = P^T and prolongation P per edge (Eqs. eq_mg_pro, eq_mg_res), the p = 0
  * level and the Q1 levels with Chebyshev steps, P_J / P_J^T between p = 0 and
  * Q1 (Eq. eq_h_mg_pro), bilinear transfers, and an FP64 Cholesky solve on the
- * coarsest mesh. r, z: device [ndof][nrhs] (double for FP64, float otherwise).
+ * coarsest mesh. r, z: device [ndof][nrhs] (double for FP64 and F32X2, float
+ * for FP32 and BF16; the Q1 levels run in the vector type, the coarsest solve
+ * in FP64).
  * The operator is symmetric positive definite, so CG may use it.
  */
 int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* stream);
@@ -156,10 +169,12 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
 /*
  * Solve A lambda = b (Sec. 3 step (iii)) with conjugate gradients
  * preconditioned by one V-cycle per iteration, to |b - A lambda|_2 <= rtol |b|_2.
- * b, lambda: device [ndof] doubles (nrhs must be 1). The residual, the CG
- * vectors and the update are FP64; `inner` selects the V-cycle precision
- * (FP64, or FP32/BF16 blocks with FP32 accumulation -- then CG uses the
- * flexible Polak-Ribiere beta). info (host, may be NULL) receives the
+ * b, lambda: device [ndof] doubles (nrhs must be 1). The CG vectors, the
+ * update and the residual are FP64 vectors; `inner` selects the V-cycle
+ * precision. With inner = FP64 every apply is plain FP64. With inner = FP32,
+ * BF16 or F32X2 the outer operator apply uses F32X2 blocks (FP64 vectors,
+ * ~48-bit products) and CG uses the flexible Polak-Ribiere beta, since a
+ * low-precision V-cycle is not exactly symmetric. info (host, may be NULL) receives the
  * iteration count and residual history. Errors: NOT_CONVERGED (lambda holds
  * the last iterate), BREAKDOWN, TIMEOUT, CUDA.
  */

@@ -2,7 +2,7 @@
 #include "apply_impl.cuh"
 
 namespace hdg {
-cudaError_t apply_bf16(const Context* c, int n1, const ApplyArgs& a, cudaStream_t s) {
-  return apply_dispatch<__nv_bfloat16, float, float>(c, n1, a, s);
+cudaError_t apply_bf16(const Context* c, int n1, bool diff, const ApplyArgs& a, cudaStream_t s) {
+  return diff ? apply_dispatch<__nv_bfloat16, float, float, true>(c, n1, a, s) : apply_dispatch<__nv_bfloat16, float, float, false>(c, n1, a, s);
 }
 }  // namespace hdg

@@ -24,6 +24,24 @@
 
 namespace hdg {
 
+// Launch shape of the apply: warp pairs per CTA (one CTA per SM, at most 8
+// pairs) and ring stages per pair. `tune` packs a choice made by the set-up
+// autotuner (pairs * 16 + stages); 0 = the default: as many pairs as fit up to
+// 4 (two warps per SM sub-partition), then more stages.
+// stage_bytes: one stage of blocks plus its x windows and partial sums.
+inline void apply_shape(unsigned stage_bytes, int tune, int* np, int* ns) {
+  const int total = (int)((220u * 1024u) / stage_bytes);   // stages that fit
+  if (tune > 0) {
+    *np = tune >> 4; *ns = tune & 15;
+    if (*np >= 1 && *np <= 8 && *ns >= 1 && *np * *ns <= total) return;
+  }
+  if (total <= 0) { *np = 1; *ns = 1; return; }
+  int p = total < 4 ? total : 4;
+  int st = total / p;
+  if (st > 3) st = 3;
+  *np = p; *ns = st < 1 ? 1 : st;
+}
+
 struct ApplyArgs {
   const void* rec;     // record array of the level (type TS)
   const void* v;       // gathered vector (type TV)
@@ -34,9 +52,60 @@ struct ApplyArgs {
   int stages;          // NS
   unsigned stage_bytes;
   int* err;            // device error flag (2 = bounded wait gave up)
+  int tune;            // launch shape from the autotuner (0 = default)
+};
+
+// Double-float value hi + lo (|lo| <= ulp(hi)/2 after renormalisation).
+struct dfloat {
+  float hi, lo;
 };
 
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ dfloat to_acc(float2 v, dfloat) { return dfloat{v.x, v.y}; }
+// double -> (hi, lo) with integer operations (the FP64 pipe is slow on this
+// GPU): hi keeps the leading 24 significant bits (truncated), lo the remaining
+// 29 bits rounded to 24 by the int->float conversion, so hi + lo = v to about
+// 2^-48 relative. Magnitudes below 2^-74 (where the scale 2^(e-1075) would
+// leave the normal float range), zero and huge values take the conversion path.
+__device__ __forceinline__ dfloat split_double(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 949 || e > 1150) {              // |v| < 2^-74, zero, huge: conversion path
+    const float h = __double2float_rn(v);
+    return dfloat{h, __double2float_rn(v - (double)h)};
+  }
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  const unsigned int hib = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29);
+  const unsigned int rem = (unsigned int)(mant & 0x1fffffffull);          // 29 bits below hi
+  // lo = rem * 2^(e - 1075) with the sign of v
+  const float scale = __int_as_float((unsigned int)(e - 1075 + 127) << 23);
+  float lo = __uint2float_rn(rem) * scale;
+  lo = __int_as_float(__float_as_int(lo) | (int)sign);
+  return dfloat{__int_as_float((int)hib), lo};
+}
+__device__ __forceinline__ dfloat to_acc(double v, dfloat) { return split_double(v); }
+// acc + s*x with an error-free product (FMA residual) and an error-free sum
+// (Knuth's two-sum) of the leading parts; the trailing parts are summed in
+// plain FP32, which keeps ~48 significant bits for these short dot products.
+__device__ __forceinline__ float mac(float s, float x, float acc) { return fmaf(s, x, acc); }
+__device__ __forceinline__ double mac(double s, double x, double acc) { return ::fma(s, x, acc); }
+__device__ __forceinline__ dfloat mac(dfloat s, dfloat x, dfloat acc) {
+  const float p = s.hi * x.hi;
+  float e = fmaf(s.hi, x.hi, -p);
+  e = fmaf(s.hi, x.lo, e);
+  e = fmaf(s.lo, x.hi, e);
+  const float sum = acc.hi + p;
+  const float bb = sum - acc.hi;
+  const float err = (acc.hi - (sum - bb)) + (p - bb);
+  return dfloat{sum, acc.lo + (err + e)};
+}
+// value of an accumulator in the output arithmetic
+__device__ __forceinline__ double finish(dfloat a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double finish(double a) { return a; }
+__device__ __forceinline__ float finish(float a) { return a; }
+template <typename TA> struct OutT { using type = TA; };
+template <> struct OutT<dfloat> { using type = double; };
 __device__ __forceinline__ float to_acc(float v, float) { return v; }
 __device__ __forceinline__ double to_acc(double v, double) { return v; }
 __device__ __forceinline__ double to_acc(float v, double) { return (double)v; }
@@ -74,6 +143,46 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   return ok != 0;
 }
 
+// x window of a segment (row j, elements i0..i0+15): 5 edge rows x 18 slots,
+// slot = i - (i0 - 1); each row is one contiguous range of the trace vector:
+//   row 0: vertical edges of row j      row 1: vertical edges of row j-1
+//   row 2: horizontal edges of row j    row 3: horizontal edges of row j+1
+//   row 4: horizontal edges of row j-1
+constexpr int kWinRows = 5, kWinSlots = kSeg + 2;
+
+template <int N1, typename TV>
+__device__ __forceinline__ void issue_window(TV* __restrict__ dst, const TV* __restrict__ v, int seg, int lane,
+                                             const ApplyArgs& a) {
+  const int j = seg / a.spr, i0 = (seg % a.spr) * kSeg;
+  const int nx = a.nx, nv = (nx + 1) * a.ny;
+  const int s0 = i0 == 0 ? 1 : 0;                                   // slot 0 is i = -1
+  const int sv1 = min(kWinSlots, nx - i0 + 2), sh1 = min(kWinSlots, nx - i0 + 1);
+#pragma unroll
+  for (int r = 0; r < kWinRows; ++r) {
+    if ((r == 1 || r == 4) && j == 0) continue;
+    const bool vert = r < 2;
+    const int jr = (r == 0 || r == 2) ? j : (r == 3 ? j + 1 : j - 1);
+    const long e0 = vert ? (long)(i0 - 1) + (long)(nx + 1) * jr : (long)nv + (i0 - 1) + (long)nx * jr;
+    const int hi = (vert ? sv1 : sh1) * N1;
+    TV* d = dst + r * kWinSlots * N1;
+    for (int idx = s0 * N1 + lane; idx < hi; idx += 32) {
+      const TV* src = v + e0 * N1 + idx;
+      if (sizeof(TV) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(d + idx)), "l"(src) : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(d + idx)), "l"(src) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void window_wait(int pending) {
+  // groups complete in order; `pending` = groups allowed to stay in flight
+  if (pending <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else asm volatile("cp.async.wait_group 2;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -90,174 +199,251 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   }
 }
 
-template <int N1, typename TS, typename TV, typename TA>
-__device__ __forceinline__ void apply_segment(const TS* __restrict__ st, int seg, int lane, const ApplyArgs& a) {
+__device__ __forceinline__ void pair_barrier(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+// One thread: lane -> (face, element) of the segment, `slot` = 0 for the
+// element's own row block, 1 for the neighbour across that face. Returns the
+// partial sums of the N1 outputs of the face. x values come from the window
+// (nrhs = 1) or straight from global memory (nrhs > 1).
+template <int N1, typename TS, typename TV, typename TA, bool DIFF>
+__device__ __forceinline__ void partial_segment(const TS* __restrict__ st, const TV* __restrict__ xw, int seg, int lane,
+                                                int slot, int r, const ApplyArgs& a, TA (&acc)[N1]) {
   constexpr int M = 4 * N1;
-  const int face = lane >> 4;           // 0: W faces, 1: S faces
-  const int t = lane & 15;
-  const int j = seg / a.spr;
-  const int i = (seg % a.spr) * kSeg + t;
-  if (i >= a.nx) return;
-  const int nx = a.nx, ny = a.ny;
-  const int nv = (nx + 1) * ny;
+  const int face = lane >> 4, t = lane & 15;
+  const int j = seg / a.spr, i = (seg % a.spr) * kSeg + t;
+  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+#pragma unroll
+  for (int q = 0; q < N1; ++q) acc[q] = TA{};
+  const bool bndrow = face == 0 ? (i == 0) : (j == 0);
+  if (i >= nx || bndrow) return;
+  const int ki = (slot == 1 && face == 0) ? i - 1 : i;
+  const int kj = (slot == 1 && face == 1) ? j - 1 : j;
+  int edge[4], wpos[4];
+  bool bnd[4];
+  edge[0] = ki + (nx + 1) * kj;       bnd[0] = ki <= 0;
+  edge[1] = ki + 1 + (nx + 1) * kj;   bnd[1] = ki >= nx - 1;
+  edge[2] = nv + ki + nx * kj;        bnd[2] = kj <= 0;
+  edge[3] = nv + ki + nx * (kj + 1);  bnd[3] = kj >= ny - 1;
+  {
+    const int sl = ki - (i - t) + 1;
+    const int vrow = (kj == j) ? 0 : 1;
+    const int hlo = (kj == j) ? 2 : 4, hhi = (kj == j) ? 3 : 2;
+    wpos[0] = (vrow * kWinSlots + sl) * N1;
+    wpos[1] = (vrow * kWinSlots + sl + 1) * N1;
+    wpos[2] = (hlo * kWinSlots + sl) * N1;
+    wpos[3] = (hhi * kWinSlots + sl) * N1;
+  }
   const TV* __restrict__ v = (const TV*)a.v;
+  const int nrhs = a.nrhs;
+  TA xv[M];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int b = 0; b < N1; ++b)
+      xv[f * N1 + b] = bnd[f] ? TA{}
+                              : to_acc(xw ? xw[wpos[f] + b] : __ldg(&v[((size_t)edge[f] * N1 + b) * nrhs + r]), TA{});
+  if constexpr (DIFF) {
+    TA mean = TA(0);
+#pragma unroll
+    for (int c = 0; c < M; ++c) mean += xv[c];
+    mean *= TA(1.0 / M);
+#pragma unroll
+    for (int c = 0; c < M; ++c) xv[c] -= mean;
+  }
+  const TS* __restrict__ rows = st + (size_t)((face * 2 + slot) * N1 * M) * kSeg + t;
+#pragma unroll
+  for (int c = 0; c < M; ++c)
+#pragma unroll
+    for (int q = 0; q < N1; ++q) acc[q] = mac(to_acc(rows[(q * M + c) * kSeg], TA{}), xv[c], acc[q]);
+}
+
+// Epilogue of one face (slot-0 warp): y = beta c + alpha (own + neighbour).
+template <int N1, typename TV, typename TO>
+__device__ __forceinline__ void write_face(const TO (&sum)[N1], int seg, int lane, int r, const ApplyArgs& a) {
+  const int face = lane >> 4, t = lane & 15;
+  const int j = seg / a.spr, i = (seg % a.spr) * kSeg + t;
+  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+  if (i >= nx) return;
   const TV* __restrict__ cv = (const TV*)a.cvec;
   TV* __restrict__ y = (TV*)a.y;
+  const int nrhs = a.nrhs;
   const bool bndrow = face == 0 ? (i == 0) : (j == 0);
   const int eout = face == 0 ? i + (nx + 1) * j : nv + i + nx * j;
-  const int nrhs = a.nrhs;
-  for (int r = 0; r < nrhs; ++r) {
-    TA acc[N1];
+  const TO al = (TO)a.alpha, be = (TO)a.beta;
 #pragma unroll
-    for (int q = 0; q < N1; ++q) acc[q] = TA(0);
+  for (int q = 0; q < N1; ++q) {
+    const size_t o = ((size_t)eout * N1 + q) * nrhs + r;
+    TO val = TO(0);
     if (!bndrow) {
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        const int ki = (s == 1 && face == 0) ? i - 1 : i;
-        const int kj = (s == 1 && face == 1) ? j - 1 : j;
-        const TS* __restrict__ rows = st + (size_t)((face * 2 + s) * N1 * M) * kSeg + t;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-          int edge;
-          bool bnd;
-          if (f == 0) { edge = ki + (nx + 1) * kj; bnd = ki == 0; }
-          else if (f == 1) { edge = ki + 1 + (nx + 1) * kj; bnd = ki == nx - 1; }
-          else if (f == 2) { edge = nv + ki + nx * kj; bnd = kj == 0; }
-          else { edge = nv + ki + nx * (kj + 1); bnd = kj == ny - 1; }
-          TA xv[N1];
-#pragma unroll
-          for (int b = 0; b < N1; ++b)
-            xv[b] = bnd ? TA(0) : to_acc(__ldg(&v[((size_t)edge * N1 + b) * nrhs + r]), TA(0));
-#pragma unroll
-          for (int q = 0; q < N1; ++q) {
-#pragma unroll
-            for (int b = 0; b < N1; ++b) acc[q] = fma(to_acc(rows[(q * M + f * N1 + b) * kSeg], TA(0)), xv[b], acc[q]);
-          }
-        }
-      }
+      val = al * sum[q];
+      if (cv) val = mac(be, (TO)cv[o], val);
     }
-    const TA al = (TA)a.alpha, be = (TA)a.beta;
+    y[o] = (TV)val;
+  }
+  // the E / N domain-boundary edges have no owner element: zero them here
+  if (face == 0 && i == nx - 1) {
+    const int eb = nx + (nx + 1) * j;
 #pragma unroll
-    for (int q = 0; q < N1; ++q) {
-      const size_t o = ((size_t)eout * N1 + q) * nrhs + r;
-      TA val = TA(0);
-      if (!bndrow) {
-        val = al * acc[q];
-        if (cv) val = fma(be, to_acc(cv[o], TA(0)), val);
-      }
-      y[o] = (TV)val;
-    }
-    // the E / N domain-boundary edges have no owner element: zero them here
-    if (face == 0 && i == nx - 1) {
-      const int eb = nx + (nx + 1) * j;
+    for (int q = 0; q < N1; ++q) y[((size_t)eb * N1 + q) * nrhs + r] = TV(0);
+  }
+  if (face == 1 && j == ny - 1) {
+    const int eb = nv + i + nx * ny;
 #pragma unroll
-      for (int q = 0; q < N1; ++q) y[((size_t)eb * N1 + q) * nrhs + r] = TV(0);
-    }
-    if (face == 1 && j == ny - 1) {
-      const int eb = nv + i + nx * ny;
-#pragma unroll
-      for (int q = 0; q < N1; ++q) y[((size_t)eb * N1 + q) * nrhs + r] = TV(0);
-    }
+    for (int q = 0; q < N1; ++q) y[((size_t)eb * N1 + q) * nrhs + r] = TV(0);
   }
 }
 
-template <int N1, typename TS, typename TV, typename TA>
-__global__ void __launch_bounds__(256) apply_kernel(ApplyArgs a) {
+// Shared-memory bytes of one ring stage: blocks + two x windows + partials.
+template <int N1, typename TS, typename TV, typename TO>
+constexpr size_t stage_total_bytes() {
+  return (size_t)16 * N1 * N1 * kSeg * sizeof(TS) +
+         2 * (((size_t)kWinRows * kWinSlots * N1 * sizeof(TV) + 15) / 16 * 16) +
+         (((size_t)32 * N1 * sizeof(TO) + 15) / 16 * 16) + 16;
+}
+
+// Work split: warp pairs. Both warps of a pair stream the same segments through
+// the pair's ring; warp 0 of the pair applies each element's own row blocks,
+// warp 1 the neighbours' row blocks and hands its partial sums to warp 0
+// through shared memory (named barrier per pair), which writes the faces.
+template <int N1, typename TS, typename TV, typename TA, bool DIFF>
+__global__ void __launch_bounds__(512) apply_kernel(ApplyArgs a) {
+  using TO = typename OutT<TA>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
+  const int np = blockDim.x >> 6;                 // pairs per CTA
+  const int pr = w >> 1, role = w & 1;            // role 0: own blocks, 1: neighbour blocks
   const int NS = a.stages;
   const unsigned SB = a.stage_bytes;
-  unsigned char* ring = smem_raw + (size_t)w * NS * SB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)nw * NS * SB) + w * NS;
-  const int gw = blockIdx.x * nw + w, tw = gridDim.x * nw;
+  constexpr size_t XWB = ((size_t)kWinRows * kWinSlots * N1 * sizeof(TV) + 15) / 16 * 16;
+  constexpr size_t PB = ((size_t)32 * N1 * sizeof(TO) + 15) / 16 * 16;
+  const size_t pair_bytes = (size_t)NS * (SB + 2 * XWB + PB + 16);
+  unsigned char* base = smem_raw + (size_t)pr * pair_bytes;
+  unsigned char* ring = base;                                    // [NS][SB]
+  unsigned char* wins = base + (size_t)NS * SB;                  // [2][NS][XWB]
+  unsigned char* parts = wins + (size_t)2 * NS * XWB;            // [NS][PB]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(parts + (size_t)NS * PB);   // [NS]
+  TV* mywin = reinterpret_cast<TV*>(wins + (size_t)role * NS * XWB);
+  const int gp = blockIdx.x * np + pr, tp = gridDim.x * np;
   const TS* rec = (const TS*)a.rec;
+  const TV* vin = (const TV*)a.v;
   const size_t seg_elems = (size_t)SB / sizeof(TS);
-  if (lane == 0) {
+  const bool use_win = (a.nrhs == 1);
+  const int bar_id = 1 + pr;
+  if (role == 0 && lane == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int s = 0; s < NS; ++s) {
-      const int seg = gw + s * tw;
+      const int seg = gp + s * tp;
       if (seg < a.nseg) {
         mbar_expect_tx(&bars[s], SB);
         bulk_load(ring + (size_t)s * SB, rec + (size_t)seg * seg_elems, SB, &bars[s]);
       }
     }
   }
-  __syncwarp();
-  int it = 0;
-  for (;; ++it) {
-    const int seg = gw + it * tw;
+  pair_barrier(bar_id);            // barriers initialised before the partner waits
+  if (use_win) {
+    for (int s = 0; s < NS; ++s) {
+      const int seg = gp + s * tp;
+      if (seg < a.nseg) issue_window<N1, TV>(mywin + (size_t)s * (XWB / sizeof(TV)), vin, seg, lane, a);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  }
+  for (int it = 0;; ++it) {
+    const int seg = gp + it * tp;
     if (seg >= a.nseg) break;
     const int stg = it % NS;
     const unsigned par = (unsigned)((it / NS) & 1);
+    if (use_win) window_wait(NS - 1);
     const bool ok = mbar_wait_bounded(&bars[stg], par);
     if (__any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicExch(a.err, 2);
-      // let any other copy this warp issued land before the warp exits
+      asm volatile("cp.async.wait_all;" ::: "memory");
       for (int s = 1; s < NS; ++s) {
         const int it2 = it + s;
-        if (gw + it2 * tw < a.nseg) (void)mbar_wait_bounded(&bars[it2 % NS], (unsigned)((it2 / NS) & 1));
+        if (gp + it2 * tp < a.nseg) (void)mbar_wait_bounded(&bars[it2 % NS], (unsigned)((it2 / NS) & 1));
       }
-      return;
+      return;      // the partner warp times out on the same barrier and returns too
     }
-    apply_segment<N1, TS, TV, TA>(reinterpret_cast<const TS*>(ring + (size_t)stg * SB), seg, lane, a);
     __syncwarp();
-    if (lane == 0) {
-      const int nseg2 = seg + NS * tw;
-      if (nseg2 < a.nseg) {
+    const TS* st = reinterpret_cast<const TS*>(ring + (size_t)stg * SB);
+    const TV* xw = use_win ? mywin + (size_t)stg * (XWB / sizeof(TV)) : nullptr;
+    TO* part = reinterpret_cast<TO*>(parts + (size_t)stg * PB);
+    for (int r = 0; r < a.nrhs; ++r) {
+      TA acc[N1];
+      partial_segment<N1, TS, TV, TA, DIFF>(st, xw, seg, lane, role, r, a, acc);
+      if (role == 1) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) part[q * 32 + lane] = finish(acc[q]);
+      }
+      pair_barrier(bar_id);
+      if (role == 0) {
+        TO sum[N1];
+#pragma unroll
+        for (int q = 0; q < N1; ++q) sum[q] = finish(acc[q]) + part[q * 32 + lane];
+        write_face<N1, TV, TO>(sum, seg, lane, r, a);
+      }
+      if (a.nrhs > 1) pair_barrier(bar_id);   // partials consumed before the next right-hand side
+    }
+    const int nseg2 = seg + NS * tp;
+    if (role == 0) {
+      __syncwarp();
+      if (lane == 0 && nseg2 < a.nseg) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&bars[stg], SB);
         bulk_load(ring + (size_t)stg * SB, rec + (size_t)nseg2 * seg_elems, SB, &bars[stg]);
       }
     }
-    __syncwarp();
+    if (use_win) {
+      __syncwarp();
+      if (nseg2 < a.nseg) issue_window<N1, TV>(mywin + (size_t)stg * (XWB / sizeof(TV)), vin, nseg2, lane, a);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Host-side launcher for one (degree, storage, vector) combination.
-template <int N1, typename TS, typename TV, typename TA>
+template <int N1, typename TS, typename TV, typename TA, bool DIFF>
 cudaError_t apply_launch(const Context* c, const ApplyArgs& args0, cudaStream_t s) {
+  using TO = typename OutT<TA>::type;
   ApplyArgs a = args0;
-  constexpr int R = 4 * N1 * 4 * N1;
-  a.stage_bytes = (unsigned)(R * kSeg * sizeof(TS));
-  // ring budget ~220 KB per CTA: 3 stages per warp when that still leaves two
-  // or more warps, else 2, else 1; at most 8 warps
-  const size_t budget = 220 * 1024;
-  int NS = 3;
-  int nw = (int)(budget / ((size_t)NS * a.stage_bytes));
-  if (nw < 2) { NS = 2; nw = (int)(budget / ((size_t)NS * a.stage_bytes)); }
-  if (nw < 1) { NS = 1; nw = 1; }
-  if (nw > 8) nw = 8;
+  a.stage_bytes = (unsigned)(16 * N1 * N1 * kSeg * sizeof(TS));
+  int np = 0, NS = 0;
+  apply_shape((unsigned)stage_total_bytes<N1, TS, TV, TO>(), a.tune, &np, &NS);
   a.stages = NS;
-  const size_t smem = (size_t)nw * NS * a.stage_bytes + (size_t)nw * NS * sizeof(uint64_t);
-  auto kern = apply_kernel<N1, TS, TV, TA>;
+  const size_t smem = (size_t)np * NS * stage_total_bytes<N1, TS, TV, TO>();
+  auto kern = apply_kernel<N1, TS, TV, TA, DIFF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int blocks = c->num_sms;
-  const int need = (a.nseg + nw - 1) / nw;
+  const int need = (a.nseg + np - 1) / np;
   if (need < blocks) blocks = need > 0 ? need : 1;
-  kern<<<blocks, 32 * nw, smem, s>>>(a);
+  kern<<<blocks, 64 * np, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename TS, typename TV, typename TA>
+template <typename TS, typename TV, typename TA, bool DIFF>
 cudaError_t apply_dispatch(const Context* c, int n1, const ApplyArgs& a, cudaStream_t s) {
   switch (n1) {
-    case 1: return apply_launch<1, TS, TV, TA>(c, a, s);
-    case 2: return apply_launch<2, TS, TV, TA>(c, a, s);
-    case 3: return apply_launch<3, TS, TV, TA>(c, a, s);
-    case 4: return apply_launch<4, TS, TV, TA>(c, a, s);
-    case 5: return apply_launch<5, TS, TV, TA>(c, a, s);
-    case 6: return apply_launch<6, TS, TV, TA>(c, a, s);
-    case 7: return apply_launch<7, TS, TV, TA>(c, a, s);
-    case 8: return apply_launch<8, TS, TV, TA>(c, a, s);
+    case 1: return apply_launch<1, TS, TV, TA, DIFF>(c, a, s);
+    case 2: return apply_launch<2, TS, TV, TA, DIFF>(c, a, s);
+    case 3: return apply_launch<3, TS, TV, TA, DIFF>(c, a, s);
+    case 4: return apply_launch<4, TS, TV, TA, DIFF>(c, a, s);
+    case 5: return apply_launch<5, TS, TV, TA, DIFF>(c, a, s);
+    case 6: return apply_launch<6, TS, TV, TA, DIFF>(c, a, s);
+    case 7: return apply_launch<7, TS, TV, TA, DIFF>(c, a, s);
+    case 8: return apply_launch<8, TS, TV, TA, DIFF>(c, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t apply_fp64(const Context* c, int n1, const ApplyArgs& a, cudaStream_t s);
-cudaError_t apply_fp32(const Context* c, int n1, const ApplyArgs& a, cudaStream_t s);
-cudaError_t apply_bf16(const Context* c, int n1, const ApplyArgs& a, cudaStream_t s);
+// diff = true applies the blocks to x - mean(x) per element (for blocks with
+// zero row sums, i.e. the condensed operator S); false for the Schwarz blocks
+cudaError_t apply_fp64(const Context* c, int n1, bool diff, const ApplyArgs& a, cudaStream_t s);
+cudaError_t apply_fp32(const Context* c, int n1, bool diff, const ApplyArgs& a, cudaStream_t s);
+cudaError_t apply_bf16(const Context* c, int n1, bool diff, const ApplyArgs& a, cudaStream_t s);
+cudaError_t apply_x2(const Context* c, int n1, bool diff, const ApplyArgs& a, cudaStream_t s);
 
 }  // namespace hdg

@@ -9,6 +9,7 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
   const void* rec = nullptr;
   if (prec == HDG_PREC_FP64) rec = which ? (const void*)L.M64 : (const void*)L.S64;
   else if (prec == HDG_PREC_FP32) rec = which ? (const void*)L.M32 : (const void*)L.S32;
+  else if (prec == HDG_PREC_F32X2) rec = which ? (const void*)L.M2 : (const void*)L.S2;
   else rec = which ? (const void*)L.M16 : (const void*)L.S16;
   if (!rec) return cudaErrorInvalidValue;
   ApplyArgs a{};
@@ -17,9 +18,14 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
   a.nx = c->mesh.nx; a.ny = c->mesh.ny;
   a.spr = (c->mesh.nx + kSeg - 1) / kSeg;
   a.nseg = L.nseg; a.nrhs = nrhs; a.err = c->err_flag;
-  if (prec == HDG_PREC_FP64) return apply_fp64(c, L.n1, a, s);
-  if (prec == HDG_PREC_FP32) return apply_fp32(c, L.n1, a, s);
-  return apply_bf16(c, L.n1, a, s);
+  a.tune = L.tune[prec][which ? 1 : 0];
+  // the condensed blocks have zero row sums: apply the low-precision copies to
+  // x - mean(x) per element; FP64 and the Schwarz blocks use x directly
+  const bool diff = (which == 0) && (prec == HDG_PREC_FP32 || prec == HDG_PREC_BF16);
+  if (prec == HDG_PREC_FP64) return apply_fp64(c, L.n1, diff, a, s);
+  if (prec == HDG_PREC_F32X2) return apply_x2(c, L.n1, diff, a, s);
+  if (prec == HDG_PREC_FP32) return apply_fp32(c, L.n1, diff, a, s);
+  return apply_bf16(c, L.n1, diff, a, s);
 }
 
 __global__ void fill_kernel_d(double* p, size_t n) {
@@ -38,6 +44,87 @@ cudaError_t vec_fill(void* p, int prec, size_t n, cudaStream_t s) {
   if (prec == HDG_PREC_FP64) fill_kernel_d<<<blocks, 256, 0, s>>>((double*)p, n);
   else fill_kernel_f<<<blocks, 256, 0, s>>>((float*)p, n);
   return cudaGetLastError();
+}
+
+}  // namespace hdg
+
+namespace hdg {
+
+// Set-up autotuner: for every level, precision and block kind, time the
+// candidate launch shapes (warps per CTA x ring stages per warp) on a test
+// vector and keep the fastest. Shapes only change speed, never results.
+// bytes of one ring stage with its x windows and partial sums (matches
+// stage_total_bytes in the launcher)
+static unsigned stage_bytes_of(int n1, int prec) {
+  const unsigned R = 16u * n1 * n1;
+  const unsigned w = prec == HDG_PREC_FP64 || prec == HDG_PREC_F32X2 ? 8u : prec == HDG_PREC_FP32 ? 4u : 2u;
+  const unsigned wv = prec_double(prec) ? 8u : 4u;
+  const unsigned xwb = ((unsigned)kWinRows * kWinSlots * n1 * wv + 15u) / 16u * 16u;
+  const unsigned pb = (32u * n1 * wv + 15u) / 16u * 16u;
+  return R * kSeg * w + 2 * xwb + pb + 16;
+}
+
+__global__ void pattern_kernel(double* d, float* f, size_t n) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double v = 0.5 + (double)((t * 7919u) % 1009u) / 1009.0;
+    d[t] = v;
+    f[t] = (float)v;
+  }
+}
+
+cudaError_t autotune_applies(Context* c, cudaStream_t s) {
+  const size_t n = (size_t)c->ndof;
+  double *xd, *yd;
+  float *xf, *yf;
+  HDG_CUDA_TRY(cudaMallocAsync((void**)&xd, n * sizeof(double), s));
+  HDG_CUDA_TRY(cudaMallocAsync((void**)&yd, n * sizeof(double), s));
+  HDG_CUDA_TRY(cudaMallocAsync((void**)&xf, n * sizeof(float), s));
+  HDG_CUDA_TRY(cudaMallocAsync((void**)&yf, n * sizeof(float), s));
+  pattern_kernel<<<1024, 256, 0, s>>>(xd, xf, n);
+  HDG_CUDA_TRY(cudaGetLastError());
+  cudaEvent_t e0, e1;
+  HDG_CUDA_TRY(cudaEventCreate(&e0));
+  HDG_CUDA_TRY(cudaEventCreate(&e1));
+  const int precs[4] = {HDG_PREC_FP64, HDG_PREC_FP32, HDG_PREC_BF16, HDG_PREC_F32X2};
+  for (int p = 0; p <= c->k; ++p) {
+    PLevel& L = c->plev[p];
+    for (int pi = 0; pi < 4; ++pi) {
+      const int prec = precs[pi];
+      if (prec != HDG_PREC_FP64 && !c->opt.mixed) continue;
+      for (int which = 0; which < 2; ++which) {
+        if (which == 1 && p == 0) continue;       // no Schwarz blocks at p = 0
+        const unsigned sb = stage_bytes_of(L.n1, prec);
+        const int total = (int)((220u * 1024u) / sb);
+        const void* x = prec_double(prec) ? (const void*)xd : (const void*)xf;
+        void* y = prec_double(prec) ? (void*)yd : (void*)yf;
+        float best = 1e30f;
+        int best_tune = 0;
+        const int nps[5] = {1, 2, 3, 4, 6};
+        for (int wi = 0; wi < 5; ++wi)
+          for (int ns = 1; ns <= 3; ++ns) {
+            const int nw = nps[wi];                  // warp pairs
+            if (nw * ns > total) continue;
+            L.tune[prec][which] = nw * 16 + ns;
+            HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
+            HDG_CUDA_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
+            HDG_CUDA_TRY(cudaEventRecord(e1, s));
+            HDG_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            HDG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_tune = nw * 16 + ns; }
+          }
+        L.tune[prec][which] = best_tune;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HDG_CUDA_TRY(cudaFreeAsync(xd, s));
+  HDG_CUDA_TRY(cudaFreeAsync(yd, s));
+  HDG_CUDA_TRY(cudaFreeAsync(xf, s));
+  HDG_CUDA_TRY(cudaFreeAsync(yf, s));
+  return cudaSuccess;
 }
 
 }  // namespace hdg

@@ -56,6 +56,7 @@ extern "C" {
 void hdg_default_options(hdg_options* o) {
   if (!o) return;
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
+  o->autotune = 1;
 }
 
 const char* hdg_error_string(int s) {
@@ -116,12 +117,14 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     if (mixed) {
       TRY(ctx_alloc(c, (void**)&L.S32, L.rec_entries * sizeof(float)));
       TRY(ctx_alloc(c, (void**)&L.S16, L.rec_entries * sizeof(__nv_bfloat16)));
+      TRY(ctx_alloc(c, (void**)&L.S2, L.rec_entries * sizeof(float2)));
     }
     if (p >= 1) {
       TRY(ctx_alloc(c, (void**)&L.M64, L.rec_entries * sizeof(double)));
       if (mixed) {
         TRY(ctx_alloc(c, (void**)&L.M32, L.rec_entries * sizeof(float)));
         TRY(ctx_alloc(c, (void**)&L.M16, L.rec_entries * sizeof(__nv_bfloat16)));
+        TRY(ctx_alloc(c, (void**)&L.M2, L.rec_entries * sizeof(float2)));
       }
       std::vector<double> Pp;
       p_prolongation_1d(p - 1, Pp);
@@ -143,6 +146,7 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   const size_t nd = (size_t)c->ndof;
   for (double** p : {&c->cg_r, &c->cg_z, &c->cg_p, &c->cg_q, &c->cg_zold})
     TRY(ctx_alloc(c, (void**)p, nd * sizeof(double)));
+  if (c->opt.autotune) TRY(autotune_applies(c, s));
   TRY(build_hierarchy(c, s));
   for (int p = 0; p <= k; ++p) {
     TRY(cudaFreeAsync(c->plev[p].Sdense, s));
@@ -197,7 +201,7 @@ int hdg_get_info(void* ctx, hdg_info* info) {
   if (!c || !info) return HDG_ERR_INVALID_ARG;
   info->nel = c->nel; info->n_edges = c->n_edges; info->ndof = c->ndof; info->k = c->k;
   info->n_plevels = c->k + 1; info->n_hlevels = (int)c->hlev.size(); info->coarse_dim = c->coarse_dim;
-  info->device_bytes = c->bytes; info->setup_ms = c->setup_ms;
+  info->device_bytes = c->bytes; info->setup_ms = c->setup_ms; info->vcycle_kernels = c->vcycle_kernels;
   return HDG_OK;
 }
 
@@ -219,7 +223,7 @@ int hdg_get_maps(void* ctx, int32_t* elem_to_edge, int32_t* edge_to_elem, int32_
 
 static bool prec_ok(Context* c, int prec) {
   if (prec == HDG_PREC_FP64) return true;
-  if (prec == HDG_PREC_FP32 || prec == HDG_PREC_BF16) return c->opt.mixed != 0;
+  if (prec == HDG_PREC_FP32 || prec == HDG_PREC_BF16 || prec == HDG_PREC_F32X2) return c->opt.mixed != 0;
   return false;
 }
 
@@ -233,7 +237,7 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream) {
   Context* c = (Context*)ctx;
   if (!c || !x || !y || nrhs < 1 || x == y) return HDG_ERR_INVALID_ARG;
-  if (prec < 0 || prec > 2) return HDG_ERR_INVALID_ARG;
+  if (prec < 0 || prec > 3) return HDG_ERR_INVALID_ARG;
   if (!prec_ok(c, prec)) return HDG_ERR_UNSUPPORTED;
   TRY(launch_apply(c, c->k, 0, prec, x, nullptr, y, 1.0, 0.0, nrhs, (cudaStream_t)stream));
   return HDG_OK;
@@ -242,7 +246,7 @@ int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void*
 int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* stream) {
   Context* c = (Context*)ctx;
   if (!c || !r || !z || nrhs < 1) return HDG_ERR_INVALID_ARG;
-  if (prec < 0 || prec > 2) return HDG_ERR_INVALID_ARG;
+  if (prec < 0 || prec > 3) return HDG_ERR_INVALID_ARG;
   if (!prec_ok(c, prec)) return HDG_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   if (nrhs == 1) {
@@ -251,18 +255,18 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
   }
   // one right-hand side at a time through contiguous scratch
   const size_t n = (size_t)c->ndof;
-  const size_t w = prec == HDG_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t w = prec_double(prec) ? sizeof(double) : sizeof(float);
   void *ri, *zi;
   TRY(cudaMallocAsync(&ri, n * w, s));
   TRY(cudaMallocAsync(&zi, n * w, s));
   int blocks = (int)((n + 255) / 256);
   if (blocks > 2048) blocks = 2048;
   for (int q = 0; q < nrhs; ++q) {
-    if (prec == HDG_PREC_FP64) strided_copy_kernel<double><<<blocks, 256, 0, s>>>(n, (const double*)r + q, nrhs, (double*)ri, 1);
+    if (prec_double(prec)) strided_copy_kernel<double><<<blocks, 256, 0, s>>>(n, (const double*)r + q, nrhs, (double*)ri, 1);
     else strided_copy_kernel<float><<<blocks, 256, 0, s>>>(n, (const float*)r + q, nrhs, (float*)ri, 1);
     TRY(cudaGetLastError());
     TRY(vcycle(c, prec, ri, zi, s));
-    if (prec == HDG_PREC_FP64) strided_copy_kernel<double><<<blocks, 256, 0, s>>>(n, (const double*)zi, 1, (double*)z + q, nrhs);
+    if (prec_double(prec)) strided_copy_kernel<double><<<blocks, 256, 0, s>>>(n, (const double*)zi, 1, (double*)z + q, nrhs);
     else strided_copy_kernel<float><<<blocks, 256, 0, s>>>(n, (const float*)zi, 1, (float*)z + q, nrhs);
     TRY(cudaGetLastError());
   }
@@ -275,7 +279,7 @@ int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol,
               hdg_solve_info* info, void* stream) {
   Context* c = (Context*)ctx;
   if (!c || !b || !lambda || nrhs != 1 || !(rtol > 0.0) || maxit < 1 || b == lambda) return HDG_ERR_INVALID_ARG;
-  if (inner < 0 || inner > 2) return HDG_ERR_INVALID_ARG;
+  if (inner < 0 || inner > 3) return HDG_ERR_INVALID_ARG;
   if (!prec_ok(c, inner)) return HDG_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const auto t0 = std::chrono::steady_clock::now();

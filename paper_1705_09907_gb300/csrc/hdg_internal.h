@@ -54,6 +54,7 @@ struct PLevel {
   size_t rec_entries = 0;                   // nseg * R * 16
   double* S64 = nullptr; float* S32 = nullptr; __nv_bfloat16* S16 = nullptr;
   double* M64 = nullptr; float* M32 = nullptr; __nv_bfloat16* M16 = nullptr;
+  float2* S2 = nullptr; float2* M2 = nullptr;   // double-float (hi, lo) copies
   double* Sdense = nullptr;                 // [nel][m][m] FP64 element blocks
   double* Pp = nullptr;                     // prolongation from p-1 [(p+1) x p] (device)
   // V-cycle work vectors, [ndof] each, per precision (d = double, f = float)
@@ -62,6 +63,7 @@ struct PLevel {
   // p = 0 only: inverse diagonal of the assembled operator (Chebyshev/Jacobi)
   double* dinv64 = nullptr; float* dinv32 = nullptr;
   double lmax = 0.0;
+  int tune[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};   // apply launch shape per (prec, S/M)
 };
 
 // One Q1 level (interior vertices (nx-1) x (ny-1)); 9-point stencils stored as
@@ -110,9 +112,13 @@ struct Context {
   double setup_ms = 0.0;
   std::vector<void*> allocs;
   // CUDA graphs of the V-cycle body, per precision, keyed by stream
-  cudaGraphExec_t vc_graph[3] = {nullptr, nullptr, nullptr};
-  cudaStream_t vc_graph_stream[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t vc_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t vc_graph_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+  int vcycle_kernels = 0;                   // kernel nodes of the captured V-cycle
 };
+
+// vectors of a V-cycle / apply in this precision are double (else float)
+inline bool prec_double(int prec) { return prec == HDG_PREC_FP64 || prec == HDG_PREC_F32X2; }
 
 // allocation helper: records the pointer for hdg_destroy
 cudaError_t ctx_alloc(Context* c, void** p, size_t bytes);
@@ -124,6 +130,7 @@ cudaError_t launch_galerkin_coarsen(Context* c, int p_fine, cudaStream_t s);
 cudaError_t launch_build_records(Context* c, int p, cudaStream_t s);
 cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s);
 cudaError_t launch_p0_diag(Context* c, cudaStream_t s);
+cudaError_t autotune_applies(Context* c, cudaStream_t s);
 
 // Trace-operator apply on the record layout of level p:
 //   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)

@@ -444,9 +444,9 @@ static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x
   const bool p0 = (H == nullptr);
   PLevel& L0 = c->plev[0];
   const size_t n = p0 ? (size_t)c->n_edges : (size_t)H->nv;
-  const T* dinv = p0 ? (const T*)(prec == HDG_PREC_FP64 ? (const void*)L0.dinv64 : (const void*)L0.dinv32)
-                     : (const T*)(prec == HDG_PREC_FP64 ? (const void*)H->dinv64 : (const void*)H->dinv32);
-  const T* st = p0 ? nullptr : (const T*)(prec == HDG_PREC_FP64 ? (const void*)H->st64 : (const void*)H->st32);
+  const T* dinv = p0 ? (const T*)(prec_double(prec) ? (const void*)L0.dinv64 : (const void*)L0.dinv32)
+                     : (const T*)(prec_double(prec) ? (const void*)H->dinv64 : (const void*)H->dinv32);
+  const T* st = p0 ? nullptr : (const T*)(prec_double(prec) ? (const void*)H->st64 : (const void*)H->st32);
   const ChebCoef cc = cheb_coefficients(p0 ? L0.lmax : H->lmax, c->opt.cheb_degree);
   auto A = [&](const T* v, const T* cv, T* y, double al, double be) -> cudaError_t {
     if (p0) return p0_apply(c, prec, v, cv, y, al, be, s);
@@ -490,22 +490,22 @@ static cudaError_t hmg(Context* c, int prec, int l, const T* r, T* x, cudaStream
   PLevel& L0 = c->plev[0];
   T *t, *d;
   if (p0) {
-    t = (T*)(prec == HDG_PREC_FP64 ? (void*)L0.t64 : (void*)L0.t32);
-    d = (T*)(prec == HDG_PREC_FP64 ? (void*)L0.d64 : (void*)L0.d32);
+    t = (T*)(prec_double(prec) ? (void*)L0.t64 : (void*)L0.t32);
+    d = (T*)(prec_double(prec) ? (void*)L0.d64 : (void*)L0.d32);
   } else {
-    t = (T*)(prec == HDG_PREC_FP64 ? (void*)H->t64 : (void*)H->t32);
-    d = (T*)(prec == HDG_PREC_FP64 ? (void*)H->d64 : (void*)H->d32);
+    t = (T*)(prec_double(prec) ? (void*)H->t64 : (void*)H->t32);
+    d = (T*)(prec_double(prec) ? (void*)H->d64 : (void*)H->d32);
   }
   HDG_CUDA_TRY(cheb_smooth<T>(c, prec, H, r, x, t, d, true, c->opt.nu1, s));
   // residual and restriction to the next (coarser) Q1 level
   HLevel& Hc = c->hlev[l + 1];
-  T* rc = (T*)(prec == HDG_PREC_FP64 ? (void*)Hc.r64 : (void*)Hc.r32);
-  T* xc = (T*)(prec == HDG_PREC_FP64 ? (void*)Hc.x64 : (void*)Hc.x32);
+  T* rc = (T*)(prec_double(prec) ? (void*)Hc.r64 : (void*)Hc.r32);
+  T* xc = (T*)(prec_double(prec) ? (void*)Hc.x64 : (void*)Hc.x32);
   if (p0) {
     HDG_CUDA_TRY(p0_apply(c, prec, x, r, t, -1.0, 1.0, s));
     restrict_J_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, t, rc);
   } else {
-    const T* st = (const T*)(prec == HDG_PREC_FP64 ? (const void*)H->st64 : (const void*)H->st32);
+    const T* st = (const T*)(prec_double(prec) ? (const void*)H->st64 : (const void*)H->st32);
     HDG_CUDA_TRY(q_apply<T>(*H, st, x, r, t, -1.0, 1.0, s));
     restrict_q_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(Hc.nx, Hc.ny, t, rc);
   }
@@ -522,7 +522,7 @@ template <typename T>
 static cudaError_t pmg(Context* c, int prec, int p, const T* r, T* x, cudaStream_t s) {
   PLevel& L = c->plev[p];
   PLevel& Lc = c->plev[p - 1];
-  T* t = (T*)(prec == HDG_PREC_FP64 ? (void*)L.t64 : (void*)L.t32);
+  T* t = (T*)(prec_double(prec) ? (void*)L.t64 : (void*)L.t32);
   const int nu1 = c->opt.nu1, nu2 = c->opt.nu2;
   // pre-smoothing: x = M r, then x += M (r - A x)
   HDG_CUDA_TRY(launch_apply(c, p, 1, prec, r, nullptr, x, 1.0, 0.0, 1, s));
@@ -532,8 +532,8 @@ static cudaError_t pmg(Context* c, int prec, int p, const T* r, T* x, cudaStream
   }
   // restricted residual
   HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
-  T* rc = (T*)(prec == HDG_PREC_FP64 ? (void*)Lc.r64 : (void*)Lc.r32);
-  T* xc = (T*)(prec == HDG_PREC_FP64 ? (void*)Lc.x64 : (void*)Lc.x32);
+  T* rc = (T*)(prec_double(prec) ? (void*)Lc.r64 : (void*)Lc.r32);
+  T* xc = (T*)(prec_double(prec) ? (void*)Lc.x64 : (void*)Lc.x32);
   restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1), 256, 0, s>>>(c->n_edges, Lc.n1, L.Pp, t, rc);
   HDG_CUDA_TRY(cudaGetLastError());
   if (p - 1 == 0) HDG_CUDA_TRY(hmg<T>(c, prec, -1, rc, xc, s));
@@ -551,14 +551,14 @@ static cudaError_t pmg(Context* c, int prec, int p, const T* r, T* x, cudaStream
 template <typename T>
 static cudaError_t vcycle_body(Context* c, int prec, cudaStream_t s) {
   PLevel& L = c->plev[c->k];
-  const T* r = (const T*)(prec == HDG_PREC_FP64 ? (void*)L.r64 : (void*)L.r32);
-  T* x = (T*)(prec == HDG_PREC_FP64 ? (void*)L.x64 : (void*)L.x32);
+  const T* r = (const T*)(prec_double(prec) ? (void*)L.r64 : (void*)L.r32);
+  T* x = (T*)(prec_double(prec) ? (void*)L.x64 : (void*)L.x32);
   if (c->k == 0) return hmg<T>(c, prec, -1, r, x, s);
   return pmg<T>(c, prec, c->k, r, x, s);
 }
 
 static cudaError_t vcycle_body_any(Context* c, int prec, cudaStream_t s) {
-  if (prec == HDG_PREC_FP64) return vcycle_body<double>(c, prec, s);
+  if (prec_double(prec)) return vcycle_body<double>(c, prec, s);
   return vcycle_body<float>(c, prec, s);
 }
 
@@ -567,7 +567,7 @@ cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_do
   PLevel& L = c->plev[c->k];
   const size_t n = (size_t)c->ndof;
   const int g = grid_for(n);
-  if (prec == HDG_PREC_FP64) {
+  if (prec_double(prec)) {
     HDG_CUDA_TRY(cudaMemcpyAsync(L.r64, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else if (r_double) {
     copy_convert_kernel<double, float><<<g, 256, 0, s>>>(n, (const double*)r, L.r32);
@@ -593,6 +593,17 @@ cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_do
       HDG_CUDA_TRY(eb);
       HDG_CUDA_TRY(ee);
       HDG_CUDA_TRY(cudaGraphInstantiate(&c->vc_graph[gi], g0, 0));
+      size_t nn = 0;
+      HDG_CUDA_TRY(cudaGraphGetNodes(g0, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      HDG_CUDA_TRY(cudaGraphGetNodes(g0, nodes.data(), &nn));
+      int nk = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        HDG_CUDA_TRY(cudaGraphNodeGetType(nd, &ty));
+        if (ty == cudaGraphNodeTypeKernel) ++nk;
+      }
+      c->vcycle_kernels = nk;
       cudaGraphDestroy(g0);
       c->vc_graph_stream[gi] = s;
     }
@@ -600,7 +611,7 @@ cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_do
   } else {
     HDG_CUDA_TRY(vcycle_body_any(c, prec, s));
   }
-  if (prec == HDG_PREC_FP64) {
+  if (prec_double(prec)) {
     HDG_CUDA_TRY(cudaMemcpyAsync(z, L.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else if (r_double) {
     copy_convert_kernel<float, double><<<g, 256, 0, s>>>(n, L.x32, (double*)z);
@@ -773,6 +784,9 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
   double* sc = c->scal;
   double* h = c->h_scal;
   const bool flexible = inner != HDG_PREC_FP64;
+  // plain FP64 mode applies FP64 blocks everywhere; the other modes compute the
+  // outer residual with the double-float blocks (FP64 vectors, ~48-bit products)
+  const int outer = (inner == HDG_PREC_FP64) ? HDG_PREC_FP64 : HDG_PREC_F32X2;
 #define CK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return HDG_ERR_CUDA; } while (0)
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -792,7 +806,7 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
   double rel = 1.0;
   int status = HDG_ERR_NOT_CONVERGED;
   for (it = 1; it <= maxit; ++it) {
-    CK(launch_apply(c, c->k, 0, HDG_PREC_FP64, p, nullptr, q, 1.0, 0.0, 1, s));
+    CK(launch_apply(c, c->k, 0, outer, p, nullptr, q, 1.0, 0.0, 1, s));
     CK(dots<double>(c, n, p, q, nullptr, nullptr, nullptr, nullptr, sc + 1, s));
     CK(cudaMemcpyAsync(h + 1, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     cg_xr_kernel<<<g, 256, 0, s>>>(n, sc, p, q, x, r);

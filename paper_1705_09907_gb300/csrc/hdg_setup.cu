@@ -180,6 +180,15 @@ __global__ void records_kernel(int nx, int ny, int n1, const double* __restrict_
 
 template <typename T>
 __global__ void convert_kernel(const double* __restrict__ in, T* __restrict__ out, long n);
+// double -> (hi, lo) float pair: hi = fl(v), lo = fl(v - hi)
+template <>
+__global__ void convert_kernel<float2>(const double* __restrict__ in, float2* __restrict__ out, long n) {
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x) {
+    const double v = in[t];
+    const float hi = (float)v;
+    out[t] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
 template <>
 __global__ void convert_kernel<float>(const double* __restrict__ in, float* __restrict__ out, long n) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
@@ -193,7 +202,7 @@ __global__ void convert_kernel<__nv_bfloat16>(const double* __restrict__ in, __n
 }
 
 static cudaError_t write_records(Context* c, int p, const double* dense, double* r64, float* r32,
-                                 __nv_bfloat16* r16, cudaStream_t s) {
+                                 __nv_bfloat16* r16, float2* r2, cudaStream_t s) {
   PLevel& L = c->plev[p];
   const long total = (long)L.rec_entries;
   int blocks = (int)((total + 255) / 256);
@@ -202,12 +211,13 @@ static cudaError_t write_records(Context* c, int p, const double* dense, double*
   HDG_CUDA_TRY(cudaGetLastError());
   if (r32) { convert_kernel<float><<<blocks, 256, 0, s>>>(r64, r32, total); HDG_CUDA_TRY(cudaGetLastError()); }
   if (r16) { convert_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(r64, r16, total); HDG_CUDA_TRY(cudaGetLastError()); }
+  if (r2) { convert_kernel<float2><<<blocks, 256, 0, s>>>(r64, r2, total); HDG_CUDA_TRY(cudaGetLastError()); }
   return cudaSuccess;
 }
 
 cudaError_t launch_build_records(Context* c, int p, cudaStream_t s) {
   PLevel& L = c->plev[p];
-  return write_records(c, p, L.Sdense, L.S64, L.S32, L.S16, s);
+  return write_records(c, p, L.Sdense, L.S64, L.S32, L.S16, L.S2, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,7 +310,7 @@ cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s) {
   if (blocks > c->num_sms * 16) blocks = c->num_sms * 16;
   asm_kernel<<<blocks, 32 * wpb, smem, s>>>(c->mesh.nx, c->mesh.ny, L.n1, L.Sdense, Md, c->err_flag);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = write_records(c, p, Md, L.M64, L.M32, L.M16, s);
+  if (e == cudaSuccess) e = write_records(c, p, Md, L.M64, L.M32, L.M16, L.M2, s);
   cudaError_t e2 = cudaFreeAsync(Md, s);
   return e != cudaSuccess ? e : e2;
 }

@@ -23,8 +23,8 @@ HDG_ERR_BREAKDOWN = 5
 HDG_ERR_TIMEOUT = 6
 HDG_ERR_UNSUPPORTED = 7
 
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
-VEC_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.float32}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "f32x2": 3}
+VEC_DTYPE = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.float32, "f32x2": torch.float64}
 
 
 class hdg_mesh(ctypes.Structure):
@@ -34,13 +34,14 @@ class hdg_mesh(ctypes.Structure):
 
 class hdg_options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_n", ctypes.c_int), ("tau", ctypes.c_double),
-                ("cheb_degree", ctypes.c_int), ("mixed", ctypes.c_int), ("use_graphs", ctypes.c_int)]
+                ("cheb_degree", ctypes.c_int), ("mixed", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class hdg_info(ctypes.Structure):
     _fields_ = [("nel", ctypes.c_int), ("n_edges", ctypes.c_int), ("ndof", ctypes.c_int), ("k", ctypes.c_int),
                 ("n_plevels", ctypes.c_int), ("n_hlevels", ctypes.c_int), ("coarse_dim", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double)]
+                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double), ("vcycle_kernels", ctypes.c_int)]
 
 
 class hdg_solve_info(ctypes.Structure):
@@ -152,6 +153,11 @@ class HDGSolver:
         _check(_lib.hdg_get_info(self.ctx, ctypes.byref(inf)), "hdg_get_info")
         self.info = {f: getattr(inf, f) for f, _ in hdg_info._fields_}
         self.nel, self.n_edges, self.ndof = inf.nel, inf.n_edges, inf.ndof
+
+    def get_info(self):
+        inf = hdg_info()
+        _check(_lib.hdg_get_info(self.ctx, ctypes.byref(inf)), "hdg_get_info")
+        return {f: getattr(inf, f) for f, _ in hdg_info._fields_}
 
     def close(self):
         if getattr(self, "ctx", None):
