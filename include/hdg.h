@@ -204,6 +204,24 @@ int hdg_adjoint_grad(void* ctx, const double* f_q, const double* lambda, const d
                      double rtol, int maxit, double* dJ_dlogk, double* dJ_df, double* J,
                      double* psi, void* stream);
 
+/*
+ * hdg_condense_rhs without any device allocation, for callers that cannot
+ * allocate device memory when they need the right-hand side (code running
+ * where an allocation would synchronise the device or is not permitted).
+ * The paper has no counterpart; this is a library-interface addition.
+ * Same arguments, layout and result as hdg_condense_rhs. Its per-element
+ * scratch is a fixed array of 2^19 doubles (4 MiB) inside the library, held
+ * by every GPU that loads the library until the process exits; contexts
+ * with nel * 4(k+1) > 2^19 are rejected with HDG_ERR_INVALID_ARG. The first
+ * call on a device looks up that array's device address (a host-side step);
+ * make that first call before any stream capture. All calls share the array:
+ * calls that overlap on the GPU (different streams, no ordering between them)
+ * race on it and must not be issued. The array needs no clearing: every call
+ * overwrites the entries it reads. Allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine).
+ */
+int hdg_condense_rhs_noalloc(void* ctx, const double* f_q, double* b, int nrhs, void* stream);
+
 /* Release everything the context owns. NULL is ignored. */
 void hdg_destroy(void* ctx);
 

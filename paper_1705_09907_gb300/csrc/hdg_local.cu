@@ -112,6 +112,22 @@ cudaError_t launch_condense(Context* c, const double* f_q, double* b, int nrhs, 
   return cudaSuccess;
 }
 
+// Same as launch_condense with the per-element partial results in `scratch`
+// ([nel][m] doubles, caller-provided).
+cudaError_t launch_condense_into(Context* c, const double* f_q, double* b, int nrhs, double* scratch,
+                                 cudaStream_t s) {
+  LocalArgs a = local_args(c);
+  for (int r = 0; r < nrhs; ++r) {
+    condense_elem_kernel<<<grid_of(c->nel, c->num_sms * 16), 128, 0, s>>>(a, f_q + (size_t)r * c->nel * a.nf,
+                                                                         scratch);
+    HDG_CUDA_TRY(cudaGetLastError());
+    gather_edges_kernel<<<grid_of((size_t)c->n_edges * c->ref.n1, c->num_sms * 32), 128, 0, s>>>(
+        c->n_edges, c->ref.n1, c->edge_elem, c->edge_face, scratch, b, nrhs, r);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
 // Local solution (U, Q) of element e for trace values lamK [m] and load F
 // (F may be null for f = 0). U [n], Q [2n].
 __device__ void local_solution(const LocalArgs& a, int e, const double* lamK, const double* F, double* U,

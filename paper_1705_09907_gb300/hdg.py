@@ -72,6 +72,7 @@ def _load():
         "hdg_solve": (i, [vp, vp, vp, i, d, i, i, ctypes.POINTER(hdg_solve_info), vp]),
         "hdg_recover_local": (i, [vp, vp, vp, vp, vp, vp]),
         "hdg_adjoint_grad": (i, [vp, vp, vp, vp, d, i, vp, vp, vp, vp, vp]),
+        "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
         "hdg_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -95,6 +96,7 @@ hdg_gmg_vcycle = _lib.hdg_gmg_vcycle
 hdg_solve = _lib.hdg_solve
 hdg_recover_local = _lib.hdg_recover_local
 hdg_adjoint_grad = _lib.hdg_adjoint_grad
+hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
 hdg_destroy = _lib.hdg_destroy
 
 
