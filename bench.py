@@ -283,10 +283,13 @@ def run_ours(args):
     tflops = fp["flops"] / (apply_ms["fp64"] * 1e-3) / 1e12
     # FP64: 0.25 flop/byte needs more FP64 issue than the GPU has (1.25 TFLOP/s
     # nominal), so the FP64 apply is bound by the FP64 pipe, not by HBM.
+    # DRAM read+write of one FP64 level-k apply: ncu capture at 256 x 256 (218.8 MB,
+    # profiles/apply_k4_256_dram.md) scaled by the element count to 512 x 512
+    traffic = 218.775e6 * (nel / 65536.0) if (N, k) == (512, 4) else None
     roof = {"kernel": "apply_kernel<5,double,double,double> (FP64 trace apply, level k)",
             "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": tflops / 1.25,
             "peak_source": "nominal FP64 rate of GB300 (recipe table); HBM fraction in trace_apply",
-            "traffic": None}
+            "traffic": traffic, "algorithmic_bytes": fp["algorithmic_bytes"]}
     cpu = None
     if not args.no_cpu_baseline:
         try:

@@ -415,7 +415,11 @@ cudaError_t apply_launch(const Context* c, const ApplyArgs& args0, cudaStream_t 
   a.stages = NS;
   const size_t smem = (size_t)np * NS * stage_total_bytes<N1, TS, TV, TO>();
   auto kern = apply_kernel<N1, TS, TV, TA, DIFF>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one kernel serves launches with different ring sizes (S and Schwarz blocks,
+  // tuned shapes), some of them replayed later from a captured graph: allow the
+  // device's whole opt-in shared memory once instead of the size of this launch
+  if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
   if (e != cudaSuccess) return e;
   int blocks = c->num_sms;
   const int need = (a.nseg + np - 1) / np;

@@ -77,6 +77,7 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   const int k = c->k;
   TRY(cudaGetDevice(&c->dev));
   TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev));
+  TRY(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
   build_ref_tables(k, c->hx, c->hy, c->ref);
   // upload the finest tables in one buffer
   std::vector<double> pack;

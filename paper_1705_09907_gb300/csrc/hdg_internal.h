@@ -71,6 +71,7 @@ struct PLevel {
 struct HLevel {
   int nx = 0, ny = 0, nv = 0;
   double* st64 = nullptr; float* st32 = nullptr;
+  float* rsum32 = nullptr;                  // row sums (difference-form float apply)
   double* dinv64 = nullptr; float* dinv32 = nullptr;
   double lmax = 0.0;
   double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
@@ -82,6 +83,7 @@ struct Context {
   hdg_options opt{};
   int k = 0, nel = 0, n_edges = 0, ndof = 0;
   int dev = 0, num_sms = 0;
+  int smem_optin = 0;                       // max dynamic shared memory per block (opt-in)
   double hx = 0, hy = 0;
   double* kappa = nullptr;                  // [nel] (copy)
   int32_t* e2e = nullptr;                   // [nel][4]

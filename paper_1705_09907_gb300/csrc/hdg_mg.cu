@@ -192,24 +192,44 @@ __global__ void prolong_J_add_kernel(int nx, int ny, const T* __restrict__ xq, T
 
 // ---------------------------------------------------------------------------
 // Q1 stencil levels. Stencil [9][nv], offset o = (dy+1)*3 + (dx+1).
+// y = beta c + alpha A x. With `rsum` (row sums of A, low-precision levels)
+// the product is taken in difference form, sum_{o != centre} a_o (x_{v+o} - x_v)
+// + rsum_v x_v: exact in exact arithmetic, and the rounded stencil then sees the
+// variation of x around v rather than its (smooth, large) value.
 template <typename T>
 __global__ void stencil_apply_kernel(int nx, int ny, const T* __restrict__ st, const T* __restrict__ x,
-                                     const T* __restrict__ c, T* __restrict__ y, T alpha, T beta) {
+                                     const T* __restrict__ c, T* __restrict__ y, T alpha, T beta,
+                                     const T* __restrict__ rsum) {
   const int nvx = nx - 1, nvy = ny - 1, nvert = nvx * nvy;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
     const int I = t % nvx, J = t / nvx;
-    T s = 0;
+    const T xc = x[t];
+    T s = rsum ? rsum[t] * xc : T(0);
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const int I2 = I + dx, J2 = J + dy;
         if (I2 < 0 || J2 < 0 || I2 >= nvx || J2 >= nvy) continue;
-        s += st[((dy + 1) * 3 + dx + 1) * (size_t)nvert + t] * x[I2 + nvx * J2];
+        const T a = st[((dy + 1) * 3 + dx + 1) * (size_t)nvert + t];
+        if (rsum) {
+          if (dx != 0 || dy != 0) s += a * (x[I2 + nvx * J2] - xc);
+        } else {
+          s += a * x[I2 + nvx * J2];
+        }
       }
     T v = alpha * s;
     if (c) v += beta * c[t];
     y[t] = v;
+  }
+}
+
+// row sums of a stencil level (FP64), stored in float for the difference form
+__global__ void stencil_rowsum_kernel(int nvert, const double* __restrict__ st, float* __restrict__ rs) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int o = 0; o < 9; ++o) s += st[o * (size_t)nvert + t];
+    rs[t] = (float)s;
   }
 }
 
@@ -414,7 +434,9 @@ static cudaError_t p0_apply(Context* c, int prec, const void* v, const void* cv,
 template <typename T>
 static cudaError_t q_apply(HLevel& H, const T* st, const T* x, const T* cv, T* y, double al, double be,
                            cudaStream_t s) {
-  stencil_apply_kernel<T><<<grid_for(H.nv), 256, 0, s>>>(H.nx, H.ny, st, x, cv, y, (T)al, (T)be);
+  // float levels use the difference form (rowsum32), double levels the plain one
+  const T* rs = (sizeof(T) == 4) ? (const T*)(const void*)H.rsum32 : nullptr;
+  stencil_apply_kernel<T><<<grid_for(H.nv), 256, 0, s>>>(H.nx, H.ny, st, x, cv, y, (T)al, (T)be, rs);
   return cudaGetLastError();
 }
 
@@ -502,7 +524,7 @@ static cudaError_t hmg(Context* c, int prec, int l, const T* r, T* x, cudaStream
   T* rc = (T*)(prec_double(prec) ? (void*)Hc.r64 : (void*)Hc.r32);
   T* xc = (T*)(prec_double(prec) ? (void*)Hc.x64 : (void*)Hc.x32);
   if (p0) {
-    HDG_CUDA_TRY(p0_apply(c, prec, x, r, t, -1.0, 1.0, s));
+    HDG_CUDA_TRY(p0_apply(c, prec == HDG_PREC_BF16 ? HDG_PREC_FP32 : prec, x, r, t, -1.0, 1.0, s));
     restrict_J_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, t, rc);
   } else {
     const T* st = (const T*)(prec_double(prec) ? (const void*)H->st64 : (const void*)H->st32);
@@ -530,8 +552,11 @@ static cudaError_t pmg(Context* c, int prec, int p, const T* r, T* x, cudaStream
     HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
     HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, 1, s));
   }
-  // restricted residual
-  HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
+  // restricted residual; a BF16 cycle takes it with the FP32 blocks: its smooth
+  // part drives the coarse correction, and BF16 rounding (2^-9) of the blocks
+  // would swamp it on fine meshes
+  const int rprec = prec == HDG_PREC_BF16 ? HDG_PREC_FP32 : prec;
+  HDG_CUDA_TRY(launch_apply(c, p, 0, rprec, x, r, t, -1.0, 1.0, 1, s));
   T* rc = (T*)(prec_double(prec) ? (void*)Lc.r64 : (void*)Lc.r32);
   T* xc = (T*)(prec_double(prec) ? (void*)Lc.x64 : (void*)Lc.x32);
   restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1), 256, 0, s>>>(c->n_edges, Lc.n1, L.Pp, t, rc);
@@ -732,6 +757,9 @@ cudaError_t build_hierarchy(Context* c, cudaStream_t s) {
     HDG_CUDA_TRY(cudaGetLastError());
     if (mixed) {
       copy_convert_kernel<double, float><<<grid_for(9 * n), 256, 0, s>>>(9 * n, H.st64, H.st32);
+      HDG_CUDA_TRY(cudaGetLastError());
+      HDG_CUDA_TRY(ctx_alloc(c, (void**)&H.rsum32, n * sizeof(float)));
+      stencil_rowsum_kernel<<<grid_for(n), 256, 0, s>>>((int)n, H.st64, H.rsum32);
       HDG_CUDA_TRY(cudaGetLastError());
     }
   }

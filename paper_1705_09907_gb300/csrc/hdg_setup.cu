@@ -103,7 +103,7 @@ cudaError_t launch_local_setup(Context* c, cudaStream_t s) {
   if (wpb < 1) wpb = 1;
   if (wpb > 8) wpb = 8;
   const size_t smem = per_warp * wpb;
-  HDG_CUDA_TRY(cudaFuncSetAttribute(local_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HDG_CUDA_TRY(cudaFuncSetAttribute(local_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin));
   LocalTables tb{c->d_ref + c->off_P, c->d_ref + c->off_Mb, c->d_ref + c->off_Z,
                  c->d_ref + c->off_Eb, c->d_ref + c->off_Y, c->d_ref + c->off_Ml};
   int blocks = (c->nel + wpb - 1) / wpb;
@@ -303,7 +303,7 @@ cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s) {
   if (wpb < 1) wpb = 1;
   if (wpb > 8) wpb = 8;
   const size_t smem = per_warp * wpb;
-  HDG_CUDA_TRY(cudaFuncSetAttribute(asm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  HDG_CUDA_TRY(cudaFuncSetAttribute(asm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin));
   double* Md = nullptr;
   HDG_CUDA_TRY(cudaMallocAsync((void**)&Md, (size_t)c->nel * L.m * L.m * sizeof(double), s));
   int blocks = (c->nel + wpb - 1) / wpb;
