@@ -154,6 +154,19 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
 
 /*
+ * Batched apply for a uniform coefficient (every S_K equal): Y = A X for nrhs
+ * right-hand sides on the 5th-generation tensor cores. Each owned face computes
+ * y_e = [S[F rows], S[F' rows]] [x_K; x_nb] (Alg. 3 with a shared block) as one
+ * MMA row block: two faces x 64 right-hand sides (M = 128) by the 2*4(k+1)
+ * gathered dofs (K) by k+1 outputs (N, padded to 16), FP32 accumulation in
+ * tensor memory. X: device BF16 [ndof][nrhs] (right-hand side fastest), Y:
+ * device FP32 [ndof][nrhs]; nrhs a multiple of 64; both 16-byte aligned; boundary
+ * entries of X are ignored and Y is 0 there. Errors: INVALID_ARG (nrhs, alignment,
+ * null), UNSUPPORTED (the context's kappa is not uniform).
+ */
+int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void* stream);
+
+/*
  * One nested V-cycle z = V r (Algs. 2 then 1, zero initial guess): p-levels
  * k..1 with nu1/nu2 weighted additive Schwarz steps (Sec. 6.4.2), restriction
  * R = P^T and prolongation P per edge (Eqs. eq_mg_pro, eq_mg_res), the p = 0

@@ -134,6 +134,17 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     }
   }
   TRY(launch_local_setup(c, s));
+  {
+    // a uniform coefficient makes every element block equal: keep that block for
+    // the tensor-core batched apply
+    std::vector<double> hk(c->nel);
+    TRY(cudaMemcpyAsync(hk.data(), kappa, (size_t)c->nel * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    bool uni = true;
+    for (int e = 1; e < c->nel && uni; ++e) uni = (hk[e] == hk[0]);
+    c->uniform_kappa = uni;
+    if (uni) TRY(prepare_shared_blocks(c, s));
+  }
   for (int p = k; p >= 1; --p) TRY(launch_galerkin_coarsen(c, p, s));
   for (int p = k; p >= 0; --p) {
     TRY(launch_build_records(c, p, s));
@@ -273,6 +284,15 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
   }
   TRY(cudaFreeAsync(ri, s));
   TRY(cudaFreeAsync(zi, s));
+  return HDG_OK;
+}
+
+int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void* stream) {
+  Context* c = (Context*)ctx;
+  if (!c || !X || !Y || nrhs < 64 || nrhs % 64 != 0) return HDG_ERR_INVALID_ARG;
+  if (((uintptr_t)X % 16) != 0 || ((uintptr_t)Y % 16) != 0) return HDG_ERR_INVALID_ARG;
+  if (!c->uniform_kappa || !c->shared_B) return HDG_ERR_UNSUPPORTED;
+  TRY(launch_batched_apply(c, X, Y, nrhs, (cudaStream_t)stream));
   return HDG_OK;
 }
 

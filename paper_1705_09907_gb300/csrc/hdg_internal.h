@@ -117,6 +117,9 @@ struct Context {
   cudaGraphExec_t vc_graph[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t vc_graph_stream[4] = {nullptr, nullptr, nullptr, nullptr};
   int vcycle_kernels = 0;                   // kernel nodes of the captured V-cycle
+  // uniform coefficient: the shared block for the tensor-core batched apply
+  bool uniform_kappa = false;
+  __nv_bfloat16* shared_B = nullptr;        // [2][16][Kp] BF16
 };
 
 // vectors of a V-cycle / apply in this precision are double (else float)
@@ -133,6 +136,9 @@ cudaError_t launch_build_records(Context* c, int p, cudaStream_t s);
 cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s);
 cudaError_t launch_p0_diag(Context* c, cudaStream_t s);
 cudaError_t autotune_applies(Context* c, cudaStream_t s);
+// tensor-core batched apply of the shared block (hdg_batched.cu)
+cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s);
+cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s);
 
 // Trace-operator apply on the record layout of level p:
 //   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)

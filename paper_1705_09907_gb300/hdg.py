@@ -73,6 +73,7 @@ def _load():
         "hdg_recover_local": (i, [vp, vp, vp, vp, vp, vp]),
         "hdg_adjoint_grad": (i, [vp, vp, vp, vp, d, i, vp, vp, vp, vp, vp]),
         "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
+        "hdg_apply_shared_batched": (i, [vp, vp, vp, i, vp]),
         "hdg_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -97,6 +98,7 @@ hdg_solve = _lib.hdg_solve
 hdg_recover_local = _lib.hdg_recover_local
 hdg_adjoint_grad = _lib.hdg_adjoint_grad
 hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
+hdg_apply_shared_batched = _lib.hdg_apply_shared_batched
 hdg_destroy = _lib.hdg_destroy
 
 
@@ -192,6 +194,16 @@ class HDGSolver:
         _check(_lib.hdg_apply_trace(self.ctx, _ptr(x, VEC_DTYPE[prec]), _ptr(y, VEC_DTYPE[prec]), nrhs, PREC[prec],
                                     _stream()), "hdg_apply_trace")
         return y
+
+    def apply_shared_batched(self, X, out=None):
+        """Y = A X for a uniform coefficient on the tensor cores: X BF16 [ndof, nrhs]
+        (nrhs a multiple of 64), Y FP32 [ndof, nrhs]."""
+        if X.dtype != torch.bfloat16 or X.dim() != 2:
+            raise ValueError("X must be a 2-D bfloat16 CUDA tensor [ndof, nrhs]")
+        Y = torch.empty(X.shape, dtype=torch.float32, device="cuda") if out is None else out
+        _check(_lib.hdg_apply_shared_batched(self.ctx, _ptr(X), _ptr(Y, torch.float32), X.shape[1], _stream()),
+               "hdg_apply_shared_batched")
+        return Y
 
     def vcycle(self, r, prec="fp64", out=None):
         nrhs = 1 if r.dim() == 1 else r.shape[1]
