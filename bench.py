@@ -204,6 +204,14 @@ def run_ours(args):
             for _ in range(3):
                 solver.apply(xx, p_)
             torch.cuda.nvtx.range_pop()
+        # tensor-core batched apply, same mesh with kappa = 1, 64 right-hand sides
+        sbs = hdg.HDGSolver(N, N, k, torch.ones(N * N, dtype=torch.float64, device="cuda"), mixed=0, autotune=0)
+        X4 = torch.randn((sbs.ndof, 64), device="cuda").to(torch.bfloat16)
+        torch.cuda.nvtx.range_push("apply_batched")
+        for _ in range(3):
+            sbs.apply_shared_batched(X4)
+        torch.cuda.nvtx.range_pop()
+        sbs.close()
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": True, "iterations": last["info"]["iterations"],
                           "relres": last["info"]["relres"], "vcycle_kernels": solver.get_info()["vcycle_kernels"]}))
@@ -239,6 +247,50 @@ def run_ours(args):
         err = float(torch.linalg.norm(lam - lam64) / torch.linalg.norm(lam64))
         mixed[inner] = {"ms_per_solve": ms, "iterations": inf["iterations"], "relres": inf["relres"],
                         "rel_diff_vs_fp64_solution": err}
+    # tensor-core batched apply: uniform kappa, 256 x 256, k = 5, 64 right-hand sides
+    # (Fourier sources, seed 3); BF16 inputs, FP32 outputs
+    sb = {}
+    if not args.profile:
+        Nb, kb, nr = 256, 5, 64
+        sbs = hdg.HDGSolver(Nb, Nb, kb, torch.ones(Nb * Nb, dtype=torch.float64, device="cuda"), mixed=0)
+        fq4 = torch.as_tensor(inputs.fourier_rhs(Nb, kb, nr, seed=3), device="cuda")
+        B4 = sbs.condense_rhs(fq4)                       # [ndof, 64] FP64
+        X4 = B4.to(torch.bfloat16).contiguous()
+        Y4 = torch.empty(X4.shape, dtype=torch.float32, device="cuda")
+        sbs.apply_shared_batched(X4, out=Y4)
+        ms4 = timed_events(lambda: sbs.apply_shared_batched(X4, out=Y4), args.apply_reps, torch)
+        algo4 = X4.numel() * 2 + Y4.numel() * 4 + 2 * 16 * 48 * 2
+        fl4 = 2.0 * Nb * Nb * 16 * (kb + 1) ** 2 * nr
+        sb = {"workload": "256x256 k=5 kappa=1, 64 Fourier right-hand sides (seed 3)", "ms": ms4,
+              "GBps": algo4 / (ms4 * 1e-3) / 1e9, "frac_hbm": algo4 / (ms4 * 1e-3) / 1e9 / peaks["hbm_gbs"],
+              "TFLOPs": fl4 / (ms4 * 1e-3) / 1e12, "algorithmic_bytes": algo4, "flops": fl4,
+              "kernel": "batched_apply_kernel (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 TMEM)"}
+        sbs.close()
+    # uneven instances in one persistent launch: 12 meshes N in {64..512}, k in {2,3,4}
+    # (seeded mix), kappa = 1, FP64 blocks; one hdg_apply_multi vs 12 single applies
+    mi = {}
+    if not args.profile:
+        mix = inputs.instance_mix(12, seed=4)
+        sols, xs = [], []
+        for q, (Nq, kq) in enumerate(mix):
+            sq = hdg.HDGSolver(Nq, Nq, kq, torch.ones(Nq * Nq, dtype=torch.float64, device="cuda"), mixed=0)
+            sols.append(sq)
+            xs.append(torch.as_tensor(inputs.random_trace(sq.n_edges, kq, seed=60 + q), device="cuda"))
+        ys = [torch.empty_like(x) for x in xs]
+        hdg.apply_multi(sols, xs, outs=ys)
+        ms_multi = timed_events(lambda: hdg.apply_multi(sols, xs, outs=ys), args.apply_reps, torch)
+
+        def singles():
+            for sq, x, y in zip(sols, xs, ys):
+                sq.apply(x, out=y)
+
+        ms_single = timed_events(singles, args.apply_reps, torch)
+        algo = sum(sq.nel * 16 * (sq.k + 1) ** 2 * 8 + 2 * sq.n_edges * (sq.k + 1) * 8 for sq in sols)
+        mi = {"instances": [[int(a_), int(b_)] for a_, b_ in mix], "ms_one_launch": ms_multi,
+              "ms_12_launches": ms_single, "GBps_one_launch": algo / (ms_multi * 1e-3) / 1e9,
+              "algorithmic_bytes": algo}
+        for sq in sols:
+            sq.close()
     # end to end through the public API with host buffers
     fq_pin = torch.as_tensor(fq_h).pin_memory()
     lam_pin = torch.empty(solver.ndof, dtype=torch.float64).pin_memory()
@@ -306,7 +358,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (FP64 S + Schwarz blocks %.0f MB)" % (2 * nel * 16 * n1 * n1 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
-        "roofline": roof, "trace_apply": tra, "mixed": mixed,
+        "roofline": roof, "trace_apply": tra, "mixed": mixed, "shared_batched_apply": sb, "multi_instance_apply": mi,
         "e2e": {"value": 1000.0 / e2e_ms, "unit": "solve/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(fq_h.nbytes), "d2h_bytes_per_step": int(solver.ndof * 8 + u.numel() * 8)},
         "gpu_launches": int(launches_per_step * args.steps),

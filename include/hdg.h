@@ -154,6 +154,18 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
 
 /*
+ * The trace apply of Alg. 3 for n independent meshes (1 <= n <= 16 contexts,
+ * uneven sizes, degrees 0..5) in ONE persistent kernel launch: the segments of
+ * all meshes form a single work list, so small meshes do not leave SMs idle
+ * behind large ones. y[q] = A_q x[q] for each q, same layouts and boundary rules
+ * as hdg_apply_trace (nrhs = 1). prec: HDG_PREC_FP64 (double vectors) or
+ * HDG_PREC_FP32 (float vectors). All contexts must belong to the current device.
+ * Errors: INVALID_ARG (count, pointers, degree, device), UNSUPPORTED (FP32 when a
+ * context has no FP32 blocks, other precisions).
+ */
+int hdg_apply_multi(int n, void* const* ctxs, const void* const* x, void* const* y, int prec, void* stream);
+
+/*
  * Batched apply for a uniform coefficient (every S_K equal): Y = A X for nrhs
  * right-hand sides on the 5th-generation tensor cores. Each owned face computes
  * y_e = [S[F rows], S[F' rows]] [x_K; x_nb] (Alg. 3 with a shared block) as one

@@ -23,7 +23,6 @@ namespace hdg {
 
 namespace {
 
-constexpr int kTilesPerBatch = 4;          // MMA tiles (face pairs) per batch
 constexpr int kTileM = 128;
 constexpr int kTileN = 16;
 constexpr int kThreads = 128;
@@ -79,30 +78,37 @@ __device__ __forceinline__ bool mbar_wait_1s(uint64_t* bar, unsigned parity) {
   }
 }
 
-// Offset of element (m, k) of an MN-major tile: core matrices of 8 k-rows x 16
-// bytes (8 consecutive m), K-direction core matrices 128 bytes apart, M-direction
-// groups of 8 m `sbo` bytes apart.
-__device__ __forceinline__ uint32_t a_off(int m8, int k, uint32_t sbo) {
-  return (uint32_t)m8 * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 16u;
-}
+// A tiles are MN-major without swizzle: core matrices of 8 k-rows x 16 bytes (8
+// consecutive m), K-direction core matrices 128 bytes apart, groups of 8 m
+// `sbo` bytes apart. B tiles are K-major with the same core-matrix strides.
+// x window of one segment and one group of 64 right-hand sides, built once and
+// read by the MMAs directly. 5 edge rows (V1: vertical edges of row j-1, V0:
+// row j, Hm: horizontal edges of row j-1, H0: row j, H1: row j+1) x 18 slots
+// (slot = i - (i0 - 1)); one slot holds one edge as 8 m-groups (8 right-hand
+// sides each) x 8 k-rows (the edge's nodes, zero beyond k+1) x 16 bytes, i.e.
+// eight MN-major core matrices 128 bytes apart. With SBO = 128 B an MMA's 16
+// m-groups cover two consecutive slots = two neighbouring elements' faces; the
+// two core matrices of a K16 step are the edges (W, E) of one element (next
+// slot, LBO = 1 KB) or (S, N) (next row, LBO = one row).
+constexpr int kBS = 8;                      // elements per segment of this kernel
+constexpr int kWRows = 5, kWSlots = kBS + 2;
+constexpr uint32_t kSlotB = 1024u, kRowB = kWSlots * kSlotB;
+enum { RV1 = 0, RV0 = 1, RHM = 2, RH0 = 3, RH1 = 4 };
 
 __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Kp = a.Kp;                                      // padded K (multiple of 16)
-  const uint32_t sboA = (uint32_t)(Kp / 8) * 128u;          // bytes between 8-row groups of A
-  const uint32_t tileA = (uint32_t)kTileM * Kp * 2;         // bytes of one A tile
-  const uint32_t sboB = (uint32_t)(Kp / 8) * 128u;
-  const uint32_t tileB = (uint32_t)kTileN * Kp * 2;
-  unsigned char* Abuf = sm;                                  // [kTilesPerBatch][tileA]
-  unsigned char* Bbuf = sm + kTilesPerBatch * tileA;         // [2][tileB]
+  constexpr uint32_t tileB = kTileN * 64 * 2;                // K = 64 (4 steps x 16)
+  unsigned char* W = sm;                                     // [5][18][1 KB]
+  unsigned char* Bbuf = sm + kWRows * kRowB;                 // [2][tileB]
   uint64_t* bar = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  constexpr int kTiles = kBS;                                // kBS/2 W pairs + kBS/2 S pairs
+  constexpr int kCols = kTiles * kTileN;                     // 8 tiles x 16 columns = 128
 
-  // tensor memory: kTilesPerBatch x 16 fp32 columns (64, a power of two >= 32)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(kTilesPerBatch * kTileN)
+                 "r"(kCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -110,11 +116,11 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // shared blocks B (both face types) in the K-major core-matrix layout
-  for (int idx = tid; idx < 2 * kTileN * Kp; idx += kThreads) {
-    const int t = idx / (kTileN * Kp), rem = idx % (kTileN * Kp);
-    const int n = rem / Kp, k = rem % Kp;
-    const uint32_t off = (uint32_t)(n >> 3) * sboB + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u +
+  // shared blocks B (both face types), K-major core matrices: k = step*16 + h*8 + node
+  for (int idx = tid; idx < 2 * kTileN * 64; idx += kThreads) {
+    const int t = idx / (kTileN * 64), rem = idx % (kTileN * 64);
+    const int n = rem / 64, k = rem % 64;
+    const uint32_t off = (uint32_t)(n >> 3) * 1024u + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u +
                          (uint32_t)(k & 7) * 2u;
     *reinterpret_cast<__nv_bfloat16*>(Bbuf + t * tileB + off) = a.B[idx];
   }
@@ -124,51 +130,38 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  const int n1 = a.n1, m = 4 * n1, twoM = 2 * m;
+  const int n1 = a.n1;
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int chunks = a.nrhs / 64;
-  const long items = (long)a.nseg * chunks * (2 * kSeg / 2 / kTilesPerBatch);   // batches of 4 tiles
-  const int bps = kSeg / kTilesPerBatch;          // batches per segment (2 W + 2 S)
+  const long items = (long)a.nseg * chunks;
   unsigned phase = 0;
   bool failed = false;
   for (long item = blockIdx.x; item < items && !failed; item += gridDim.x) {
-    const int batch = (int)(item % bps);
-    const long rest = item / bps;
-    const int chunk = (int)(rest % chunks);
-    const int seg = (int)(rest / chunks);
-    const int j = seg / a.spr, i0 = (seg % a.spr) * kSeg;
-    const int type = batch >= bps / 2 ? 1 : 0;    // 0: W faces, 1: S faces
-    const int pair0 = (batch % (bps / 2)) * kTilesPerBatch;   // first face pair of the batch
-    // ---- gather A: 4 tiles x 2 faces x Kp columns x 8 groups of 8 rhs ----
-    const int per_tile = 2 * Kp * 8;
-    for (int idx = tid; idx < kTilesPerBatch * per_tile; idx += kThreads) {
-      const int tl = idx / per_tile, rem = idx % per_tile;
-      const int s = rem / (Kp * 8), rem2 = rem % (Kp * 8);
-      const int k = rem2 >> 3, m8 = rem2 & 7;
-      const int L = 2 * (pair0 + tl) + s;          // element lane in the segment
-      const int i = i0 + L;
-      unsigned char* dst = Abuf + tl * tileA + a_off(s * 8 + m8, k, sboA);
-      bool valid = i < nx && k < twoM;
-      int ki = i, kj = j;
-      int c = k;
-      if (k >= m) {                                // neighbour across the face
-        c = k - m;
-        if (type == 0) ki = i - 1; else kj = j - 1;
-        if (ki < 0 || kj < 0) valid = false;
-      }
+    const int chunk = (int)(item % chunks);
+    const int seg = (int)(item / chunks);
+    const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
+    // ---- window: 5 rows x (kBS + 2) slots x 8 nodes x 8 groups of 16 bytes ----
+    for (int idx = tid; idx < kWRows * kWSlots * 64; idx += kThreads) {
+      const int g = idx & 7, nd = (idx >> 3) & 7, rs = idx >> 6;
+      const int r = rs / kWSlots, sl = rs - r * kWSlots;
+      const int i = i0 - 1 + sl;
       long row = -1;
-      if (valid) {
-        const int f = c / n1, nd = c % n1;
-        int edge;
-        bool bnd;
-        if (f == 0) { edge = ki + (nx + 1) * kj; bnd = ki == 0; }
-        else if (f == 1) { edge = ki + 1 + (nx + 1) * kj; bnd = ki == nx - 1; }
-        else if (f == 2) { edge = nv + ki + nx * kj; bnd = kj == 0; }
-        else { edge = nv + ki + nx * (kj + 1); bnd = kj == ny - 1; }
-        if (!bnd) row = (long)edge * n1 + nd;
+      if (nd < n1) {
+        int edge = -1;
+        bool inb = false;
+        switch (r) {
+          case RV1: inb = j >= 1 && i >= 1 && i <= nx - 1; edge = i + (nx + 1) * (j - 1); break;
+          case RV0: inb = i >= 1 && i <= nx - 1; edge = i + (nx + 1) * j; break;
+          case RHM: inb = j >= 2 && i >= 0 && i < nx; edge = nv + i + nx * (j - 1); break;
+          case RH0: inb = j >= 1 && i >= 0 && i < nx; edge = nv + i + nx * j; break;
+          default: inb = j + 1 <= ny - 1 && i >= 0 && i < nx; edge = nv + i + nx * (j + 1); break;
+        }
+        // interior edges only (the boundary trace is zero)
+        if (inb) row = (long)edge * n1 + nd;
       }
+      unsigned char* dst = W + (uint32_t)(r * kWSlots + sl) * kSlotB + (uint32_t)g * 128u + (uint32_t)nd * 16u;
       if (row >= 0) {
-        const __nv_bfloat16* src = a.X + (size_t)row * a.nrhs + chunk * 64 + m8 * 8;
+        const __nv_bfloat16* src = a.X + (size_t)row * a.nrhs + chunk * 64 + g * 8;
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
       } else {
         *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
@@ -179,15 +172,28 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- MMAs: one thread issues Kp/16 steps per tile, then commits ----
+    // ---- kBS tiles (kBS/2 W face pairs, kBS/2 S face pairs) x 4 K16 steps ----
     if (tid == 0) {
-      for (int tl = 0; tl < kTilesPerBatch; ++tl) {
-        const uint32_t abase = su32(Abuf + tl * tileA), bbase = su32(Bbuf + type * tileB);
-        const uint32_t dcol = tmem + (uint32_t)(tl * kTileN);
-        for (int kk = 0; kk < Kp / 16; ++kk) {
-          const uint64_t ad = smem_desc(abase + (uint32_t)kk * 256u, 128u, sboA);
-          const uint64_t bd = smem_desc(bbase + (uint32_t)kk * 256u, 128u, sboB);
-          const uint32_t acc = kk > 0 ? 1u : 0u;
+      const uint32_t wb = su32(W);
+      for (int t = 0; t < kTiles; ++t) {
+        const int type = t / (kTiles / 2), L = 2 * (t % (kTiles / 2));
+        const int sl = L + 1;                      // slot of the own element's W edge
+        const uint32_t bb = su32(Bbuf + type * tileB);
+        uint32_t start[4], lbo[4];
+        start[0] = wb + (uint32_t)(RV0 * kWSlots + sl) * kSlotB;  lbo[0] = kSlotB;   // own W, E
+        start[1] = wb + (uint32_t)(RH0 * kWSlots + sl) * kSlotB;  lbo[1] = kRowB;    // own S, N
+        if (type == 0) {                                                              // west neighbour
+          start[2] = wb + (uint32_t)(RV0 * kWSlots + sl - 1) * kSlotB;  lbo[2] = kSlotB;
+          start[3] = wb + (uint32_t)(RH0 * kWSlots + sl - 1) * kSlotB;  lbo[3] = kRowB;
+        } else {                                                                      // south neighbour
+          start[2] = wb + (uint32_t)(RV1 * kWSlots + sl) * kSlotB;  lbo[2] = kSlotB;
+          start[3] = wb + (uint32_t)(RHM * kWSlots + sl) * kSlotB;  lbo[3] = kRowB;
+        }
+        const uint32_t dcol = tmem + (uint32_t)(t * kTileN);
+        for (int p = 0; p < 4; ++p) {
+          const uint64_t ad = smem_desc(start[p], lbo[p], 128u);
+          const uint64_t bd = smem_desc(bb + (uint32_t)p * 256u, 128u, 1024u);
+          const uint32_t acc = p > 0 ? 1u : 0u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
@@ -200,46 +206,54 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
     }
     const bool ok = mbar_wait_1s(bar, phase);
     phase ^= 1u;
-    // one decision for the whole CTA (each thread timed its own wait)
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicExch(a.err, 2);
-        (void)mbar_wait_1s(bar, phase ^ 1u);   // let issued MMAs land before the columns are freed
+        (void)mbar_wait_1s(bar, phase ^ 1u);
       }
       failed = true;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!failed) {
-      // ---- epilogue: warp w reads lanes 32w..32w+31 (rows = 64 rhs of face s) ----
+      // ---- epilogue: warp w reads lanes 32w..32w+31 of every tile ----
       const int mrow = warp * 32 + lane;
       const int s = mrow >> 6, r = mrow & 63;
-      for (int tl = 0; tl < kTilesPerBatch; ++tl) {
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(tl * kTileN);
+      float* ybase = a.Y + chunk * 64 + r;
+      for (int t0 = 0; t0 < kTiles; t0 += 2) {
+        // two tiles per wait: 32 columns of this warp's 32 lanes
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t0 * kTileN);
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
             : "r"(taddr)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int L = 2 * (pair0 + tl) + s;
-        const int i = i0 + L;
+#pragma unroll
+        for (int tt = 0; tt < 2; ++tt) {
+        const int t = t0 + tt;
+        const uint32_t* vt = v + tt * kTileN;
+        const int type = t / (kTiles / 2);
+        const int i = i0 + 2 * (t % (kTiles / 2)) + s;
         if (i < nx) {
           const bool bndrow = type == 0 ? (i == 0) : (j == 0);
           const int eout = type == 0 ? i + (nx + 1) * j : nv + i + nx * j;
-          float* y = a.Y + chunk * 64 + r;
           for (int q = 0; q < n1; ++q)
-            y[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0f : __uint_as_float(v[q]);
-          // E / N domain-boundary edges have no owner: zero them
+            ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0f : __uint_as_float(vt[q]);
           if (type == 0 && i == nx - 1) {
             const int eb = nx + (nx + 1) * j;
-            for (int q = 0; q < n1; ++q) y[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
+            for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
           }
           if (type == 1 && j == ny - 1) {
             const int eb = nv + i + nx * ny;
-            for (int q = 0; q < n1; ++q) y[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
+            for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
           }
+        }
         }
       }
     }
@@ -249,24 +263,27 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTilesPerBatch * kTileN)
-                 : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
 // B blocks from the shared FP64 block S (element 0 of the finest level):
 // type 0 (W faces): row n < k+1: [S[W row n, :], S[E row n, :]]; type 1 (S faces):
 // [S[S row n, :], S[N row n, :]]; zero rows n >= k+1 and columns k >= 2m.
 __global__ void pack_shared_b_kernel(const double* __restrict__ S, int n1, int Kp, __nv_bfloat16* __restrict__ B) {
+  // B[type][n][k], k = step*16 + h*8 + node: step 0 own (W, E), 1 own (S, N),
+  // 2 neighbour (W, E), 3 neighbour (S, N); rows n = the face's node (zero past k+1)
   const int m = 4 * n1;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * kTileN * Kp; idx += gridDim.x * blockDim.x) {
-    const int t = idx / (kTileN * Kp), rem = idx % (kTileN * Kp);
-    const int n = rem / Kp, k = rem % Kp;
+  (void)Kp;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * kTileN * 64; idx += gridDim.x * blockDim.x) {
+    const int t = idx / (kTileN * 64), rem = idx % (kTileN * 64);
+    const int n = rem / 64, k = rem % 64;
+    const int step = k >> 4, h = (k >> 3) & 1, nd = k & 7;
     double v = 0.0;
-    if (n < n1 && k < 2 * m) {
+    if (n < n1 && nd < n1) {
       const int own_face = t == 0 ? 0 : 2, nb_face = t == 0 ? 1 : 3;
-      const int face = k < m ? own_face : nb_face;
-      const int c = k < m ? k : k - m;
-      v = S[(size_t)(face * n1 + n) * m + c];
+      const int row_face = step < 2 ? own_face : nb_face;          // rows of S used
+      const int col_face = (step & 1) * 2 + h;                      // W, E, S, N
+      v = S[(size_t)(row_face * n1 + n) * m + col_face * n1 + nd];
     }
     B[idx] = __float2bfloat16_rn((float)v);
   }
@@ -274,30 +291,30 @@ __global__ void pack_shared_b_kernel(const double* __restrict__ S, int n1, int K
 
 }  // namespace
 
-int shared_kp(int n1) { return ((8 * n1 + 15) / 16) * 16; }
+int shared_kp(int n1) { (void)n1; return 64; }
 
 cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s) {
-  const int n1 = c->k + 1, Kp = shared_kp(n1);
-  HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->shared_B, (size_t)2 * kTileN * Kp * sizeof(__nv_bfloat16)));
-  pack_shared_b_kernel<<<8, 256, 0, s>>>(c->plev[c->k].Sdense, n1, Kp, c->shared_B);
+  const int n1 = c->k + 1;
+  HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->shared_B, (size_t)2 * kTileN * 64 * sizeof(__nv_bfloat16)));
+  pack_shared_b_kernel<<<8, 256, 0, s>>>(c->plev[c->k].Sdense, n1, 64, c->shared_B);
   return cudaGetLastError();
 }
 
 size_t batched_smem_bytes(int n1) {
-  const int Kp = shared_kp(n1);
-  return (size_t)kTilesPerBatch * kTileM * Kp * 2 + (size_t)2 * kTileN * Kp * 2 + 16;
+  (void)n1;
+  return (size_t)kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 16;
 }
 
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s) {
   BatchedArgs a{};
   a.X = (const __nv_bfloat16*)X; a.Y = Y; a.B = c->shared_B;
   a.nx = c->mesh.nx; a.ny = c->mesh.ny; a.n1 = c->k + 1; a.Kp = shared_kp(a.n1);
-  a.nrhs = nrhs; a.spr = (c->mesh.nx + kSeg - 1) / kSeg; a.nseg = a.spr * c->mesh.ny; a.err = c->err_flag;
+  a.nrhs = nrhs; a.spr = (c->mesh.nx + kBS - 1) / kBS; a.nseg = a.spr * c->mesh.ny; a.err = c->err_flag;
   const size_t smem = batched_smem_bytes(a.n1);
   if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
   HDG_CUDA_TRY(cudaFuncSetAttribute(batched_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin));
-  const long items = (long)a.nseg * (nrhs / 64) * (kSeg / kTilesPerBatch);
-  // up to 4 resident CTAs per SM (64 TMEM columns each, < 60 KB shared memory each)
+  const long items = (long)a.nseg * (nrhs / 64);
+  // four resident CTAs per SM (128 TMEM columns and ~54 KB shared memory each)
   long blocks = (long)c->num_sms * 4;
   if (blocks > items) blocks = items;
   batched_apply_kernel<<<(int)blocks, kThreads, smem, s>>>(a);

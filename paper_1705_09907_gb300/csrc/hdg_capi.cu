@@ -287,6 +287,11 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
   return HDG_OK;
 }
 
+int hdg_apply_multi(int n, void* const* ctxs, const void* const* x, void* const* y, int prec, void* stream) {
+  if (n < 1 || !ctxs) return HDG_ERR_INVALID_ARG;
+  return apply_multi(reinterpret_cast<Context* const*>(ctxs), n, x, y, prec, (cudaStream_t)stream);
+}
+
 int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void* stream) {
   Context* c = (Context*)ctx;
   if (!c || !X || !Y || nrhs < 64 || nrhs % 64 != 0) return HDG_ERR_INVALID_ARG;

@@ -139,6 +139,8 @@ cudaError_t autotune_applies(Context* c, cudaStream_t s);
 // tensor-core batched apply of the shared block (hdg_batched.cu)
 cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s);
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s);
+// one persistent launch over several contexts (apply_multi.cu); returns hdg_status
+int apply_multi(Context* const* ctx, int n, const void* const* x, void* const* y, int prec, cudaStream_t s);
 
 // Trace-operator apply on the record layout of level p:
 //   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)

@@ -74,6 +74,7 @@ def _load():
         "hdg_adjoint_grad": (i, [vp, vp, vp, vp, d, i, vp, vp, vp, vp, vp]),
         "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_shared_batched": (i, [vp, vp, vp, i, vp]),
+        "hdg_apply_multi": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
         "hdg_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -99,6 +100,19 @@ hdg_recover_local = _lib.hdg_recover_local
 hdg_adjoint_grad = _lib.hdg_adjoint_grad
 hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
 hdg_apply_shared_batched = _lib.hdg_apply_shared_batched
+hdg_apply_multi = _lib.hdg_apply_multi
+
+
+def apply_multi(solvers, xs, prec="fp64", outs=None):
+    """One launch of y_q = A_q x_q over several HDGSolver instances."""
+    n = len(solvers)
+    ys = [torch.empty_like(x) for x in xs] if outs is None else outs
+    arr = ctypes.c_void_p * n
+    ctxs = arr(*[s.ctx.value for s in solvers])
+    xp = arr(*[_ptr(x, VEC_DTYPE[prec]).value for x in xs])
+    yp = arr(*[_ptr(y, VEC_DTYPE[prec]).value for y in ys])
+    _check(_lib.hdg_apply_multi(n, ctxs, xp, yp, PREC[prec], _stream()), "hdg_apply_multi")
+    return ys
 hdg_destroy = _lib.hdg_destroy
 
 
