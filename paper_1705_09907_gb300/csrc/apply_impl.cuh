@@ -307,8 +307,13 @@ constexpr size_t stage_total_bytes() {
 // the pair's ring; warp 0 of the pair applies each element's own row blocks,
 // warp 1 the neighbours' row blocks and hands its partial sums to warp 0
 // through shared memory (named barrier per pair), which writes the faces.
+// 8-byte blocks (FP64, F32X2) never fit more than 4 warp pairs per CTA, so they
+// get up to 255 registers; 2- and 4-byte blocks may use 8 pairs.
+template <typename TS>
+struct ApplyMaxThreads { static constexpr int value = sizeof(TS) >= 8 ? 256 : 512; };
+
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
-__global__ void __launch_bounds__(512) apply_kernel(ApplyArgs a) {
+__global__ void __launch_bounds__(ApplyMaxThreads<TS>::value) apply_kernel(ApplyArgs a) {
   using TO = typename OutT<TA>::type;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -412,6 +417,7 @@ cudaError_t apply_launch(const Context* c, const ApplyArgs& args0, cudaStream_t 
   a.stage_bytes = (unsigned)(16 * N1 * N1 * kSeg * sizeof(TS));
   int np = 0, NS = 0;
   apply_shape((unsigned)stage_total_bytes<N1, TS, TV, TO>(), a.tune, &np, &NS);
+  if (64 * np > ApplyMaxThreads<TS>::value) np = ApplyMaxThreads<TS>::value / 64;
   a.stages = NS;
   const size_t smem = (size_t)np * NS * stage_total_bytes<N1, TS, TV, TO>();
   auto kern = apply_kernel<N1, TS, TV, TA, DIFF>;

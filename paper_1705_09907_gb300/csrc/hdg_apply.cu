@@ -104,6 +104,7 @@ cudaError_t autotune_applies(Context* c, cudaStream_t s) {
           for (int ns = 1; ns <= 3; ++ns) {
             const int nw = nps[wi];                  // warp pairs
             if (nw * ns > total) continue;
+            if (prec_double(prec) && nw > 4) continue;   // 8-byte blocks: at most 4 pairs
             L.tune[prec][which] = nw * 16 + ns;
             HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
             HDG_CUDA_TRY(cudaEventRecord(e0, s));
