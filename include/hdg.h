@@ -96,7 +96,10 @@ typedef struct {
 
 typedef struct {
   int iterations;             /* CG iterations taken                         */
-  double relres;              /* final |b - A x|_2 / |b|_2 (FP64 residual)    */
+  double relres;              /* final |r|_2 / |b|_2, r the residual CG
+                                 updates (FP64 vectors); a recomputed b - A x
+                                 differs by rounding, ~eps |A||x| per row,
+                                 which grows like h^-2 relative to |b|        */
   double relres_history[256]; /* per iteration, [0] = 1                       */
   double solve_ms;            /* wall time of the call                       */
 } hdg_solve_info;
@@ -193,7 +196,8 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
 
 /*
  * Solve A lambda = b (Sec. 3 step (iii)) with conjugate gradients
- * preconditioned by one V-cycle per iteration, to |b - A lambda|_2 <= rtol |b|_2.
+ * preconditioned by one V-cycle per iteration, until the updated residual
+ * satisfies |r|_2 <= rtol |b|_2.
  * b, lambda: device [ndof] doubles (nrhs must be 1). The CG vectors, the
  * update and the residual are FP64 vectors; `inner` selects the V-cycle
  * precision. With inner = FP64 every apply is plain FP64. With inner = FP32,

@@ -1,0 +1,81 @@
+"""Full-size checks in the benchmark's launch configuration, on sampled outputs
+the oracle computes one by one from its own element blocks:
+  * 512 x 512, k = 4, lognormal kappa (seed 0), f = 1, FP64 V-cycle: the trace
+    apply at 300 sampled interior edges, the condensed right-hand side there,
+    and the residual of the solve there;
+  * 1024 x 1024, k = 3, same generator, FP32 V-cycle (mixed): the same checks,
+    and agreement with the FP64-preconditioned solve.
+Residual bound per row: rtol |b|_2 (the CG stopping rule on the updated
+residual) plus the rounding of a recomputed residual, which is of order
+eps * (8(k+1) terms) * (|S||lambda|)_row times the drift that accumulates over
+the iterations; 1e-13 (|S||lambda|)_row covers both (at 512^2 the rounding term
+alone is already ~1e-10 |b|_2, growing like h^-2)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hdg as ohdg, mesh as omesh
+from paper_1705_09907_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_edge_rows(m, k, kappa, fq, edges):
+    """For each sampled interior edge, per adjacent element: (S_K rows of the
+    edge, the element's global dofs, b_K rows of the edge)."""
+    el, fc = m.edge_to_elem()
+    prob = ohdg.HDGProblem(m, k, kappa)
+    out = []
+    for e in edges:
+        rows = []
+        for side in (0, 1):
+            K, f = el[e, side], fc[e, side]
+            mt = prob.mats(K)
+            S = ohdg.schur_block(mt)
+            bK = ohdg.rhs_block(mt, ohdg.load_vector(prob.ref, mt, fq[K]))
+            sl = slice(f * (k + 1), (f + 1) * (k + 1))
+            rows.append((S[sl], prob.dofs(K), bK[sl]))
+        out.append(rows)
+    return out, prob
+
+
+@pytest.mark.parametrize("N,k,inner", [(512, 4, "fp64"), (1024, 3, "fp32")])
+def test_fullsize_apply_condense_solve_sampled(N, k, inner):
+    from paper_1705_09907_gb300 import hdg
+    m = omesh.Mesh(N, N)
+    kappa = inputs.lognormal_kappa(N, 0)
+    fq = inputs.constant_f(N, k)
+    edges = np.random.default_rng(N + k).choice(m.interior_edges(), size=300, replace=False)
+    rows, prob = _oracle_edge_rows(m, k, kappa, fq, edges)
+    boundary = np.setdiff1d(np.arange(prob.ndof), prob.interior_dofs())
+    n1 = k + 1
+    s = hdg.HDGSolver(N, N, k, torch.as_tensor(kappa, device="cuda"))
+    # apply: boundary entries of x are nonzero and must be ignored
+    x = inputs.random_trace(m.n_edges, k, seed=7)
+    y = s.apply(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    xm = x.copy()
+    xm[boundary] = 0.0
+    for e, rr in zip(edges, rows):
+        ref = sum(S @ xm[d] for S, d, _ in rr)
+        scale = sum(np.abs(S) @ np.abs(xm[d]) for S, d, _ in rr)
+        assert np.all(np.abs(y[e * n1:(e + 1) * n1] - ref) <= 1e-12 * scale)
+    # condensed right-hand side
+    b = s.condense_rhs(torch.as_tensor(fq, device="cuda"))
+    b_h = b.cpu().numpy()
+    bmax, b2 = np.abs(b_h).max(), np.linalg.norm(b_h)
+    for e, rr in zip(edges, rows):
+        assert np.abs(b_h[e * n1:(e + 1) * n1] - sum(bk for _, _, bk in rr)).max() <= 1e-12 * bmax
+    # solve: residual of the GPU lambda in the oracle's operator at the sampled rows
+    rtol = 1e-10
+    lam, info = s.solve(b, rtol=rtol, maxit=400, inner=inner)
+    assert info["relres"] <= rtol
+    lam_h = lam.cpu().numpy()
+    assert np.all(lam_h[boundary] == 0.0)
+    for e, rr in zip(edges, rows):
+        res = sum(bk for _, _, bk in rr) - sum(S @ lam_h[d] for S, d, _ in rr)
+        absl = sum(np.abs(S) @ np.abs(lam_h[d]) for S, d, _ in rr)
+        assert np.all(np.abs(res) <= rtol * b2 + 1e-13 * absl)
+    if inner != "fp64":
+        lam64, _ = s.solve(b, rtol=rtol, maxit=400, inner="fp64")
+        assert float(torch.linalg.norm(lam - lam64) / torch.linalg.norm(lam64)) <= 1e-7
+    s.close()
