@@ -151,7 +151,8 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
  * interior edge, y = 0 on boundary edges. Each face is written once, by one
  * thread, with no atomics. x, y: device [ndof][nrhs] in the type `prec`
  * selects (double for FP64 and F32X2, float for FP32 and BF16); x and y must
- * not overlap. Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED
+ * not overlap. With nrhs > 1 each CTA stages one segment's blocks in shared
+ * memory once and applies them to all columns (lanes over right-hand sides). Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED
  * (FP32/BF16/F32X2 when the context was built with mixed = 0).
  */
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
@@ -190,6 +191,10 @@ int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void*
  * coarsest mesh. r, z: device [ndof][nrhs] (double for FP64 and F32X2, float
  * for FP32 and BF16; the Q1 levels run in the vector type, the coarsest solve
  * in FP64).
+ * With nrhs > 1 every level works on all columns at once; the work vectors for
+ * that nrhs are allocated on the first such call (and replaced when nrhs
+ * changes), and the cycle is captured as its own CUDA graph. Errors: OOM when
+ * those vectors do not fit.
  * The operator is symmetric positive definite, so CG may use it.
  */
 int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* stream);
@@ -198,7 +203,11 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
  * Solve A lambda = b (Sec. 3 step (iii)) with conjugate gradients
  * preconditioned by one V-cycle per iteration, until the updated residual
  * satisfies |r|_2 <= rtol |b|_2.
- * b, lambda: device [ndof] doubles (nrhs must be 1). The CG vectors, the
+ * b, lambda: device [ndof][nrhs] doubles (right-hand side fastest). With
+ * nrhs > 1 the columns iterate together: one batched operator apply and one
+ * batched V-cycle per iteration, step lengths per column, and a column stops
+ * updating once its own residual meets rtol; info then reports the iteration
+ * at which the last column converged and the largest residual. The CG vectors, the
  * update and the residual are FP64 vectors; `inner` selects the V-cycle
  * precision. With inner = FP64 every apply is plain FP64. With inner = FP32,
  * BF16 or F32X2 the outer operator apply uses F32X2 blocks (FP64 vectors,

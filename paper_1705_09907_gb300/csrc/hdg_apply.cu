@@ -1,5 +1,5 @@
 // Dispatch of the record-layout apply and small vector kernels.
-#include "apply_impl.cuh"
+#include "apply_cols.cuh"
 
 namespace hdg {
 
@@ -12,6 +12,21 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
   else if (prec == HDG_PREC_F32X2) rec = which ? (const void*)L.M2 : (const void*)L.S2;
   else rec = which ? (const void*)L.M16 : (const void*)L.S16;
   if (!rec) return cudaErrorInvalidValue;
+  // the condensed blocks have zero row sums: apply the low-precision copies to
+  // x - mean(x) per element; FP64 and the Schwarz blocks use x directly
+  const bool diff = (which == 0) && (prec == HDG_PREC_FP32 || prec == HDG_PREC_BF16);
+  if (nrhs > 1) {   // right-hand-side-fastest columns: the column-batched kernel
+    ColsArgs b{};
+    b.rec = rec; b.v = v; b.cvec = cvec; b.y = y;
+    b.alpha = alpha; b.beta = beta;
+    b.nx = c->mesh.nx; b.ny = c->mesh.ny;
+    b.spr = (c->mesh.nx + kSeg - 1) / kSeg;
+    b.nseg = L.nseg; b.nb = nrhs;
+    if (prec == HDG_PREC_FP64) return cols_fp64(c, L.n1, diff, b, s);
+    if (prec == HDG_PREC_F32X2) return cols_x2(c, L.n1, diff, b, s);
+    if (prec == HDG_PREC_FP32) return cols_fp32(c, L.n1, diff, b, s);
+    return cols_bf16(c, L.n1, diff, b, s);
+  }
   ApplyArgs a{};
   a.rec = rec; a.v = v; a.cvec = cvec; a.y = y;
   a.alpha = alpha; a.beta = beta;
@@ -19,9 +34,6 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
   a.spr = (c->mesh.nx + kSeg - 1) / kSeg;
   a.nseg = L.nseg; a.nrhs = nrhs; a.err = c->err_flag;
   a.tune = L.tune[prec][which ? 1 : 0];
-  // the condensed blocks have zero row sums: apply the low-precision copies to
-  // x - mean(x) per element; FP64 and the Schwarz blocks use x directly
-  const bool diff = (which == 0) && (prec == HDG_PREC_FP32 || prec == HDG_PREC_BF16);
   if (prec == HDG_PREC_FP64) return apply_fp64(c, L.n1, diff, a, s);
   if (prec == HDG_PREC_F32X2) return apply_x2(c, L.n1, diff, a, s);
   if (prec == HDG_PREC_FP32) return apply_fp32(c, L.n1, diff, a, s);

@@ -10,7 +10,6 @@
 namespace hdg {
 cudaError_t launch_maps(Context* c, cudaStream_t s);
 cudaError_t launch_check_kappa(Context* c, cudaStream_t s);
-cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_double, cudaStream_t s);
 }  // namespace hdg
 
 using namespace hdg;
@@ -43,12 +42,6 @@ static int read_err_flag(Context* c, cudaStream_t s) {
     case 1: case 3: return HDG_ERR_INVALID_ARG;   // non-SPD local system / bad kappa
     default: return HDG_ERR_CUDA;
   }
-}
-
-template <typename T>
-__global__ void strided_copy_kernel(size_t n, const T* __restrict__ a, size_t sa, T* __restrict__ b, size_t sb) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
-    b[t * sb] = a[t * sa];
 }
 
 extern "C" {
@@ -260,30 +253,10 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
   if (!c || !r || !z || nrhs < 1) return HDG_ERR_INVALID_ARG;
   if (prec < 0 || prec > 3) return HDG_ERR_INVALID_ARG;
   if (!prec_ok(c, prec)) return HDG_ERR_UNSUPPORTED;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (nrhs == 1) {
-    TRY(vcycle(c, prec, r, z, s));
-    return HDG_OK;
-  }
-  // one right-hand side at a time through contiguous scratch
-  const size_t n = (size_t)c->ndof;
-  const size_t w = prec_double(prec) ? sizeof(double) : sizeof(float);
-  void *ri, *zi;
-  TRY(cudaMallocAsync(&ri, n * w, s));
-  TRY(cudaMallocAsync(&zi, n * w, s));
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 2048) blocks = 2048;
-  for (int q = 0; q < nrhs; ++q) {
-    if (prec_double(prec)) strided_copy_kernel<double><<<blocks, 256, 0, s>>>(n, (const double*)r + q, nrhs, (double*)ri, 1);
-    else strided_copy_kernel<float><<<blocks, 256, 0, s>>>(n, (const float*)r + q, nrhs, (float*)ri, 1);
-    TRY(cudaGetLastError());
-    TRY(vcycle(c, prec, ri, zi, s));
-    if (prec_double(prec)) strided_copy_kernel<double><<<blocks, 256, 0, s>>>(n, (const double*)zi, 1, (double*)z + q, nrhs);
-    else strided_copy_kernel<float><<<blocks, 256, 0, s>>>(n, (const float*)zi, 1, (float*)z + q, nrhs);
-    TRY(cudaGetLastError());
-  }
-  TRY(cudaFreeAsync(ri, s));
-  TRY(cudaFreeAsync(zi, s));
+  // nrhs > 1: all columns through one batched cycle (work vectors allocated on first use)
+  const cudaError_t e = vcycle(c, prec, r, z, nrhs, (cudaStream_t)stream);
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HDG_ERR_OOM; }
+  TRY(e);
   return HDG_OK;
 }
 
@@ -304,12 +277,13 @@ int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void*
 int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol, int maxit, int inner,
               hdg_solve_info* info, void* stream) {
   Context* c = (Context*)ctx;
-  if (!c || !b || !lambda || nrhs != 1 || !(rtol > 0.0) || maxit < 1 || b == lambda) return HDG_ERR_INVALID_ARG;
+  if (!c || !b || !lambda || nrhs < 1 || !(rtol > 0.0) || maxit < 1 || b == lambda) return HDG_ERR_INVALID_ARG;
   if (inner < 0 || inner > 3) return HDG_ERR_INVALID_ARG;
   if (!prec_ok(c, inner)) return HDG_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   const auto t0 = std::chrono::steady_clock::now();
-  int st = pcg_solve(c, b, lambda, rtol, maxit, inner, info, s);
+  int st = nrhs == 1 ? pcg_solve(c, b, lambda, rtol, maxit, inner, info, s)
+                     : pcg_solve_batched(c, b, lambda, nrhs, rtol, maxit, inner, info, s);
   const int fl = read_err_flag(c, s);
   if (st == HDG_OK && fl != HDG_OK) st = fl;
   if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -377,8 +351,7 @@ void hdg_destroy(void* ctx) {
   Context* c = (Context*)ctx;
   if (!c) return;
   cudaDeviceSynchronize();
-  for (int g = 0; g < 3; ++g)
-    if (c->vc_graph[g]) cudaGraphExecDestroy(c->vc_graph[g]);
+  release_works(c);
   for (auto& L : c->plev)
     if (L.Sdense) cudaFree(L.Sdense);
   for (void* p : c->allocs) cudaFree(p);

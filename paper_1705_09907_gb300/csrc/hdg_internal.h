@@ -78,6 +78,28 @@ struct HLevel {
   float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;
 };
 
+// Work vectors of one V-cycle in one vector type (double for FP64 / F32X2
+// cycles, float for FP32 / BF16 cycles) for nb right-hand sides stored
+// right-hand-side fastest ([n][nb]). The single-vector work points into the
+// levels' own buffers; a batched work owns its buffers (and the batched CG
+// vectors of hdg_solve with nrhs > 1).
+struct VWork {
+  int nb = 1;
+  bool dbl = true;
+  std::vector<void*> pr, px, pt;            // p-levels 0..k: residual, correction, scratch
+  void* p0d = nullptr;                      // p = 0 Chebyshev direction
+  std::vector<void*> hr, hx, ht, hd;        // Q1 levels, finest first
+  double* coarse_w = nullptr;               // [nb][coarse_dim] FP64 scratch
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};   // per precision
+  cudaStream_t gstream[4] = {nullptr, nullptr, nullptr, nullptr};
+  // batched CG (double works only): vectors [ndof][nb], per-column scalars, partials
+  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_zold = nullptr;
+  double* cg_sc = nullptr;                  // [kCgScalars][nb]
+  double* cg_part = nullptr;                // [3][reduction blocks][nb]
+  double* h_sc = nullptr;                   // pinned host mirror [2][nb]
+  std::vector<void*> own;                   // device buffers owned by this work
+};
+
 struct Context {
   hdg_mesh mesh{};
   hdg_options opt{};
@@ -113,9 +135,9 @@ struct Context {
   size_t bytes = 0;
   double setup_ms = 0.0;
   std::vector<void*> allocs;
-  // CUDA graphs of the V-cycle body, per precision, keyed by stream
-  cudaGraphExec_t vc_graph[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaStream_t vc_graph_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+  // V-cycle work: single vector (double, float family) and batched (on demand)
+  VWork w1[2];                              // [0] double, [1] float
+  VWork* wb[2] = {nullptr, nullptr};
   int vcycle_kernels = 0;                   // kernel nodes of the captured V-cycle
   // uniform coefficient: the shared block for the tensor-core batched apply
   bool uniform_kappa = false;
@@ -150,9 +172,17 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
 
 // Multigrid pieces (hdg_mg.cu)
 cudaError_t build_hierarchy(Context* c, cudaStream_t s);
-cudaError_t vcycle(Context* c, int prec, const void* r, void* z, cudaStream_t s);
+// z = V r for nb right-hand sides ([ndof][nb]; double for FP64 / F32X2, float otherwise)
+cudaError_t vcycle(Context* c, int prec, const void* r, void* z, int nb, cudaStream_t s);
 int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, int inner,
               hdg_solve_info* info, cudaStream_t s);
+// CG on nb right-hand sides at once (b, x: [ndof][nb]), one V-cycle of all
+// columns per iteration, per-column step lengths; a column stops updating once
+// its residual meets rtol
+int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rtol, int maxit, int inner,
+                      hdg_solve_info* info, cudaStream_t s);
+// releases the V-cycle works' graphs and the batched works' buffers
+void release_works(Context* c);
 
 // Vector helpers (hdg_apply.cu)
 cudaError_t vec_dot(Context* c, const double* a, const double* b, int n, double* out_dev, cudaStream_t s);

@@ -8,6 +8,7 @@
 //                 triple products below), Chebyshev smoothing, bilinear P and
 //                 R = P^T; P_J / P_J^T (edge means, Eq. eq_h_mg_pro) between the
 //                 finest Q1 level and p = 0; FP64 Cholesky on the coarsest mesh.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -17,6 +18,7 @@
 namespace hdg {
 
 constexpr int kRedBlocks = 304;   // fixed reduction grid (deterministic sums)
+constexpr int kCgScalars = 12;    // per-column scalars of the batched CG
 
 // ---------------------------------------------------------------------------
 // Deterministic dot products: fixed grid of partial sums, then one block sums
@@ -104,21 +106,22 @@ static int grid_for(size_t n) {
 
 // Chebyshev steps: first step from x = 0 (x = d = c0 * dinv .* f), first step
 // with x given (d = c0 * dinv .* t; x += d), later steps (d = a1 d + a2 dinv .* t;
-// x += d).
+// x += d). Vectors hold nb right-hand sides per unknown (right-hand side
+// fastest); n counts unknowns x columns.
 template <typename T>
-__global__ void cheb_first_zero_kernel(size_t n, const T* __restrict__ dinv, const T* __restrict__ f,
+__global__ void cheb_first_zero_kernel(size_t n, int nb, const T* __restrict__ dinv, const T* __restrict__ f,
                                        T* __restrict__ x, T* __restrict__ d, T c0) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const T v = c0 * dinv[t] * f[t];
+    const T v = c0 * dinv[t / nb] * f[t];
     x[t] = v;
     d[t] = v;
   }
 }
 template <typename T>
-__global__ void cheb_step_kernel(size_t n, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ x,
-                                 T* __restrict__ d, T a1, T a2) {
+__global__ void cheb_step_kernel(size_t n, int nb, const T* __restrict__ dinv, const T* __restrict__ r,
+                                 T* __restrict__ x, T* __restrict__ d, T a1, T a2) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const T v = a1 * d[t] + a2 * dinv[t] * r[t];
+    const T v = a1 * d[t] + a2 * dinv[t / nb] * r[t];
     d[t] = v;
     x[t] += v;
   }
@@ -127,50 +130,58 @@ __global__ void cheb_step_kernel(size_t n, const T* __restrict__ dinv, const T* 
 // ---------------------------------------------------------------------------
 // p-transfers per edge. P is [(pc+2) x (pc+1)] row-major: fine node a', coarse a.
 template <typename T>
-__global__ void restrict_p_kernel(int n_edges, int n1c, const double* __restrict__ P,
+__global__ void restrict_p_kernel(int n_edges, int n1c, int nb, const double* __restrict__ P,
                                   const T* __restrict__ rf, T* __restrict__ rc) {
   const int n1f = n1c + 1;
-  const size_t total = (size_t)n_edges * n1c;
+  const size_t total = (size_t)n_edges * n1c * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t e = t / n1c;
-    const int a = (int)(t % n1c);
+    const size_t u = t / nb;
+    const int col = (int)(t % nb);
+    const size_t e = u / n1c;
+    const int a = (int)(u % n1c);
     T s = 0;
-    for (int b = 0; b < n1f; ++b) s += (T)P[b * n1c + a] * rf[e * n1f + b];
+    for (int b = 0; b < n1f; ++b) s += (T)P[b * n1c + a] * rf[(e * n1f + b) * nb + col];
     rc[t] = s;
   }
 }
 template <typename T>
-__global__ void prolong_p_add_kernel(int n_edges, int n1c, const double* __restrict__ P,
+__global__ void prolong_p_add_kernel(int n_edges, int n1c, int nb, const double* __restrict__ P,
                                      const T* __restrict__ xc, T* __restrict__ xf) {
   const int n1f = n1c + 1;
-  const size_t total = (size_t)n_edges * n1f;
+  const size_t total = (size_t)n_edges * n1f * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t e = t / n1f;
-    const int a = (int)(t % n1f);
+    const size_t u = t / nb;
+    const int col = (int)(t % nb);
+    const size_t e = u / n1f;
+    const int a = (int)(u % n1f);
     T s = 0;
-    for (int b = 0; b < n1c; ++b) s += (T)P[a * n1c + b] * xc[e * n1c + b];
+    for (int b = 0; b < n1c; ++b) s += (T)P[a * n1c + b] * xc[(e * n1c + b) * nb + col];
     xf[t] += s;
   }
 }
 
 // P_J^T: interior vertex (I, J) gets half the sum of its 4 edges' residuals.
 template <typename T>
-__global__ void restrict_J_kernel(int nx, int ny, const T* __restrict__ r0, T* __restrict__ rq) {
-  const int nvx = nx - 1, nvert = (nx - 1) * (ny - 1);
-  const int nv = (nx + 1) * ny;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
-    const int I = t % nvx + 1, J = t / nvx + 1;
-    const T s = r0[I + (nx + 1) * (J - 1)] + r0[I + (nx + 1) * J] + r0[nv + (I - 1) + nx * J] + r0[nv + I + nx * J];
+__global__ void restrict_J_kernel(int nx, int ny, int nb, const T* __restrict__ r0, T* __restrict__ rq) {
+  const int nvx = nx - 1;
+  const size_t nv = (size_t)(nx + 1) * ny, total = (size_t)(nx - 1) * (ny - 1) * nb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int u = (int)(t / nb), col = (int)(t % nb);
+    const size_t I = u % nvx + 1, J = u / nvx + 1;
+    const T s = r0[(I + (nx + 1) * (J - 1)) * nb + col] + r0[(I + (nx + 1) * J) * nb + col] +
+                r0[(nv + (I - 1) + nx * J) * nb + col] + r0[(nv + I + nx * J) * nb + col];
     rq[t] = T(0.5) * s;
   }
 }
 // P_J: every edge gets the mean of its two end vertices (boundary vertices 0);
 // boundary edges stay 0.
 template <typename T>
-__global__ void prolong_J_add_kernel(int nx, int ny, const T* __restrict__ xq, T* __restrict__ x0) {
+__global__ void prolong_J_add_kernel(int nx, int ny, int nb, const T* __restrict__ xq, T* __restrict__ x0) {
   const int nvx = nx - 1;
   const int nv = (nx + 1) * ny, ne = nv + nx * (ny + 1);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ne; t += gridDim.x * blockDim.x) {
+  const size_t total = (size_t)ne * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(tt / nb), col = (int)(tt % nb);
     int I0, J0, I1, J1;
     bool interior;
     if (t < nv) {
@@ -184,9 +195,9 @@ __global__ void prolong_J_add_kernel(int nx, int ny, const T* __restrict__ xq, T
     }
     if (!interior) continue;
     T s = 0;
-    if (I0 > 0 && I0 < nx && J0 > 0 && J0 < ny) s += xq[(I0 - 1) + nvx * (J0 - 1)];
-    if (I1 > 0 && I1 < nx && J1 > 0 && J1 < ny) s += xq[(I1 - 1) + nvx * (J1 - 1)];
-    x0[t] += T(0.5) * s;
+    if (I0 > 0 && I0 < nx && J0 > 0 && J0 < ny) s += xq[((size_t)(I0 - 1) + nvx * (J0 - 1)) * nb + col];
+    if (I1 > 0 && I1 < nx && J1 > 0 && J1 < ny) s += xq[((size_t)(I1 - 1) + nvx * (J1 - 1)) * nb + col];
+    x0[tt] += T(0.5) * s;
   }
 }
 
@@ -197,13 +208,15 @@ __global__ void prolong_J_add_kernel(int nx, int ny, const T* __restrict__ xq, T
 // + rsum_v x_v: exact in exact arithmetic, and the rounded stencil then sees the
 // variation of x around v rather than its (smooth, large) value.
 template <typename T>
-__global__ void stencil_apply_kernel(int nx, int ny, const T* __restrict__ st, const T* __restrict__ x,
+__global__ void stencil_apply_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ x,
                                      const T* __restrict__ c, T* __restrict__ y, T alpha, T beta,
                                      const T* __restrict__ rsum) {
   const int nvx = nx - 1, nvy = ny - 1, nvert = nvx * nvy;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+  const size_t total = (size_t)nvert * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(tt / nb), col = (int)(tt % nb);
     const int I = t % nvx, J = t / nvx;
-    const T xc = x[t];
+    const T xc = x[tt];
     T s = rsum ? rsum[t] * xc : T(0);
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
@@ -212,15 +225,16 @@ __global__ void stencil_apply_kernel(int nx, int ny, const T* __restrict__ st, c
         const int I2 = I + dx, J2 = J + dy;
         if (I2 < 0 || J2 < 0 || I2 >= nvx || J2 >= nvy) continue;
         const T a = st[((dy + 1) * 3 + dx + 1) * (size_t)nvert + t];
+        const T xn = x[((size_t)I2 + (size_t)nvx * J2) * nb + col];
         if (rsum) {
-          if (dx != 0 || dy != 0) s += a * (x[I2 + nvx * J2] - xc);
+          if (dx != 0 || dy != 0) s += a * (xn - xc);
         } else {
-          s += a * x[I2 + nvx * J2];
+          s += a * xn;
         }
       }
     T v = alpha * s;
-    if (c) v += beta * c[t];
-    y[t] = v;
+    if (c) v += beta * c[tt];
+    y[tt] = v;
   }
 }
 
@@ -235,10 +249,12 @@ __global__ void stencil_rowsum_kernel(int nvert, const double* __restrict__ st, 
 
 // full weighting R = P^T of bilinear interpolation
 template <typename T>
-__global__ void restrict_q_kernel(int nxc, int nyc, const T* __restrict__ rf, T* __restrict__ rc) {
+__global__ void restrict_q_kernel(int nxc, int nyc, int nb, const T* __restrict__ rf, T* __restrict__ rc) {
   const int nxf = 2 * nxc, nyf = 2 * nyc;
-  const int nvxc = nxc - 1, nvert = (nxc - 1) * (nyc - 1), nvxf = nxf - 1;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+  const int nvxc = nxc - 1, nvxf = nxf - 1;
+  const size_t total = (size_t)(nxc - 1) * (nyc - 1) * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(tt / nb), col = (int)(tt % nb);
     const int I = t % nvxc + 1, J = t / nvxc + 1;
     T s = 0;
     for (int b = -1; b <= 1; ++b)
@@ -246,17 +262,19 @@ __global__ void restrict_q_kernel(int nxc, int nyc, const T* __restrict__ rf, T*
         const int i = 2 * I + a, j = 2 * J + b;
         if (i <= 0 || j <= 0 || i >= nxf || j >= nyf) continue;
         const T w = (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5));
-        s += w * rf[(i - 1) + nvxf * (j - 1)];
+        s += w * rf[((size_t)(i - 1) + (size_t)nvxf * (j - 1)) * nb + col];
       }
-    rc[t] = s;
+    rc[tt] = s;
   }
 }
 
 template <typename T>
-__global__ void prolong_q_add_kernel(int nxc, int nyc, const T* __restrict__ xc, T* __restrict__ xf) {
+__global__ void prolong_q_add_kernel(int nxc, int nyc, int nb, const T* __restrict__ xc, T* __restrict__ xf) {
   const int nxf = 2 * nxc, nyf = 2 * nyc;
-  const int nvxf = nxf - 1, nvert = (nxf - 1) * (nyf - 1), nvxc = nxc - 1;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
+  const int nvxf = nxf - 1, nvxc = nxc - 1;
+  const size_t total = (size_t)(nxf - 1) * (nyf - 1) * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(tt / nb), col = (int)(tt % nb);
     const int i = t % nvxf + 1, j = t / nvxf + 1;
     const int i0 = i / 2, j0 = j / 2;
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
@@ -266,9 +284,9 @@ __global__ void prolong_q_add_kernel(int nxc, int nyc, const T* __restrict__ xc,
       for (int a = 0; a < ni; ++a) {
         const int I = i0 + a, J = j0 + b;
         if (I <= 0 || J <= 0 || I >= nxc || J >= nyc) continue;
-        s += wx * wy * xc[(I - 1) + nvxc * (J - 1)];
+        s += wx * wy * xc[((size_t)(I - 1) + (size_t)nvxc * (J - 1)) * nb + col];
       }
-    xf[t] += s;
+    xf[tt] += s;
   }
 }
 
@@ -377,11 +395,14 @@ __global__ void cholesky_block_kernel(int n, double* __restrict__ A, int* err) {
   }
 }
 
+// one CTA per right-hand side (column blockIdx.x of [n][nb]); w: [nb][n] scratch
 template <typename T>
-__global__ void coarse_solve_kernel(int n, const double* __restrict__ L, const T* __restrict__ r,
+__global__ void coarse_solve_kernel(int n, int nb, const double* __restrict__ L, const T* __restrict__ r,
                                     T* __restrict__ x, double* __restrict__ w) {
-  // forward then backward substitution, columns in parallel over threads
-  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = (double)r[i];
+  const int col = blockIdx.x;
+  w += (size_t)col * n;
+  // forward then backward substitution, rows in parallel over threads
+  for (int i = threadIdx.x; i < n; i += blockDim.x) w[i] = (double)r[(size_t)i * nb + col];
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) w[j] /= L[(size_t)j * n + j];
@@ -397,7 +418,7 @@ __global__ void coarse_solve_kernel(int n, const double* __restrict__ L, const T
     for (int i = threadIdx.x; i < j; i += blockDim.x) w[i] -= L[(size_t)j * n + i] * wj;
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (T)w[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[(size_t)i * nb + col] = (T)w[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -425,18 +446,19 @@ __global__ void power_start_verts_kernel(int n, double* __restrict__ x) {
 }
 
 // ---------------------------------------------------------------------------
-// Level operators used by the V-cycle, generic over the vector type.
+// Level operators used by the V-cycle, generic over the vector type; nb
+// right-hand sides per unknown.
 static cudaError_t p0_apply(Context* c, int prec, const void* v, const void* cv, void* y, double al, double be,
-                            cudaStream_t s) {
-  return launch_apply(c, 0, 0, prec, v, cv, y, al, be, 1, s);
+                            int nb, cudaStream_t s) {
+  return launch_apply(c, 0, 0, prec, v, cv, y, al, be, nb, s);
 }
 
 template <typename T>
-static cudaError_t q_apply(HLevel& H, const T* st, const T* x, const T* cv, T* y, double al, double be,
+static cudaError_t q_apply(HLevel& H, const T* st, const T* x, const T* cv, T* y, double al, double be, int nb,
                            cudaStream_t s) {
   // float levels use the difference form (rowsum32), double levels the plain one
   const T* rs = (sizeof(T) == 4) ? (const T*)(const void*)H.rsum32 : nullptr;
-  stencil_apply_kernel<T><<<grid_for(H.nv), 256, 0, s>>>(H.nx, H.ny, st, x, cv, y, (T)al, (T)be, rs);
+  stencil_apply_kernel<T><<<grid_for((size_t)H.nv * nb), 256, 0, s>>>(H.nx, H.ny, nb, st, x, cv, y, (T)al, (T)be, rs);
   return cudaGetLastError();
 }
 
@@ -462,34 +484,34 @@ static ChebCoef cheb_coefficients(double lmax, int degree) {
 // nu Chebyshev smoothing steps on one h-level (the p = 0 level when H == nullptr).
 template <typename T>
 static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x, T* t, T* d, bool x_zero,
-                               int nu, cudaStream_t s) {
+                               int nu, int nb, cudaStream_t s) {
   const bool p0 = (H == nullptr);
   PLevel& L0 = c->plev[0];
-  const size_t n = p0 ? (size_t)c->n_edges : (size_t)H->nv;
+  const size_t n = (p0 ? (size_t)c->n_edges : (size_t)H->nv) * nb;
   const T* dinv = p0 ? (const T*)(prec_double(prec) ? (const void*)L0.dinv64 : (const void*)L0.dinv32)
                      : (const T*)(prec_double(prec) ? (const void*)H->dinv64 : (const void*)H->dinv32);
   const T* st = p0 ? nullptr : (const T*)(prec_double(prec) ? (const void*)H->st64 : (const void*)H->st32);
   const ChebCoef cc = cheb_coefficients(p0 ? L0.lmax : H->lmax, c->opt.cheb_degree);
   auto A = [&](const T* v, const T* cv, T* y, double al, double be) -> cudaError_t {
-    if (p0) return p0_apply(c, prec, v, cv, y, al, be, s);
-    return q_apply<T>(*H, st, v, cv, y, al, be, s);
+    if (p0) return p0_apply(c, prec, v, cv, y, al, be, nb, s);
+    return q_apply<T>(*H, st, v, cv, y, al, be, nb, s);
   };
   const int g = grid_for(n);
   for (int step = 0; step < nu; ++step) {
     const T* rsrc;
     if (step == 0 && x_zero) {
-      cheb_first_zero_kernel<T><<<g, 256, 0, s>>>(n, dinv, f, x, d, (T)cc.c0);
+      cheb_first_zero_kernel<T><<<g, 256, 0, s>>>(n, nb, dinv, f, x, d, (T)cc.c0);
       HDG_CUDA_TRY(cudaGetLastError());
       rsrc = f;
     } else {
       HDG_CUDA_TRY(A(x, f, t, -1.0, 1.0));                    // t = f - A x
-      cheb_step_kernel<T><<<g, 256, 0, s>>>(n, dinv, t, x, d, (T)0, (T)cc.c0);   // d = c0 D^-1 t
+      cheb_step_kernel<T><<<g, 256, 0, s>>>(n, nb, dinv, t, x, d, (T)0, (T)cc.c0);   // d = c0 D^-1 t
       HDG_CUDA_TRY(cudaGetLastError());
       rsrc = t;
     }
     for (size_t i = 0; i < cc.a1.size(); ++i) {
       HDG_CUDA_TRY(A(d, rsrc, t, -1.0, 1.0));                 // t = r - A d
-      cheb_step_kernel<T><<<g, 256, 0, s>>>(n, dinv, t, x, d, (T)cc.a1[i], (T)cc.a2[i]);
+      cheb_step_kernel<T><<<g, 256, 0, s>>>(n, nb, dinv, t, x, d, (T)cc.a1[i], (T)cc.a2[i]);
       HDG_CUDA_TRY(cudaGetLastError());
       rsrc = t;
     }
@@ -500,110 +522,109 @@ static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x
 // Alg. 1 on the h-levels: level l = -1 is the p = 0 HDG space, l >= 0 the Q1
 // levels (finest first); the last Q1 level is solved directly.
 template <typename T>
-static cudaError_t hmg(Context* c, int prec, int l, const T* r, T* x, cudaStream_t s) {
+static cudaError_t hmg(Context* c, VWork& w, int prec, int l, const T* r, T* x, cudaStream_t s) {
   const int nh = (int)c->hlev.size();
+  const int nb = w.nb;
   if (l == nh - 1) {
     HLevel& H = c->hlev[l];
-    coarse_solve_kernel<T><<<1, 256, 0, s>>>(H.nv, c->coarse_L, r, x, c->coarse_rhs);
+    coarse_solve_kernel<T><<<nb, 256, 0, s>>>(H.nv, nb, c->coarse_L, r, x, w.coarse_w);
     return cudaGetLastError();
   }
   const bool p0 = (l < 0);
   HLevel* H = p0 ? nullptr : &c->hlev[l];
-  PLevel& L0 = c->plev[0];
-  T *t, *d;
-  if (p0) {
-    t = (T*)(prec_double(prec) ? (void*)L0.t64 : (void*)L0.t32);
-    d = (T*)(prec_double(prec) ? (void*)L0.d64 : (void*)L0.d32);
-  } else {
-    t = (T*)(prec_double(prec) ? (void*)H->t64 : (void*)H->t32);
-    d = (T*)(prec_double(prec) ? (void*)H->d64 : (void*)H->d32);
-  }
-  HDG_CUDA_TRY(cheb_smooth<T>(c, prec, H, r, x, t, d, true, c->opt.nu1, s));
+  T* t = (T*)(p0 ? w.pt[0] : w.ht[l]);
+  T* d = (T*)(p0 ? w.p0d : w.hd[l]);
+  HDG_CUDA_TRY(cheb_smooth<T>(c, prec, H, r, x, t, d, true, c->opt.nu1, nb, s));
   // residual and restriction to the next (coarser) Q1 level
   HLevel& Hc = c->hlev[l + 1];
-  T* rc = (T*)(prec_double(prec) ? (void*)Hc.r64 : (void*)Hc.r32);
-  T* xc = (T*)(prec_double(prec) ? (void*)Hc.x64 : (void*)Hc.x32);
+  T* rc = (T*)w.hr[l + 1];
+  T* xc = (T*)w.hx[l + 1];
   if (p0) {
-    HDG_CUDA_TRY(p0_apply(c, prec == HDG_PREC_BF16 ? HDG_PREC_FP32 : prec, x, r, t, -1.0, 1.0, s));
-    restrict_J_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, t, rc);
+    HDG_CUDA_TRY(p0_apply(c, prec == HDG_PREC_BF16 ? HDG_PREC_FP32 : prec, x, r, t, -1.0, 1.0, nb, s));
+    restrict_J_kernel<T><<<grid_for((size_t)Hc.nv * nb), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, nb, t, rc);
   } else {
     const T* st = (const T*)(prec_double(prec) ? (const void*)H->st64 : (const void*)H->st32);
-    HDG_CUDA_TRY(q_apply<T>(*H, st, x, r, t, -1.0, 1.0, s));
-    restrict_q_kernel<T><<<grid_for(Hc.nv), 256, 0, s>>>(Hc.nx, Hc.ny, t, rc);
+    HDG_CUDA_TRY(q_apply<T>(*H, st, x, r, t, -1.0, 1.0, nb, s));
+    restrict_q_kernel<T><<<grid_for((size_t)Hc.nv * nb), 256, 0, s>>>(Hc.nx, Hc.ny, nb, t, rc);
   }
   HDG_CUDA_TRY(cudaGetLastError());
-  HDG_CUDA_TRY(hmg<T>(c, prec, l + 1, rc, xc, s));
-  if (p0) prolong_J_add_kernel<T><<<grid_for(c->n_edges), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, xc, x);
-  else prolong_q_add_kernel<T><<<grid_for(H->nv), 256, 0, s>>>(Hc.nx, Hc.ny, xc, x);
+  HDG_CUDA_TRY(hmg<T>(c, w, prec, l + 1, rc, xc, s));
+  if (p0)
+    prolong_J_add_kernel<T><<<grid_for((size_t)c->n_edges * nb), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, nb, xc, x);
+  else
+    prolong_q_add_kernel<T><<<grid_for((size_t)H->nv * nb), 256, 0, s>>>(Hc.nx, Hc.ny, nb, xc, x);
   HDG_CUDA_TRY(cudaGetLastError());
-  return cheb_smooth<T>(c, prec, H, r, x, t, d, false, c->opt.nu2, s);
+  return cheb_smooth<T>(c, prec, H, r, x, t, d, false, c->opt.nu2, nb, s);
 }
 
 // Alg. 2 on p-level p >= 1 (zero initial guess): r, x are level-p vectors.
 template <typename T>
-static cudaError_t pmg(Context* c, int prec, int p, const T* r, T* x, cudaStream_t s) {
+static cudaError_t pmg(Context* c, VWork& w, int prec, int p, const T* r, T* x, cudaStream_t s) {
   PLevel& L = c->plev[p];
   PLevel& Lc = c->plev[p - 1];
-  T* t = (T*)(prec_double(prec) ? (void*)L.t64 : (void*)L.t32);
+  const int nb = w.nb;
+  T* t = (T*)w.pt[p];
   const int nu1 = c->opt.nu1, nu2 = c->opt.nu2;
   // pre-smoothing: x = M r, then x += M (r - A x)
-  HDG_CUDA_TRY(launch_apply(c, p, 1, prec, r, nullptr, x, 1.0, 0.0, 1, s));
+  HDG_CUDA_TRY(launch_apply(c, p, 1, prec, r, nullptr, x, 1.0, 0.0, nb, s));
   for (int i = 1; i < nu1; ++i) {
-    HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
-    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, 1, s));
+    HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, nb, s));
+    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, nb, s));
   }
   // restricted residual; a BF16 cycle takes it with the FP32 blocks: its smooth
   // part drives the coarse correction, and BF16 rounding (2^-9) of the blocks
   // would swamp it on fine meshes
   const int rprec = prec == HDG_PREC_BF16 ? HDG_PREC_FP32 : prec;
-  HDG_CUDA_TRY(launch_apply(c, p, 0, rprec, x, r, t, -1.0, 1.0, 1, s));
-  T* rc = (T*)(prec_double(prec) ? (void*)Lc.r64 : (void*)Lc.r32);
-  T* xc = (T*)(prec_double(prec) ? (void*)Lc.x64 : (void*)Lc.x32);
-  restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1), 256, 0, s>>>(c->n_edges, Lc.n1, L.Pp, t, rc);
+  HDG_CUDA_TRY(launch_apply(c, p, 0, rprec, x, r, t, -1.0, 1.0, nb, s));
+  T* rc = (T*)w.pr[p - 1];
+  T* xc = (T*)w.px[p - 1];
+  restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, L.Pp, t, rc);
   HDG_CUDA_TRY(cudaGetLastError());
-  if (p - 1 == 0) HDG_CUDA_TRY(hmg<T>(c, prec, -1, rc, xc, s));
-  else HDG_CUDA_TRY(pmg<T>(c, prec, p - 1, rc, xc, s));
-  prolong_p_add_kernel<T><<<grid_for((size_t)c->n_edges * L.n1), 256, 0, s>>>(c->n_edges, Lc.n1, L.Pp, xc, x);
+  if (p - 1 == 0) HDG_CUDA_TRY(hmg<T>(c, w, prec, -1, rc, xc, s));
+  else HDG_CUDA_TRY(pmg<T>(c, w, prec, p - 1, rc, xc, s));
+  prolong_p_add_kernel<T><<<grid_for((size_t)c->n_edges * L.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, L.Pp, xc, x);
   HDG_CUDA_TRY(cudaGetLastError());
   for (int i = 0; i < nu2; ++i) {
-    HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, 1, s));
-    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, 1, s));
+    HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, nb, s));
+    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, nb, s));
   }
   return cudaSuccess;
 }
 
-// V-cycle body on the context's top-level buffers r -> x of level k.
+// V-cycle body on the work's top-level buffers r -> x of level k.
 template <typename T>
-static cudaError_t vcycle_body(Context* c, int prec, cudaStream_t s) {
-  PLevel& L = c->plev[c->k];
-  const T* r = (const T*)(prec_double(prec) ? (void*)L.r64 : (void*)L.r32);
-  T* x = (T*)(prec_double(prec) ? (void*)L.x64 : (void*)L.x32);
-  if (c->k == 0) return hmg<T>(c, prec, -1, r, x, s);
-  return pmg<T>(c, prec, c->k, r, x, s);
+static cudaError_t vcycle_body(Context* c, VWork& w, int prec, cudaStream_t s) {
+  const T* r = (const T*)w.pr[c->k];
+  T* x = (T*)w.px[c->k];
+  if (c->k == 0) return hmg<T>(c, w, prec, -1, r, x, s);
+  return pmg<T>(c, w, prec, c->k, r, x, s);
 }
 
-static cudaError_t vcycle_body_any(Context* c, int prec, cudaStream_t s) {
-  if (prec_double(prec)) return vcycle_body<double>(c, prec, s);
-  return vcycle_body<float>(c, prec, s);
+static cudaError_t vcycle_body_any(Context* c, VWork& w, int prec, cudaStream_t s) {
+  if (prec_double(prec)) return vcycle_body<double>(c, w, prec, s);
+  return vcycle_body<float>(c, w, prec, s);
 }
 
-// z = V r. r and z are double for FP64, float otherwise (device, [ndof]).
-cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_double, cudaStream_t s) {
-  PLevel& L = c->plev[c->k];
-  const size_t n = (size_t)c->ndof;
+// z = V r on work w. r and z are double for FP64 / F32X2, float otherwise
+// (device, [ndof][w.nb]); r_double: r and z are double for a float cycle.
+static cudaError_t vcycle_typed(Context* c, VWork& w, int prec, const void* r, void* z, bool r_double,
+                                cudaStream_t s) {
+  const size_t n = (size_t)c->ndof * w.nb;
   const int g = grid_for(n);
+  void* wr = w.pr[c->k];
+  void* wx = w.px[c->k];
   if (prec_double(prec)) {
-    HDG_CUDA_TRY(cudaMemcpyAsync(L.r64, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HDG_CUDA_TRY(cudaMemcpyAsync(wr, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else if (r_double) {
-    copy_convert_kernel<double, float><<<g, 256, 0, s>>>(n, (const double*)r, L.r32);
+    copy_convert_kernel<double, float><<<g, 256, 0, s>>>(n, (const double*)r, (float*)wr);
     HDG_CUDA_TRY(cudaGetLastError());
   } else {
-    HDG_CUDA_TRY(cudaMemcpyAsync(L.r32, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    HDG_CUDA_TRY(cudaMemcpyAsync(wr, r, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
   }
   const int gi = prec;
   if (c->opt.use_graphs) {
-    if (c->vc_graph[gi] == nullptr || c->vc_graph_stream[gi] != s) {
-      if (c->vc_graph[gi]) { cudaGraphExecDestroy(c->vc_graph[gi]); c->vc_graph[gi] = nullptr; }
+    if (w.graph[gi] == nullptr || w.gstream[gi] != s) {
+      if (w.graph[gi]) { cudaGraphExecDestroy(w.graph[gi]); w.graph[gi] = nullptr; }
       cudaStream_t cap = s;
       bool own = false;
       if (cap == 0) {  // the legacy stream cannot be captured: capture on a private stream
@@ -612,12 +633,12 @@ cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_do
       }
       cudaGraph_t g0;
       HDG_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      cudaError_t eb = vcycle_body_any(c, prec, cap);
+      cudaError_t eb = vcycle_body_any(c, w, prec, cap);
       cudaError_t ee = cudaStreamEndCapture(cap, &g0);
       if (own) cudaStreamDestroy(cap);
       HDG_CUDA_TRY(eb);
       HDG_CUDA_TRY(ee);
-      HDG_CUDA_TRY(cudaGraphInstantiate(&c->vc_graph[gi], g0, 0));
+      HDG_CUDA_TRY(cudaGraphInstantiate(&w.graph[gi], g0, 0));
       size_t nn = 0;
       HDG_CUDA_TRY(cudaGraphGetNodes(g0, nullptr, &nn));
       std::vector<cudaGraphNode_t> nodes(nn);
@@ -630,25 +651,139 @@ cudaError_t vcycle_typed(Context* c, int prec, const void* r, void* z, bool r_do
       }
       c->vcycle_kernels = nk;
       cudaGraphDestroy(g0);
-      c->vc_graph_stream[gi] = s;
+      w.gstream[gi] = s;
     }
-    HDG_CUDA_TRY(cudaGraphLaunch(c->vc_graph[gi], s));
+    HDG_CUDA_TRY(cudaGraphLaunch(w.graph[gi], s));
   } else {
-    HDG_CUDA_TRY(vcycle_body_any(c, prec, s));
+    HDG_CUDA_TRY(vcycle_body_any(c, w, prec, s));
   }
   if (prec_double(prec)) {
-    HDG_CUDA_TRY(cudaMemcpyAsync(z, L.x64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HDG_CUDA_TRY(cudaMemcpyAsync(z, wx, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   } else if (r_double) {
-    copy_convert_kernel<float, double><<<g, 256, 0, s>>>(n, L.x32, (double*)z);
+    copy_convert_kernel<float, double><<<g, 256, 0, s>>>(n, (const float*)wx, (double*)z);
     HDG_CUDA_TRY(cudaGetLastError());
   } else {
-    HDG_CUDA_TRY(cudaMemcpyAsync(z, L.x32, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    HDG_CUDA_TRY(cudaMemcpyAsync(z, wx, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
   }
   return cudaSuccess;
 }
 
-cudaError_t vcycle(Context* c, int prec, const void* r, void* z, cudaStream_t s) {
-  return vcycle_typed(c, prec, r, z, false, s);
+// ---------------------------------------------------------------------------
+// Works: the single-vector ones point into the levels' buffers; batched ones
+// are allocated when first asked for with a given nb (and replaced when nb
+// changes).
+static void release_work(VWork& w) {
+  for (int g = 0; g < 4; ++g) {
+    if (w.graph[g]) cudaGraphExecDestroy(w.graph[g]);
+    w.graph[g] = nullptr;
+    w.gstream[g] = nullptr;
+  }
+  for (void* p : w.own) cudaFree(p);
+  w.own.clear();
+  if (w.h_sc) cudaFreeHost(w.h_sc);
+  w.h_sc = nullptr;
+}
+
+void release_works(Context* c) {
+  for (int f = 0; f < 2; ++f) {
+    release_work(c->w1[f]);
+    if (c->wb[f]) {
+      release_work(*c->wb[f]);
+      delete c->wb[f];
+      c->wb[f] = nullptr;
+    }
+  }
+}
+
+static void single_works(Context* c) {
+  for (int f = 0; f < 2; ++f) {
+    VWork& w = c->w1[f];
+    const bool dbl = (f == 0);
+    w.nb = 1;
+    w.dbl = dbl;
+    w.pr.clear(); w.px.clear(); w.pt.clear();
+    for (int p = 0; p <= c->k; ++p) {
+      PLevel& L = c->plev[p];
+      w.pr.push_back(dbl ? (void*)L.r64 : (void*)L.r32);
+      w.px.push_back(dbl ? (void*)L.x64 : (void*)L.x32);
+      w.pt.push_back(dbl ? (void*)L.t64 : (void*)L.t32);
+    }
+    w.p0d = dbl ? (void*)c->plev[0].d64 : (void*)c->plev[0].d32;
+    w.hr.clear(); w.hx.clear(); w.ht.clear(); w.hd.clear();
+    for (HLevel& H : c->hlev) {
+      w.hr.push_back(dbl ? (void*)H.r64 : (void*)H.r32);
+      w.hx.push_back(dbl ? (void*)H.x64 : (void*)H.x32);
+      w.ht.push_back(dbl ? (void*)H.t64 : (void*)H.t32);
+      w.hd.push_back(dbl ? (void*)H.d64 : (void*)H.d32);
+    }
+    w.coarse_w = c->coarse_rhs;
+  }
+}
+
+static void* work_alloc(VWork* w, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  w->own.push_back(p);
+  return p;
+}
+
+// the batched CG vectors and scalars of a work (allocated once)
+static cudaError_t work_cg(Context* c, VWork* w) {
+  if (w->cg_r) return cudaSuccess;
+  const size_t n = (size_t)c->ndof * w->nb * sizeof(double);
+  w->cg_r = (double*)work_alloc(w, n); w->cg_z = (double*)work_alloc(w, n);
+  w->cg_p = (double*)work_alloc(w, n); w->cg_q = (double*)work_alloc(w, n);
+  w->cg_zold = (double*)work_alloc(w, n);
+  w->cg_sc = (double*)work_alloc(w, (size_t)kCgScalars * w->nb * sizeof(double));
+  w->cg_part = (double*)work_alloc(w, (size_t)2 * kRedBlocks * w->nb * sizeof(double));
+  bool ok = w->cg_r && w->cg_z && w->cg_p && w->cg_q && w->cg_zold && w->cg_sc && w->cg_part;
+  if (ok) ok = cudaMallocHost((void**)&w->h_sc, 3 * (size_t)w->nb * sizeof(double)) == cudaSuccess;
+  if (!ok) { cudaGetLastError(); w->cg_r = nullptr; return cudaErrorMemoryAllocation; }
+  return cudaSuccess;
+}
+
+static cudaError_t batched_work(Context* c, int nb, bool dbl, VWork** out) {
+  const int f = dbl ? 0 : 1;
+  if (c->wb[f] && c->wb[f]->nb == nb) { *out = c->wb[f]; return cudaSuccess; }
+  if (c->wb[f]) { release_work(*c->wb[f]); delete c->wb[f]; c->wb[f] = nullptr; }
+  VWork* w = new VWork();
+  w->nb = nb;
+  w->dbl = dbl;
+  const size_t es = dbl ? sizeof(double) : sizeof(float);
+  bool ok = true;
+  for (int p = 0; p <= c->k && ok; ++p) {
+    const size_t n = (size_t)c->n_edges * c->plev[p].n1 * nb * es;
+    void *a = work_alloc(w, n), *b = work_alloc(w, n), *d = work_alloc(w, n);
+    ok = a && b && d;
+    w->pr.push_back(a); w->px.push_back(b); w->pt.push_back(d);
+  }
+  if (ok) { w->p0d = work_alloc(w, (size_t)c->n_edges * nb * es); ok = w->p0d != nullptr; }
+  for (size_t l = 0; l < c->hlev.size() && ok; ++l) {
+    const size_t n = (size_t)c->hlev[l].nv * nb * es;
+    void *a = work_alloc(w, n), *b = work_alloc(w, n), *d = work_alloc(w, n), *e = work_alloc(w, n);
+    ok = a && b && d && e;
+    w->hr.push_back(a); w->hx.push_back(b); w->ht.push_back(d); w->hd.push_back(e);
+  }
+  if (ok) {
+    w->coarse_w = (double*)work_alloc(w, (size_t)c->coarse_dim * nb * sizeof(double));
+    ok = w->coarse_w != nullptr;
+  }
+  if (!ok) {
+    release_work(*w);
+    delete w;
+    return cudaErrorMemoryAllocation;
+  }
+  c->wb[f] = w;
+  *out = w;
+  return cudaSuccess;
+}
+
+cudaError_t vcycle(Context* c, int prec, const void* r, void* z, int nb, cudaStream_t s) {
+  const bool dbl = prec_double(prec);
+  if (nb == 1) return vcycle_typed(c, c->w1[dbl ? 0 : 1], prec, r, z, false, s);
+  VWork* w = nullptr;
+  HDG_CUDA_TRY(batched_work(c, nb, dbl, &w));
+  return vcycle_typed(c, *w, prec, r, z, false, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -687,8 +822,8 @@ static cudaError_t power_iteration(Context* c, HLevel* H, double* out, cudaStrea
   HDG_CUDA_TRY(cudaGetLastError());
   double lam = 0.0;
   for (int it = 0; it < 10; ++it) {
-    if (p0) HDG_CUDA_TRY(p0_apply(c, HDG_PREC_FP64, x, nullptr, y, 1.0, 0.0, s));
-    else HDG_CUDA_TRY(q_apply<double>(*H, H->st64, x, nullptr, y, 1.0, 0.0, s));
+    if (p0) HDG_CUDA_TRY(p0_apply(c, HDG_PREC_FP64, x, nullptr, y, 1.0, 0.0, 1, s));
+    else HDG_CUDA_TRY(q_apply<double>(*H, H->st64, x, nullptr, y, 1.0, 0.0, 1, s));
     mul_kernel<double><<<g, 256, 0, s>>>(n, y, dinv, y);
     HDG_CUDA_TRY(cudaGetLastError());
     HDG_CUDA_TRY(dots<double>(c, n, y, y, nullptr, nullptr, nullptr, nullptr, sc, s));
@@ -775,7 +910,9 @@ cudaError_t build_hierarchy(Context* c, cudaStream_t s) {
   dense_from_stencil_kernel<<<1, 256, 0, s>>>(Hc.nx, Hc.ny, Hc.st64, c->coarse_L);
   HDG_CUDA_TRY(cudaGetLastError());
   cholesky_block_kernel<<<1, 256, 0, s>>>(nc, c->coarse_L, c->err_flag);
-  return cudaGetLastError();
+  HDG_CUDA_TRY(cudaGetLastError());
+  single_works(c);
+  return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -827,7 +964,7 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
     if (info) info->relres = 0.0;
     return (bn == 0.0) ? HDG_OK : HDG_ERR_INVALID_ARG;
   }
-  CK(vcycle_typed(c, inner, r, z, true, s));
+  CK(vcycle_typed(c, c->w1[prec_double(inner) ? 0 : 1], inner, r, z, true, s));
   CK(dots<double>(c, n, r, z, nullptr, nullptr, nullptr, nullptr, sc + 0, s));
   CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   int it = 0;
@@ -848,7 +985,7 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
     if (!std::isfinite(rel)) { status = HDG_ERR_BREAKDOWN; break; }
     if (rel <= rtol) { status = HDG_OK; break; }
     if (flexible) CK(cudaMemcpyAsync(zold, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    CK(vcycle_typed(c, inner, r, z, true, s));
+    CK(vcycle_typed(c, c->w1[prec_double(inner) ? 0 : 1], inner, r, z, true, s));
     if (flexible) CK(dots<double>(c, n, r, z, r, zold, nullptr, nullptr, sc + 8, s));
     else CK(dots<double>(c, n, r, z, nullptr, nullptr, nullptr, nullptr, sc + 8, s));
     cg_p_kernel<<<g, 256, 0, s>>>(n, sc, z, p, flexible ? 1 : 0);
@@ -859,6 +996,195 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
 #undef CK
   if (it > maxit) it = maxit;
   if (info) { info->iterations = it; info->relres = rel; }
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// Batched CG: nb right-hand sides, vectors [n][nb], per-column scalars in
+// sc[slot * nb + col]:
+//   0 rz  1 pq  2 rr (first: bb)  3 r.zold  4 |b|  5 relres  6 active  7 breakdown
+//   8 rz_new  9 alpha  10 beta
+enum { kRz = 0, kPq, kRr, kRzOld, kBn, kRel, kAct, kErr, kRzNew, kAlpha, kBeta };
+
+// per-column dot products of [n][nb] arrays (deterministic: fixed grid, fixed
+// order): part[(q * gridDim.x + block) * nb + col]
+__global__ void cdots_kernel(size_t n, int nb, const double* __restrict__ a0, const double* __restrict__ b0,
+                             const double* __restrict__ a1, const double* __restrict__ b1,
+                             double* __restrict__ part) {
+  __shared__ double sh[2][256];
+  const int cw = nb < 256 ? nb : 256;
+  const int rl = 256 / cw;
+  const int lc = threadIdx.x % cw, rowl = threadIdx.x / cw;
+  for (int col0 = 0; col0 < nb; col0 += cw) {
+    const int col = col0 + lc;
+    double s0 = 0.0, s1 = 0.0;
+    if (rowl < rl && col < nb) {
+      for (size_t i = (size_t)blockIdx.x * rl + rowl; i < n; i += (size_t)gridDim.x * rl) {
+        const size_t o = i * nb + col;
+        s0 += a0[o] * b0[o];
+        if (a1) s1 += a1[o] * b1[o];
+      }
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    __syncthreads();
+    if (rowl == 0 && col < nb) {
+      double t0 = 0.0, t1 = 0.0;
+      for (int q = 0; q < rl; ++q) { t0 += sh[0][q * cw + lc]; t1 += sh[1][q * cw + lc]; }
+      part[(size_t)blockIdx.x * nb + col] = t0;
+      part[((size_t)gridDim.x + blockIdx.x) * nb + col] = t1;
+    }
+    __syncthreads();
+  }
+}
+__global__ void cdots_finalize_kernel(int nb, int nblk, const double* __restrict__ part, double* __restrict__ out0,
+                                      double* __restrict__ out1) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= nb) return;
+  double t0 = 0.0, t1 = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    t0 += part[(size_t)b * nb + col];
+    if (out1) t1 += part[((size_t)nblk + b) * nb + col];
+  }
+  out0[col] = t0;
+  if (out1) out1[col] = t1;
+}
+static cudaError_t cdots(VWork* w, size_t n, const double* a0, const double* b0, const double* a1,
+                         const double* b1, double* out0, double* out1, cudaStream_t s) {
+  cdots_kernel<<<kRedBlocks, 256, 0, s>>>(n, w->nb, a0, b0, a1, b1, w->cg_part);
+  HDG_CUDA_TRY(cudaGetLastError());
+  cdots_finalize_kernel<<<(w->nb + 255) / 256, 256, 0, s>>>(w->nb, kRedBlocks, w->cg_part, out0, out1);
+  return cudaGetLastError();
+}
+
+__global__ void cgb_init_kernel(int nb, double* __restrict__ sc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const double bn = sqrt(sc[kRr * nb + j]);
+  sc[kBn * nb + j] = bn;
+  sc[kAct * nb + j] = bn > 0.0 ? 1.0 : 0.0;
+  sc[kRel * nb + j] = bn > 0.0 ? 1.0 : 0.0;
+  sc[kErr * nb + j] = 0.0;
+  sc[kAlpha * nb + j] = 0.0;
+  sc[kBeta * nb + j] = 0.0;
+}
+__global__ void cgb_alpha_kernel(int nb, double* __restrict__ sc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double a = 0.0;
+  if (sc[kAct * nb + j] != 0.0) {
+    const double pq = sc[kPq * nb + j];
+    if (pq > 0.0 && isfinite(pq)) {
+      a = sc[kRz * nb + j] / pq;
+    } else {
+      sc[kErr * nb + j] = 1.0;
+      sc[kAct * nb + j] = 0.0;
+    }
+  }
+  sc[kAlpha * nb + j] = a;
+}
+__global__ void cgb_xr_kernel(size_t n, int nb, const double* __restrict__ sc, const double* __restrict__ p,
+                              const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
+  const double* al = sc + kAlpha * nb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const double a = al[t % nb];
+    if (a != 0.0) {
+      x[t] += a * p[t];
+      r[t] -= a * q[t];
+    }
+  }
+}
+__global__ void cgb_status_kernel(int nb, double* __restrict__ sc, double rtol) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  if (sc[kAct * nb + j] == 0.0) return;
+  const double rel = sqrt(sc[kRr * nb + j]) / sc[kBn * nb + j];
+  sc[kRel * nb + j] = rel;
+  if (!isfinite(rel)) { sc[kErr * nb + j] = 1.0; sc[kAct * nb + j] = 0.0; }
+  else if (rel <= rtol) sc[kAct * nb + j] = 0.0;
+}
+__global__ void cgb_beta_kernel(int nb, double* __restrict__ sc, int flexible) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  double b = 0.0;
+  if (sc[kAct * nb + j] != 0.0) {
+    const double rzn = sc[kRzNew * nb + j];
+    b = (flexible ? rzn - sc[kRzOld * nb + j] : rzn) / sc[kRz * nb + j];
+    sc[kRz * nb + j] = rzn;
+  }
+  sc[kBeta * nb + j] = b;
+}
+__global__ void cgb_p_kernel(size_t n, int nb, const double* __restrict__ sc, const double* __restrict__ z,
+                             double* __restrict__ p) {
+  const double* act = sc + kAct * nb;
+  const double* be = sc + kBeta * nb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % nb);
+    if (act[j] != 0.0) p[t] = z[t] + be[j] * p[t];
+  }
+}
+
+int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rtol, int maxit, int inner,
+                      hdg_solve_info* info, cudaStream_t s) {
+  VWork* w = nullptr;
+  if (batched_work(c, nb, prec_double(inner), &w) != cudaSuccess) return HDG_ERR_OOM;
+  if (work_cg(c, w) != cudaSuccess) return HDG_ERR_OOM;
+  const size_t n = (size_t)c->ndof * nb;
+  const int g = grid_for(n);
+  const int gs = (nb + 255) / 256;
+  double *r = w->cg_r, *z = w->cg_z, *p = w->cg_p, *q = w->cg_q, *zold = w->cg_zold, *sc = w->cg_sc;
+  double* h = w->h_sc;
+  const bool flexible = inner != HDG_PREC_FP64;
+  const int outer = (inner == HDG_PREC_FP64) ? HDG_PREC_FP64 : HDG_PREC_F32X2;
+  auto S = [&](int slot) { return sc + (size_t)slot * nb; };
+#define CK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return HDG_ERR_CUDA; } while (0)
+  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cdots(w, (size_t)c->ndof, b, b, nullptr, nullptr, S(kRr), nullptr, s));
+  cgb_init_kernel<<<gs, 256, 0, s>>>(nb, sc);
+  CK(cudaGetLastError());
+  CK(vcycle_typed(c, *w, inner, r, z, true, s));
+  CK(cdots(w, (size_t)c->ndof, r, z, nullptr, nullptr, S(kRz), nullptr, s));
+  CK(cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (info) { info->iterations = 0; info->relres = 0.0; info->relres_history[0] = 1.0; }
+  int it = 0;
+  double relmax = 0.0;
+  int status = HDG_ERR_NOT_CONVERGED;
+  for (it = 1; it <= maxit; ++it) {
+    CK(launch_apply(c, c->k, 0, outer, p, nullptr, q, 1.0, 0.0, nb, s));
+    CK(cdots(w, (size_t)c->ndof, p, q, nullptr, nullptr, S(kPq), nullptr, s));
+    cgb_alpha_kernel<<<gs, 256, 0, s>>>(nb, sc);
+    CK(cudaGetLastError());
+    cgb_xr_kernel<<<g, 256, 0, s>>>(n, nb, sc, p, q, x, r);
+    CK(cudaGetLastError());
+    CK(cdots(w, (size_t)c->ndof, r, r, nullptr, nullptr, S(kRr), nullptr, s));
+    cgb_status_kernel<<<gs, 256, 0, s>>>(nb, sc, rtol);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h, S(kRel), 3 * (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    relmax = 0.0;
+    int active = 0, err = 0;
+    for (int j = 0; j < nb; ++j) {
+      relmax = std::max(relmax, h[j]);
+      active += h[nb + j] != 0.0;
+      err += h[2 * nb + j] != 0.0;
+    }
+    if (info && it < 256) info->relres_history[it] = relmax;
+    if (err) { status = HDG_ERR_BREAKDOWN; break; }
+    if (active == 0) { status = HDG_OK; break; }
+    if (it == maxit) break;
+    if (flexible) CK(cudaMemcpyAsync(zold, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(vcycle_typed(c, *w, inner, r, z, true, s));
+    if (flexible) CK(cdots(w, (size_t)c->ndof, r, z, r, zold, S(kRzNew), S(kRzOld), s));
+    else CK(cdots(w, (size_t)c->ndof, r, z, nullptr, nullptr, S(kRzNew), nullptr, s));
+    cgb_beta_kernel<<<gs, 256, 0, s>>>(nb, sc, flexible ? 1 : 0);
+    CK(cudaGetLastError());
+    cgb_p_kernel<<<g, 256, 0, s>>>(n, nb, sc, z, p);
+    CK(cudaGetLastError());
+  }
+#undef CK
+  if (it > maxit) it = maxit;
+  if (info) { info->iterations = it; info->relres = relmax; }
   return status;
 }
 

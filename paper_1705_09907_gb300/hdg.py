@@ -227,10 +227,14 @@ class HDGSolver:
         return z
 
     def solve(self, b, rtol=1e-10, maxit=200, inner="fp64", out=None, raise_on_error=True):
+        """b: [ndof] or [ndof, nrhs] (right-hand side fastest); for nrhs > 1 all
+        columns iterate together and `iterations` / `relres` are the largest
+        over the columns."""
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
         lam = torch.empty_like(b) if out is None else out
         inf = hdg_solve_info()
-        st = _lib.hdg_solve(self.ctx, _ptr(b, torch.float64), _ptr(lam, torch.float64), 1, float(rtol), int(maxit),
-                            PREC[inner], ctypes.byref(inf), _stream())
+        st = _lib.hdg_solve(self.ctx, _ptr(b, torch.float64), _ptr(lam, torch.float64), nrhs, float(rtol),
+                            int(maxit), PREC[inner], ctypes.byref(inf), _stream())
         info = {"status": st, "iterations": inf.iterations, "relres": inf.relres, "solve_ms": inf.solve_ms,
                 "history": list(inf.relres_history[: min(inf.iterations, 255) + 1])}
         if raise_on_error:
