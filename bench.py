@@ -266,6 +266,67 @@ def run_ours(args):
               "TFLOPs": fl4 / (ms4 * 1e-3) / 1e12, "algorithmic_bytes": algo4, "flops": fl4,
               "kernel": "batched_apply_kernel (tcgen05.mma kind::f16, BF16 x BF16 -> FP32 TMEM)"}
         sbs.close()
+    # many right-hand sides in one solve: 256 x 256, k = 5, kappa = 1, 64 Fourier
+    # sources (seed 3); batched CG (one batched apply and V-cycle per iteration)
+    # against plain FP64 solves one right-hand side at a time on the same mesh
+    bs = {}
+    if not args.profile:
+        Nb, kb, nr = 256, 5, 64
+        sbm = hdg.HDGSolver(Nb, Nb, kb, torch.ones(Nb * Nb, dtype=torch.float64, device="cuda"))
+        B = sbm.condense_rhs(torch.as_tensor(inputs.fourier_rhs(Nb, kb, nr, seed=3), device="cuda"))
+        LB = torch.empty_like(B)
+        lam1 = torch.empty(sbm.ndof, dtype=torch.float64, device="cuda")
+        b0 = B[:, 0].contiguous()
+        sbm.solve(b0, rtol=rtol, maxit=400, out=lam1)
+        single = timed_events(lambda: sbm.solve(b0, rtol=rtol, maxit=400, out=lam1), 3, torch)
+        its1 = sbm.solve(b0, rtol=rtol, maxit=400, out=lam1)[1]["iterations"]
+        bs = {"workload": "256x256 k=5 kappa=1, 64 Fourier right-hand sides (seed 3), rtol 1e-10",
+              "plain_fp64_ms_per_rhs": single, "plain_fp64_iterations": its1}
+        for inner in ("fp32", "fp64"):
+            sbm.solve(B, rtol=rtol, maxit=400, inner=inner, out=LB)
+            msb = timed_events(lambda: sbm.solve(B, rtol=rtol, maxit=400, inner=inner, out=LB), 1 if inner == "fp64" else 3, torch)
+            inf = sbm.solve(B, rtol=rtol, maxit=400, inner=inner, out=LB)[1]
+            bs["batched_" + inner] = {"ms_per_batch": msb, "ms_per_rhs": msb / nr, "iterations": inf["iterations"],
+                                      "max_relres": inf["relres"], "speedup_per_rhs_vs_plain_fp64": single / (msb / nr),
+                                      "rel_diff_col0_vs_plain_fp64": float(torch.linalg.norm(LB[:, 0] - lam1) /
+                                                                            torch.linalg.norm(lam1))}
+        # the column-batched record apply at level k (S read once for all 64 columns)
+        X64 = B.clone()
+        Y64 = torch.empty_like(X64)
+        X32 = B.float()
+        Y32 = torch.empty_like(X32)
+        nelb, neb, n1b = sbm.nel, sbm.n_edges, kb + 1
+        cols = {}
+        for p_, xx, yy, bs_, bx_ in (("fp64", X64, Y64, 8, 8), ("f32x2", X64, Y64, 8, 8), ("fp32", X32, Y32, 4, 4),
+                                     ("bf16", X32, Y32, 2, 4)):
+            sbm.apply(xx, p_, out=yy)
+            msc = timed_events(lambda: sbm.apply(xx, p_, out=yy), args.apply_reps, torch)
+            algo = nelb * 16 * n1b * n1b * bs_ + 2 * neb * n1b * nr * bx_
+            fl = 2.0 * nelb * 16 * n1b * n1b * nr
+            cols[p_] = {"ms": msc, "GBps": algo / (msc * 1e-3) / 1e9,
+                        "frac_hbm": algo / (msc * 1e-3) / 1e9 / peaks["hbm_gbs"], "TFLOPs": fl / (msc * 1e-3) / 1e12,
+                        "algorithmic_bytes": algo}
+        bs["column_apply_64rhs"] = cols
+        sbm.close()
+    # mixed precision at 1024 x 1024, k = 3 (lognormal kappa, seed 0, f = 1):
+    # solve time to 1e-10 per V-cycle precision against plain FP64
+    m3 = {}
+    if not args.profile:
+        N3, k3 = 1024, 3
+        s3 = hdg.HDGSolver(N3, N3, k3, torch.as_tensor(inputs.lognormal_kappa(N3, SEED), device="cuda"))
+        b3 = s3.condense_rhs(torch.as_tensor(inputs.constant_f(N3, k3), device="cuda"))
+        l3 = torch.empty_like(b3)
+        l64 = None
+        m3 = {"workload": "1024x1024 k=3 lognormal kappa (seed 0), f=1, rtol 1e-10", "setup_ms": s3.info["setup_ms"]}
+        for inner in ("fp64", "fp32", "bf16", "f32x2"):
+            s3.solve(b3, rtol=rtol, maxit=400, inner=inner, out=l3)
+            ms3 = timed_events(lambda: s3.solve(b3, rtol=rtol, maxit=400, inner=inner, out=l3), 2, torch)
+            inf = s3.solve(b3, rtol=rtol, maxit=400, inner=inner, out=l3)[1]
+            if l64 is None:
+                l64 = l3.clone()
+            m3[inner] = {"ms_per_solve": ms3, "iterations": inf["iterations"], "relres": inf["relres"],
+                         "rel_diff_vs_fp64_solution": float(torch.linalg.norm(l3 - l64) / torch.linalg.norm(l64))}
+        s3.close()
     # uneven instances in one persistent launch: 12 meshes N in {64..512}, k in {2,3,4}
     # (seeded mix), kappa = 1, FP64 blocks; one hdg_apply_multi vs 12 single applies
     mi = {}
@@ -335,8 +396,8 @@ def run_ours(args):
     tflops = fp["flops"] / (apply_ms["fp64"] * 1e-3) / 1e12
     # FP64: 0.25 flop/byte needs more FP64 issue than the GPU has (1.25 TFLOP/s
     # nominal), so the FP64 apply is bound by the FP64 pipe, not by HBM.
-    # DRAM read+write of one FP64 level-k apply: ncu capture at 256 x 256 (218.8 MB,
-    # profiles/apply_k4_256_dram.md) scaled by the element count to 512 x 512
+    # DRAM read+write of one FP64 level-k apply: ncu capture at 256 x 256 (218.8 MB)
+    # scaled by the element count to 512 x 512
     traffic = 218.775e6 * (nel / 65536.0) if (N, k) == (512, 4) else None
     roof = {"kernel": "apply_kernel<5,double,double,double> (FP64 trace apply, level k)",
             "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": tflops / 1.25,
@@ -358,7 +419,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (FP64 S + Schwarz blocks %.0f MB)" % (2 * nel * 16 * n1 * n1 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
-        "roofline": roof, "trace_apply": tra, "mixed": mixed, "shared_batched_apply": sb, "multi_instance_apply": mi,
+        "roofline": roof, "trace_apply": tra, "mixed": mixed, "mixed_1024_k3": m3, "batched_solve": bs,
+        "shared_batched_apply": sb, "multi_instance_apply": mi,
         "e2e": {"value": 1000.0 / e2e_ms, "unit": "solve/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(fq_h.nbytes), "d2h_bytes_per_step": int(solver.ndof * 8 + u.numel() * 8)},
         "gpu_launches": int(launches_per_step * args.steps),
