@@ -212,6 +212,21 @@ def run_ours(args):
             sbs.apply_shared_batched(X4)
         torch.cuda.nvtx.range_pop()
         sbs.close()
+        # column-batched applies and one batched solve: 256 x 256, k = 5, kappa = 1,
+        # 64 Fourier right-hand sides; NVTX ranges cols_<prec> and batched_solve
+        sbm = hdg.HDGSolver(256, 256, 5, torch.ones(256 * 256, dtype=torch.float64, device="cuda"), autotune=0)
+        B = sbm.condense_rhs(torch.as_tensor(inputs.fourier_rhs(256, 5, 64, seed=3), device="cuda"))
+        B32 = B.float()
+        for p_, xx in (("fp64", B), ("f32x2", B), ("fp32", B32), ("bf16", B32)):
+            torch.cuda.nvtx.range_push("cols_" + p_)
+            for _ in range(3):
+                sbm.apply(xx, p_)
+            torch.cuda.nvtx.range_pop()
+        sbm.solve(B, rtol=1e-10, maxit=400, inner="fp32")
+        torch.cuda.nvtx.range_push("batched_solve")
+        sbm.solve(B, rtol=1e-10, maxit=400, inner="fp32")
+        torch.cuda.nvtx.range_pop()
+        sbm.close()
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": True, "iterations": last["info"]["iterations"],
                           "relres": last["info"]["relres"], "vcycle_kernels": solver.get_info()["vcycle_kernels"]}))

@@ -39,77 +39,117 @@ struct alignas(4 * sizeof(TS)) Quad {
   TS v[4];
 };
 
-template <int N1, typename TS, typename TV, typename TA, bool DIFF>
-__device__ __forceinline__ void cols_gather(const TV* __restrict__ v, int ki, int kj, int col, bool live,
-                                            const ColsArgs& a, TA (&xv)[4 * N1]) {
-  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny, nb = a.nb;
-  int edge[4];
-  bool bnd[4];
-  edge[0] = ki + (nx + 1) * kj;       bnd[0] = ki <= 0;
-  edge[1] = ki + 1 + (nx + 1) * kj;   bnd[1] = ki >= nx - 1;
-  edge[2] = nv + ki + nx * kj;        bnd[2] = kj <= 0;
-  edge[3] = nv + ki + nx * (kj + 1);  bnd[3] = kj >= ny - 1;
-#pragma unroll
-  for (int f = 0; f < 4; ++f)
-#pragma unroll
-    for (int b = 0; b < N1; ++b)
-      xv[f * N1 + b] = (bnd[f] || !live) ? TA{} : to_acc(v[((size_t)edge[f] * N1 + b) * nb + col], TA{});
-  if constexpr (DIFF) {
-    TA mean = TA(0);
-#pragma unroll
-    for (int c = 0; c < 4 * N1; ++c) mean += xv[c];
-    mean *= TA(1.0 / (4 * N1));
-#pragma unroll
-    for (int c = 0; c < 4 * N1; ++c) xv[c] -= mean;
-  }
-}
+// columns per lane: float accumulators take two (one block load feeds two
+// FMAs), the wider double / double-float accumulators one
+template <typename TA>
+struct ColsPerLane { static constexpr int value = sizeof(TA) == 4 ? 2 : 1; };
 
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
 __global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
   using TO = typename OutT<TA>::type;
   constexpr int M = ColsShape<N1>::M, R = ColsShape<N1>::R;
+  constexpr int CPL = ColsPerLane<TA>::value;
   constexpr int VEC = 16 / sizeof(TS);             // entries per 16-byte global load
   extern __shared__ __align__(128) unsigned char cols_smem[];
   TS* sS = reinterpret_cast<TS*>(cols_smem);       // [16][R], element-major
   const int seg = blockIdx.x;
-  // stage: global [(seg*R + r)*16 + t] -> sS[t*R + r]
+  // stage: global [(seg*R + r)*16 + t] -> sS[t*R + r], up to 8 16-byte loads
+  // in flight per thread before their stores
   {
     const uint4* g = reinterpret_cast<const uint4*>((const TS*)a.rec + (size_t)seg * R * kSeg);
     constexpr int NV = R * kSeg / VEC;
-    for (int idx = threadIdx.x; idx < NV; idx += blockDim.x) {
-      union { uint4 u; TS s[VEC]; } pk;
-      pk.u = __ldg(g + idx);
-      const int r = (idx * VEC) / kSeg, t0 = (idx * VEC) % kSeg;
+    constexpr int PER = (NV + kColsThreads - 1) / kColsThreads;
+    constexpr int BATCH = PER < 8 ? PER : 8;
+#pragma unroll 1
+    for (int b0 = 0; b0 < PER; b0 += BATCH) {
+      union Pk { uint4 u; TS s[VEC]; };
+      Pk buf[BATCH];
 #pragma unroll
-      for (int q = 0; q < VEC; ++q) sS[(t0 + q) * R + r] = pk.s[q];
+      for (int u = 0; u < BATCH; ++u) {
+        const int idx = (b0 + u) * kColsThreads + (int)threadIdx.x;
+        if (b0 + u < PER && idx < NV) buf[u].u = __ldg(g + idx);
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int idx = (b0 + u) * kColsThreads + (int)threadIdx.x;
+        if (b0 + u < PER && idx < NV) {
+          const int r = (idx * VEC) / kSeg, t0 = (idx * VEC) % kSeg;
+#pragma unroll
+          for (int q = 0; q < VEC; ++q) sS[(t0 + q) * R + r] = buf[u].s[q];
+        }
+      }
     }
   }
   __syncthreads();
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny, nb = a.nb;
   const int j = seg / a.spr, i0 = (seg % a.spr) * kSeg;
-  const int nchunk = (nb + 31) >> 5;
+  constexpr int CPW = 32 * CPL;                    // columns per warp item
+  const int nchunk = (nb + CPW - 1) / CPW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TV* __restrict__ v = (const TV*)a.v;
   const TV* __restrict__ cv = (const TV*)a.cvec;
   TV* __restrict__ y = (TV*)a.y;
   const TO al = (TO)a.alpha, be = (TO)a.beta;
   for (int item = warp; item < 32 * nchunk; item += (kColsThreads >> 5)) {
+    // warp-uniform: element t of the segment, owned face (W or S), column chunk
     const int chunk = item >> 5, face = (item >> 4) & 1, t = item & 15;
     const int i = i0 + t;
     if (i >= nx) continue;
-    const int col = chunk * 32 + lane;
-    const bool live = col < nb;
+    int colc[CPL];
+    bool live[CPL];
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) {
+      const int col = chunk * CPW + u * 32 + lane;
+      live[u] = col < nb;
+      colc[u] = live[u] ? col : nb - 1;            // dead lanes load a valid column
+    }
     const bool bndrow = face == 0 ? (i == 0) : (j == 0);
-    TA acc[N1];
+    TA acc[CPL][N1];
 #pragma unroll
-    for (int q = 0; q < N1; ++q) acc[q] = TA{};
+    for (int u = 0; u < CPL; ++u)
+#pragma unroll
+      for (int q = 0; q < N1; ++q) acc[u][q] = TA{};
     if (!bndrow) {
-#pragma unroll
+#pragma unroll(CPL == 2 ? 2 : 1)
       for (int side = 0; side < 2; ++side) {
         const int ki = (side == 1 && face == 0) ? i - 1 : i;
         const int kj = (side == 1 && face == 1) ? j - 1 : j;
-        TA xv[M];
-        cols_gather<N1, TS, TV, TA, DIFF>(v, ki, kj, col, live, a, xv);
+        int edge[4];
+        bool bnd[4];
+        edge[0] = ki + (nx + 1) * kj;       bnd[0] = ki <= 0;
+        edge[1] = ki + 1 + (nx + 1) * kj;   bnd[1] = ki >= nx - 1;
+        edge[2] = nv + ki + nx * kj;        bnd[2] = kj <= 0;
+        edge[3] = nv + ki + nx * (kj + 1);  bnd[3] = kj >= ny - 1;
+        TA xv[CPL][M];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          if (!bnd[f]) {                           // warp-uniform branch
+            const TV* bp = v + (size_t)edge[f] * N1 * nb;
+#pragma unroll
+            for (int b = 0; b < N1; ++b)
+#pragma unroll
+              for (int u = 0; u < CPL; ++u) xv[u][f * N1 + b] = to_acc(bp[(size_t)b * nb + colc[u]], TA{});
+          } else {
+#pragma unroll
+            for (int b = 0; b < N1; ++b)
+#pragma unroll
+              for (int u = 0; u < CPL; ++u) xv[u][f * N1 + b] = TA{};
+          }
+        }
+        if constexpr (DIFF) {
+          // S_K 1 = 0: apply the block to x - mean(x) 1 (boundary entries count as
+          // 0), so the rounded FP32 / BF16 entries see the variation of x over the
+          // element rather than its (smooth, large) value
+#pragma unroll
+          for (int u = 0; u < CPL; ++u) {
+            TA mean = TA(0);
+#pragma unroll
+            for (int c = 0; c < M; ++c) mean += xv[u][c];
+            mean *= TA(1.0 / M);
+#pragma unroll
+            for (int c = 0; c < M; ++c) xv[u][c] -= mean;
+          }
+        }
         const TS* rows = sS + t * R + (face * 2 + side) * N1 * M;
 #pragma unroll
         for (int q = 0; q < N1; ++q)
@@ -117,32 +157,40 @@ __global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
           for (int c = 0; c < M; c += 4) {
             const Quad<TS> s4 = *reinterpret_cast<const Quad<TS>*>(rows + q * M + c);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[q] = mac(to_acc(s4.v[u], TA{}), xv[c + u], acc[q]);
+            for (int w = 0; w < 4; ++w) {
+              const TA sv = to_acc(s4.v[w], TA{});
+#pragma unroll
+              for (int u = 0; u < CPL; ++u) acc[u][q] = mac(sv, xv[u][c + w], acc[u][q]);
+            }
           }
       }
     }
-    if (!live) continue;
     const int eout = face == 0 ? i + (nx + 1) * j : nv + i + nx * j;
 #pragma unroll
-    for (int q = 0; q < N1; ++q) {
-      const size_t o = ((size_t)eout * N1 + q) * nb + col;
-      TO val = TO(0);
-      if (!bndrow) {
-        val = al * finish(acc[q]);
-        if (cv) val = mac(be, (TO)cv[o], val);
+    for (int u = 0; u < CPL; ++u) {
+      if (!live[u]) continue;
+      const int col = colc[u];
+#pragma unroll
+      for (int q = 0; q < N1; ++q) {
+        const size_t o = ((size_t)eout * N1 + q) * nb + col;
+        TO val = TO(0);
+        if (!bndrow) {
+          val = al * finish(acc[u][q]);
+          if (cv) val = mac(be, (TO)cv[o], val);
+        }
+        y[o] = (TV)val;
       }
-      y[o] = (TV)val;
-    }
-    // the E / N domain-boundary edges have no owner element: zero them here
-    if (face == 0 && i == nx - 1) {
-      const size_t eb = (size_t)nx + (size_t)(nx + 1) * j;
+      // the E / N domain-boundary edges have no owner element: zero them here
+      if (face == 0 && i == nx - 1) {
+        const size_t eb = (size_t)nx + (size_t)(nx + 1) * j;
 #pragma unroll
-      for (int q = 0; q < N1; ++q) y[(eb * N1 + q) * nb + col] = TV(0);
-    }
-    if (face == 1 && j == ny - 1) {
-      const size_t eb = (size_t)nv + i + (size_t)nx * ny;
+        for (int q = 0; q < N1; ++q) y[(eb * N1 + q) * nb + col] = TV(0);
+      }
+      if (face == 1 && j == ny - 1) {
+        const size_t eb = (size_t)nv + i + (size_t)nx * ny;
 #pragma unroll
-      for (int q = 0; q < N1; ++q) y[(eb * N1 + q) * nb + col] = TV(0);
+        for (int q = 0; q < N1; ++q) y[(eb * N1 + q) * nb + col] = TV(0);
+      }
     }
   }
 }

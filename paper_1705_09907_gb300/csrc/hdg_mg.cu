@@ -97,6 +97,19 @@ __global__ void copy_convert_kernel(size_t n, const TI* __restrict__ a, TO* __re
     b[t] = (TO)a[t];
 }
 
+// t -> (t / d, t % d) with 32-bit division when t fits (64-bit division by a
+// runtime value costs far more than the memory traffic of these kernels)
+__device__ __forceinline__ size_t divmod(size_t t, int d, int* rem) {
+  if (d == 1) { *rem = 0; return t; }
+  if (t <= 0xffffffffull) {
+    const unsigned tt = (unsigned)t, q = tt / (unsigned)d;
+    *rem = (int)(tt - q * (unsigned)d);
+    return q;
+  }
+  *rem = (int)(t % (size_t)d);
+  return t / (size_t)d;
+}
+
 static int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   if (b > 2048) b = 2048;
@@ -112,7 +125,8 @@ template <typename T>
 __global__ void cheb_first_zero_kernel(size_t n, int nb, const T* __restrict__ dinv, const T* __restrict__ f,
                                        T* __restrict__ x, T* __restrict__ d, T c0) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const T v = c0 * dinv[t / nb] * f[t];
+    int col;
+    const T v = c0 * dinv[divmod(t, nb, &col)] * f[t];
     x[t] = v;
     d[t] = v;
   }
@@ -121,7 +135,8 @@ template <typename T>
 __global__ void cheb_step_kernel(size_t n, int nb, const T* __restrict__ dinv, const T* __restrict__ r,
                                  T* __restrict__ x, T* __restrict__ d, T a1, T a2) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const T v = a1 * d[t] + a2 * dinv[t / nb] * r[t];
+    int col;
+    const T v = a1 * d[t] + a2 * dinv[divmod(t, nb, &col)] * r[t];
     d[t] = v;
     x[t] += v;
   }
@@ -135,10 +150,8 @@ __global__ void restrict_p_kernel(int n_edges, int n1c, int nb, const double* __
   const int n1f = n1c + 1;
   const size_t total = (size_t)n_edges * n1c * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t u = t / nb;
-    const int col = (int)(t % nb);
-    const size_t e = u / n1c;
-    const int a = (int)(u % n1c);
+    int col, a;
+    const size_t e = divmod(divmod(t, nb, &col), n1c, &a);
     T s = 0;
     for (int b = 0; b < n1f; ++b) s += (T)P[b * n1c + a] * rf[(e * n1f + b) * nb + col];
     rc[t] = s;
@@ -150,10 +163,8 @@ __global__ void prolong_p_add_kernel(int n_edges, int n1c, int nb, const double*
   const int n1f = n1c + 1;
   const size_t total = (size_t)n_edges * n1f * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const size_t u = t / nb;
-    const int col = (int)(t % nb);
-    const size_t e = u / n1f;
-    const int a = (int)(u % n1f);
+    int col, a;
+    const size_t e = divmod(divmod(t, nb, &col), n1f, &a);
     T s = 0;
     for (int b = 0; b < n1c; ++b) s += (T)P[a * n1c + b] * xc[(e * n1c + b) * nb + col];
     xf[t] += s;
@@ -166,7 +177,8 @@ __global__ void restrict_J_kernel(int nx, int ny, int nb, const T* __restrict__ 
   const int nvx = nx - 1;
   const size_t nv = (size_t)(nx + 1) * ny, total = (size_t)(nx - 1) * (ny - 1) * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    const int u = (int)(t / nb), col = (int)(t % nb);
+    int col;
+    const int u = (int)divmod(t, nb, &col);
     const size_t I = u % nvx + 1, J = u / nvx + 1;
     const T s = r0[(I + (nx + 1) * (J - 1)) * nb + col] + r0[(I + (nx + 1) * J) * nb + col] +
                 r0[(nv + (I - 1) + nx * J) * nb + col] + r0[(nv + I + nx * J) * nb + col];
@@ -181,7 +193,8 @@ __global__ void prolong_J_add_kernel(int nx, int ny, int nb, const T* __restrict
   const int nv = (nx + 1) * ny, ne = nv + nx * (ny + 1);
   const size_t total = (size_t)ne * nb;
   for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(tt / nb), col = (int)(tt % nb);
+    int col;
+    const int t = (int)divmod(tt, nb, &col);
     int I0, J0, I1, J1;
     bool interior;
     if (t < nv) {
@@ -214,7 +227,8 @@ __global__ void stencil_apply_kernel(int nx, int ny, int nb, const T* __restrict
   const int nvx = nx - 1, nvy = ny - 1, nvert = nvx * nvy;
   const size_t total = (size_t)nvert * nb;
   for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(tt / nb), col = (int)(tt % nb);
+    int col;
+    const int t = (int)divmod(tt, nb, &col);
     const int I = t % nvx, J = t / nvx;
     const T xc = x[tt];
     T s = rsum ? rsum[t] * xc : T(0);
@@ -254,7 +268,8 @@ __global__ void restrict_q_kernel(int nxc, int nyc, int nb, const T* __restrict_
   const int nvxc = nxc - 1, nvxf = nxf - 1;
   const size_t total = (size_t)(nxc - 1) * (nyc - 1) * nb;
   for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(tt / nb), col = (int)(tt % nb);
+    int col;
+    const int t = (int)divmod(tt, nb, &col);
     const int I = t % nvxc + 1, J = t / nvxc + 1;
     T s = 0;
     for (int b = -1; b <= 1; ++b)
@@ -274,7 +289,8 @@ __global__ void prolong_q_add_kernel(int nxc, int nyc, int nb, const T* __restri
   const int nvxf = nxf - 1, nvxc = nxc - 1;
   const size_t total = (size_t)(nxf - 1) * (nyf - 1) * nb;
   for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    const int t = (int)(tt / nb), col = (int)(tt % nb);
+    int col;
+    const int t = (int)divmod(tt, nb, &col);
     const int i = t % nvxf + 1, j = t / nvxf + 1;
     const int i0 = i / 2, j0 = j / 2;
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
@@ -1019,11 +1035,25 @@ __global__ void cdots_kernel(size_t n, int nb, const double* __restrict__ a0, co
     const int col = col0 + lc;
     double s0 = 0.0, s1 = 0.0;
     if (rowl < rl && col < nb) {
-      for (size_t i = (size_t)blockIdx.x * rl + rowl; i < n; i += (size_t)gridDim.x * rl) {
-        const size_t o = i * nb + col;
-        s0 += a0[o] * b0[o];
-        if (a1) s1 += a1[o] * b1[o];
+      // four independent partial sums (loads in flight), combined in a fixed order
+      double p0[4] = {0.0, 0.0, 0.0, 0.0}, p1[4] = {0.0, 0.0, 0.0, 0.0};
+      const size_t step = (size_t)gridDim.x * rl;
+      size_t i = (size_t)blockIdx.x * rl + rowl;
+      for (; i + 3 * step < n; i += 4 * step) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const size_t o = (i + u * step) * nb + col;
+          p0[u] += a0[o] * b0[o];
+          if (a1) p1[u] += a1[o] * b1[o];
+        }
       }
+      for (; i < n; i += step) {
+        const size_t o = i * nb + col;
+        p0[0] += a0[o] * b0[o];
+        if (a1) p1[0] += a1[o] * b1[o];
+      }
+      s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+      s1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
     }
     sh[0][threadIdx.x] = s0;
     sh[1][threadIdx.x] = s1;
@@ -1087,7 +1117,9 @@ __global__ void cgb_xr_kernel(size_t n, int nb, const double* __restrict__ sc, c
                               const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
   const double* al = sc + kAlpha * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const double a = al[t % nb];
+    int col;
+    (void)divmod(t, nb, &col);
+    const double a = al[col];
     if (a != 0.0) {
       x[t] += a * p[t];
       r[t] -= a * q[t];
@@ -1119,7 +1151,8 @@ __global__ void cgb_p_kernel(size_t n, int nb, const double* __restrict__ sc, co
   const double* act = sc + kAct * nb;
   const double* be = sc + kBeta * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(t % nb);
+    int j;
+    (void)divmod(t, nb, &j);
     if (act[j] != 0.0) p[t] = z[t] + be[j] * p[t];
   }
 }
