@@ -45,7 +45,7 @@ template <typename TA>
 struct ColsPerLane { static constexpr int value = sizeof(TA) == 4 ? 2 : 1; };
 
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
-__global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
+__global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a) {
   using TO = typename OutT<TA>::type;
   constexpr int M = ColsShape<N1>::M, R = ColsShape<N1>::R;
   constexpr int CPL = ColsPerLane<TA>::value;
@@ -104,6 +104,12 @@ __global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
       colc[u] = live[u] ? col : nb - 1;            // dead lanes load a valid column
     }
     const bool bndrow = face == 0 ? (i == 0) : (j == 0);
+    const int eout = face == 0 ? i + (nx + 1) * j : nv + i + nx * j;
+    TO cpre[CPL][N1];
+#pragma unroll
+    for (int u = 0; u < CPL; ++u)
+#pragma unroll
+      for (int q = 0; q < N1; ++q) cpre[u][q] = TO(0);
     TA acc[CPL][N1];
 #pragma unroll
     for (int u = 0; u < CPL; ++u)
@@ -150,6 +156,14 @@ __global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
             for (int c = 0; c < M; ++c) xv[u][c] -= mean;
           }
         }
+        if (side == 1 && cv) {
+          // the addend's loads are issued before the last products so their
+          // latency overlaps them
+#pragma unroll
+          for (int u = 0; u < CPL; ++u)
+#pragma unroll
+            for (int q = 0; q < N1; ++q) cpre[u][q] = (TO)cv[((size_t)eout * N1 + q) * nb + colc[u]];
+        }
         const TS* rows = sS + t * R + (face * 2 + side) * N1 * M;
 #pragma unroll
         for (int q = 0; q < N1; ++q)
@@ -165,7 +179,6 @@ __global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
           }
       }
     }
-    const int eout = face == 0 ? i + (nx + 1) * j : nv + i + nx * j;
 #pragma unroll
     for (int u = 0; u < CPL; ++u) {
       if (!live[u]) continue;
@@ -176,7 +189,7 @@ __global__ void __launch_bounds__(kColsThreads) apply_cols_kernel(ColsArgs a) {
         TO val = TO(0);
         if (!bndrow) {
           val = al * finish(acc[u][q]);
-          if (cv) val = mac(be, (TO)cv[o], val);
+          if (cv) val = mac(be, cpre[u][q], val);
         }
         y[o] = (TV)val;
       }

@@ -124,6 +124,11 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
       p_prolongation_1d(p - 1, Pp);
       TRY(ctx_alloc(c, (void**)&L.Pp, Pp.size() * sizeof(double)));
       TRY(cudaMemcpyAsync(L.Pp, Pp.data(), Pp.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+      // float copy for the float V-cycles (a double -> float conversion per use
+      // would run on the FP64 pipe)
+      const std::vector<float> Pp32(Pp.begin(), Pp.end());
+      TRY(ctx_alloc(c, (void**)&L.Pp32, Pp.size() * sizeof(float)));
+      TRY(cudaMemcpyAsync(L.Pp32, Pp32.data(), Pp.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     }
   }
   TRY(launch_local_setup(c, s));

@@ -57,6 +57,7 @@ struct PLevel {
   float2* S2 = nullptr; float2* M2 = nullptr;   // double-float (hi, lo) copies
   double* Sdense = nullptr;                 // [nel][m][m] FP64 element blocks
   double* Pp = nullptr;                     // prolongation from p-1 [(p+1) x p] (device)
+  float* Pp32 = nullptr;                    // the same in float (float V-cycles)
   // V-cycle work vectors, [ndof] each, per precision (d = double, f = float)
   double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
   float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;

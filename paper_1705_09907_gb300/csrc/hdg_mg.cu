@@ -19,6 +19,7 @@ namespace hdg {
 
 constexpr int kRedBlocks = 304;   // fixed reduction grid (deterministic sums)
 constexpr int kCgScalars = 12;    // per-column scalars of the batched CG
+constexpr int kColRedBlocks = 608; // fixed grid of the per-column dot products
 
 // ---------------------------------------------------------------------------
 // Deterministic dot products: fixed grid of partial sums, then one block sums
@@ -145,29 +146,41 @@ __global__ void cheb_step_kernel(size_t n, int nb, const T* __restrict__ dinv, c
 // ---------------------------------------------------------------------------
 // p-transfers per edge. P is [(pc+2) x (pc+1)] row-major: fine node a', coarse a.
 template <typename T>
-__global__ void restrict_p_kernel(int n_edges, int n1c, int nb, const double* __restrict__ P,
+__global__ void restrict_p_kernel(int n_edges, int n1c, int nb, const T* __restrict__ P,
                                   const T* __restrict__ rf, T* __restrict__ rc) {
   const int n1f = n1c + 1;
   const size_t total = (size_t)n_edges * n1c * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     int col, a;
     const size_t e = divmod(divmod(t, nb, &col), n1c, &a);
+    // fixed-trip loop: the n1f loads issue back to back instead of one per FMA
+    T v[kMaxDegree + 1];
+#pragma unroll
+    for (int b = 0; b < kMaxDegree + 1; ++b) v[b] = b < n1f ? rf[(e * n1f + b) * nb + col] : T(0);
     T s = 0;
-    for (int b = 0; b < n1f; ++b) s += (T)P[b * n1c + a] * rf[(e * n1f + b) * nb + col];
+#pragma unroll
+    for (int b = 0; b < kMaxDegree + 1; ++b)
+      if (b < n1f) s += P[b * n1c + a] * v[b];
     rc[t] = s;
   }
 }
 template <typename T>
-__global__ void prolong_p_add_kernel(int n_edges, int n1c, int nb, const double* __restrict__ P,
+__global__ void prolong_p_add_kernel(int n_edges, int n1c, int nb, const T* __restrict__ P,
                                      const T* __restrict__ xc, T* __restrict__ xf) {
   const int n1f = n1c + 1;
   const size_t total = (size_t)n_edges * n1f * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
     int col, a;
     const size_t e = divmod(divmod(t, nb, &col), n1f, &a);
+    T v[kMaxDegree];
+#pragma unroll
+    for (int b = 0; b < kMaxDegree; ++b) v[b] = b < n1c ? xc[(e * n1c + b) * nb + col] : T(0);
+    const T old = xf[t];
     T s = 0;
-    for (int b = 0; b < n1c; ++b) s += (T)P[a * n1c + b] * xc[(e * n1c + b) * nb + col];
-    xf[t] += s;
+#pragma unroll
+    for (int b = 0; b < kMaxDegree; ++b)
+      if (b < n1c) s += P[a * n1c + b] * v[b];
+    xf[t] = old + s;
   }
 }
 
@@ -594,11 +607,12 @@ static cudaError_t pmg(Context* c, VWork& w, int prec, int p, const T* r, T* x, 
   HDG_CUDA_TRY(launch_apply(c, p, 0, rprec, x, r, t, -1.0, 1.0, nb, s));
   T* rc = (T*)w.pr[p - 1];
   T* xc = (T*)w.px[p - 1];
-  restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, L.Pp, t, rc);
+  const T* Pp = (const T*)(prec_double(prec) ? (const void*)L.Pp : (const void*)L.Pp32);
+  restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, Pp, t, rc);
   HDG_CUDA_TRY(cudaGetLastError());
   if (p - 1 == 0) HDG_CUDA_TRY(hmg<T>(c, w, prec, -1, rc, xc, s));
   else HDG_CUDA_TRY(pmg<T>(c, w, prec, p - 1, rc, xc, s));
-  prolong_p_add_kernel<T><<<grid_for((size_t)c->n_edges * L.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, L.Pp, xc, x);
+  prolong_p_add_kernel<T><<<grid_for((size_t)c->n_edges * L.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, Pp, xc, x);
   HDG_CUDA_TRY(cudaGetLastError());
   for (int i = 0; i < nu2; ++i) {
     HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, nb, s));
@@ -751,7 +765,7 @@ static cudaError_t work_cg(Context* c, VWork* w) {
   w->cg_p = (double*)work_alloc(w, n); w->cg_q = (double*)work_alloc(w, n);
   w->cg_zold = (double*)work_alloc(w, n);
   w->cg_sc = (double*)work_alloc(w, (size_t)kCgScalars * w->nb * sizeof(double));
-  w->cg_part = (double*)work_alloc(w, (size_t)2 * kRedBlocks * w->nb * sizeof(double));
+  w->cg_part = (double*)work_alloc(w, (size_t)2 * kColRedBlocks * w->nb * sizeof(double));
   bool ok = w->cg_r && w->cg_z && w->cg_p && w->cg_q && w->cg_zold && w->cg_sc && w->cg_part;
   if (ok) ok = cudaMallocHost((void**)&w->h_sc, 3 * (size_t)w->nb * sizeof(double)) == cudaSuccess;
   if (!ok) { cudaGetLastError(); w->cg_r = nullptr; return cudaErrorMemoryAllocation; }
@@ -1067,23 +1081,32 @@ __global__ void cdots_kernel(size_t n, int nb, const double* __restrict__ a0, co
     __syncthreads();
   }
 }
+// one warp per column: lanes take every 32nd partial, then a fixed shuffle tree
 __global__ void cdots_finalize_kernel(int nb, int nblk, const double* __restrict__ part, double* __restrict__ out0,
                                       double* __restrict__ out1) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (col >= nb) return;
   double t0 = 0.0, t1 = 0.0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     t0 += part[(size_t)b * nb + col];
     if (out1) t1 += part[((size_t)nblk + b) * nb + col];
   }
-  out0[col] = t0;
-  if (out1) out1[col] = t1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (lane == 0) {
+    out0[col] = t0;
+    if (out1) out1[col] = t1;
+  }
 }
 static cudaError_t cdots(VWork* w, size_t n, const double* a0, const double* b0, const double* a1,
                          const double* b1, double* out0, double* out1, cudaStream_t s) {
-  cdots_kernel<<<kRedBlocks, 256, 0, s>>>(n, w->nb, a0, b0, a1, b1, w->cg_part);
+  cdots_kernel<<<kColRedBlocks, 256, 0, s>>>(n, w->nb, a0, b0, a1, b1, w->cg_part);
   HDG_CUDA_TRY(cudaGetLastError());
-  cdots_finalize_kernel<<<(w->nb + 255) / 256, 256, 0, s>>>(w->nb, kRedBlocks, w->cg_part, out0, out1);
+  cdots_finalize_kernel<<<(w->nb + 7) / 8, 256, 0, s>>>(w->nb, kColRedBlocks, w->cg_part, out0, out1);
   return cudaGetLastError();
 }
 
