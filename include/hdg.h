@@ -79,9 +79,13 @@ typedef struct {
   int mixed;                  /* also build FP32, BF16 and F32X2 copies of the
                                  level blocks (1)                             */
   int use_graphs;             /* capture V-cycles in CUDA graphs (1)         */
-  int autotune;               /* time the apply kernels' launch shapes per
-                                 level and precision at set-up and keep the
-                                 fastest (1); shapes never change results      */
+  int autotune;               /* 1: time the apply kernels (the ring kernel's
+                                 launch shapes and the one-CTA-per-segment
+                                 kernel) per level and precision at set-up and
+                                 keep the fastest (default); 0: the ring kernel
+                                 with its default shape; 2: the segment kernel
+                                 wherever it fits. The choice changes only the
+                                 order of the floating-point sums            */
 } hdg_options;
 
 typedef struct {

@@ -409,11 +409,151 @@ __global__ void __launch_bounds__(ApplyMaxThreads<TS>::value) apply_kernel(Apply
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------
+// One CTA per record segment (nrhs = 1). One bulk copy stages the segment's
+// row blocks; the 8 warps split the products by (side, input face): warp
+// (side, f) gives every lane (element t, owned face W or S) the N1 x N1
+// products of its block row with face f of the element on that side (own or
+// neighbour). The 8 partial sums of each output are added in a fixed order
+// through shared memory. Several CTAs share an SM, so one CTA's copy overlaps
+// the others' arithmetic: the FP64 pipe stays fed without a deep ring.
+constexpr int kTuneSeg = 0x400;      // tune flag: this kernel
+constexpr int kSegThreads = 256;
+
+template <int N1, typename TS, typename TO>
+constexpr size_t seg_smem_bytes() {
+  return (size_t)16 * N1 * N1 * kSeg * sizeof(TS) + (size_t)8 * N1 * 32 * sizeof(TO) + 16;
+}
+
+template <int N1, typename TS, typename TV, typename TA, bool DIFF>
+__global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
+  using TO = typename OutT<TA>::type;
+  constexpr int M = 4 * N1, R = 16 * N1 * N1;
+  constexpr unsigned SB = (unsigned)(R * kSeg * sizeof(TS));
+  extern __shared__ __align__(128) unsigned char seg_smem[];
+  TS* st = reinterpret_cast<TS*>(seg_smem);
+  TO* part = reinterpret_cast<TO*>(seg_smem + SB);                          // [8][N1][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(seg_smem + SB + (size_t)8 * N1 * 32 * sizeof(TO));
+  const int seg = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, SB);
+    bulk_load(st, (const TS*)a.rec + (size_t)seg * (SB / sizeof(TS)), SB, bar);
+  }
+  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+  const int j = seg / a.spr, i0 = (seg % a.spr) * kSeg;
+  const int oface = lane >> 4, t = lane & 15, i = i0 + t;
+  const int side = warp >> 2, f = warp & 3;
+  const bool active = i < nx && !(oface == 0 ? (i == 0) : (j == 0));
+  // x of face f of the element on this side (loaded while the blocks arrive)
+  TA xf[N1];
+#pragma unroll
+  for (int b = 0; b < N1; ++b) xf[b] = TA{};
+  if (active) {
+    const TV* __restrict__ v = (const TV*)a.v;
+    const int ki = (side == 1 && oface == 0) ? i - 1 : i;
+    const int kj = (side == 1 && oface == 1) ? j - 1 : j;
+    int edge[4];
+    bool bnd[4];
+    edge[0] = ki + (nx + 1) * kj;       bnd[0] = ki <= 0;
+    edge[1] = ki + 1 + (nx + 1) * kj;   bnd[1] = ki >= nx - 1;
+    edge[2] = nv + ki + nx * kj;        bnd[2] = kj <= 0;
+    edge[3] = nv + ki + nx * (kj + 1);  bnd[3] = kj >= ny - 1;
+    if constexpr (DIFF) {
+      // blocks with zero row sums act on x - mean(x) (boundary entries count as 0)
+      TA xa[M];
+#pragma unroll
+      for (int g = 0; g < 4; ++g)
+#pragma unroll
+        for (int b = 0; b < N1; ++b) xa[g * N1 + b] = bnd[g] ? TA{} : to_acc(__ldg(&v[(size_t)edge[g] * N1 + b]), TA{});
+      TA mean = TA(0);
+#pragma unroll
+      for (int c = 0; c < M; ++c) mean += xa[c];
+      mean *= TA(1.0 / M);
+#pragma unroll
+      for (int b = 0; b < N1; ++b) {
+        TA xv = xa[b];
+#pragma unroll
+        for (int g = 1; g < 4; ++g) xv = (f == g) ? xa[g * N1 + b] : xv;
+        xf[b] = xv - mean;
+      }
+    } else {
+      const int ef = f == 0 ? edge[0] : (f == 1 ? edge[1] : (f == 2 ? edge[2] : edge[3]));
+      const bool bf = f == 0 ? bnd[0] : (f == 1 ? bnd[1] : (f == 2 ? bnd[2] : bnd[3]));
+      if (!bf) {
+#pragma unroll
+        for (int b = 0; b < N1; ++b) xf[b] = to_acc(__ldg(&v[(size_t)ef * N1 + b]), TA{});
+      }
+    }
+  }
+  if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+    // the copy did not land within the bound: flag it, give it one more bounded
+    // wait (it writes this CTA's shared memory), and leave together
+    if (threadIdx.x == 0) {
+      atomicExch(a.err, 2);
+      (void)mbar_wait_bounded(bar, 0);
+    }
+    __syncthreads();
+    return;
+  }
+  TA acc[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) acc[q] = TA{};
+  if (active) {
+    const TS* rows = st + (size_t)((oface * 2 + side) * N1 * M + f * N1) * kSeg + t;
+#pragma unroll
+    for (int b = 0; b < N1; ++b)
+#pragma unroll
+      for (int q = 0; q < N1; ++q) acc[q] = mac(to_acc(rows[(q * M + b) * kSeg], TA{}), xf[b], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < N1; ++q) part[(warp * N1 + q) * 32 + lane] = finish(acc[q]);
+  __syncthreads();
+  // epilogue: output o = (owned face, element, row), row fastest (contiguous y)
+  const TV* __restrict__ cv = (const TV*)a.cvec;
+  TV* __restrict__ y = (TV*)a.y;
+  const TO al = (TO)a.alpha, be = (TO)a.beta;
+  for (int o = threadIdx.x; o < 32 * N1; o += kSegThreads) {
+    const int q = o % N1, ln = o / N1;
+    const int of = ln >> 4, ii = i0 + (ln & 15);
+    if (ii >= nx) continue;
+    const bool br = of == 0 ? (ii == 0) : (j == 0);
+    const size_t eout = of == 0 ? (size_t)ii + (size_t)(nx + 1) * j : (size_t)nv + ii + (size_t)nx * j;
+    TO sum = part[q * 32 + ln];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) sum += part[(w * N1 + q) * 32 + ln];
+    TO val = TO(0);
+    if (!br) {
+      val = al * sum;
+      if (cv) val = mac(be, (TO)cv[eout * N1 + q], val);
+    }
+    y[eout * N1 + q] = (TV)val;
+    // the E / N domain-boundary edges have no owner element: zero them here
+    if (of == 0 && ii == nx - 1) y[((size_t)nx + (size_t)(nx + 1) * j) * N1 + q] = TV(0);
+    if (of == 1 && j == ny - 1) y[((size_t)nv + ii + (size_t)nx * ny) * N1 + q] = TV(0);
+  }
+}
+
 // Host-side launcher for one (degree, storage, vector) combination.
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
 cudaError_t apply_launch(const Context* c, const ApplyArgs& args0, cudaStream_t s) {
   using TO = typename OutT<TA>::type;
   ApplyArgs a = args0;
+  if (a.tune & kTuneSeg) {
+    const size_t smem = seg_smem_bytes<N1, TS, TO>();
+    if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
+    auto kern = apply_seg_kernel<N1, TS, TV, TA, DIFF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
+    if (e != cudaSuccess) return e;
+    if (a.nseg <= 0) return cudaSuccess;
+    kern<<<a.nseg, kSegThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   a.stage_bytes = (unsigned)(16 * N1 * N1 * kSeg * sizeof(TS));
   int np = 0, NS = 0;
   apply_shape((unsigned)stage_total_bytes<N1, TS, TV, TO>(), a.tune, &np, &NS);
