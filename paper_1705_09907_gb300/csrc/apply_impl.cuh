@@ -411,29 +411,34 @@ __global__ void __launch_bounds__(ApplyMaxThreads<TS>::value) apply_kernel(Apply
 
 // ---------------------------------------------------------------------------
 // One CTA per record segment (nrhs = 1). One bulk copy stages the segment's
-// row blocks; the 8 warps split the products by (side, input face): warp
-// (side, f) gives every lane (element t, owned face W or S) the N1 x N1
-// products of its block row with face f of the element on that side (own or
-// neighbour). The 8 partial sums of each output are added in a fixed order
+// row blocks; the NW warps split the products by (side, group of input faces):
+// warp (side, g) gives every lane (element t, owned face W or S) the products of
+// its block rows with faces g*8/NW .. of the element on that side (own or
+// neighbour). The NW partial sums of each output are added in a fixed order
 // through shared memory. Several CTAs share an SM, so one CTA's copy overlaps
-// the others' arithmetic: the FP64 pipe stays fed without a deep ring.
-constexpr int kTuneSeg = 0x400;      // tune flag: this kernel
-constexpr int kSegThreads = 256;
+// the others' arithmetic: the FP64 pipe stays fed without a deep ring. NW = 8
+// spreads the products widest; NW = 4 halves the partial sums (which also run
+// on the FP64 pipe in FP64).
+constexpr int kTuneSeg = 0x400;      // tune flag: this kernel, 8 warps
+constexpr int kTuneSeg4 = 0x800;     // with kTuneSeg: 4 warps
 
-template <int N1, typename TS, typename TO>
+template <int N1, typename TS, typename TO, int NW>
 constexpr size_t seg_smem_bytes() {
-  return (size_t)16 * N1 * N1 * kSeg * sizeof(TS) + (size_t)8 * N1 * 32 * sizeof(TO) + 16;
+  return (size_t)16 * N1 * N1 * kSeg * sizeof(TS) + (size_t)NW * N1 * 32 * sizeof(TO) + 16;
 }
 
-template <int N1, typename TS, typename TV, typename TA, bool DIFF>
-__global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
+template <int N1, typename TS, typename TV, typename TA, bool DIFF, int NW>
+__global__ void __launch_bounds__(32 * NW) apply_seg_kernel(ApplyArgs a) {
   using TO = typename OutT<TA>::type;
   constexpr int M = 4 * N1, R = 16 * N1 * N1;
+  constexpr int GPS = NW / 2;                  // face groups per side
+  constexpr int FPW = 4 / GPS;                 // faces per warp
+  constexpr int NC = FPW * N1;                 // block columns per warp
   constexpr unsigned SB = (unsigned)(R * kSeg * sizeof(TS));
   extern __shared__ __align__(128) unsigned char seg_smem[];
   TS* st = reinterpret_cast<TS*>(seg_smem);
-  TO* part = reinterpret_cast<TO*>(seg_smem + SB);                          // [8][N1][32]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(seg_smem + SB + (size_t)8 * N1 * 32 * sizeof(TO));
+  TO* part = reinterpret_cast<TO*>(seg_smem + SB);                          // [NW][N1][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(seg_smem + SB + (size_t)NW * N1 * 32 * sizeof(TO));
   const int seg = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -448,12 +453,13 @@ __global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int j = seg / a.spr, i0 = (seg % a.spr) * kSeg;
   const int oface = lane >> 4, t = lane & 15, i = i0 + t;
-  const int side = warp >> 2, f = warp & 3;
+  const int side = warp / GPS, g0 = (warp % GPS) * FPW;
   const bool active = i < nx && !(oface == 0 ? (i == 0) : (j == 0));
-  // x of face f of the element on this side (loaded while the blocks arrive)
-  TA xf[N1];
+  // x of faces g0 .. g0+FPW-1 of the element on this side (loaded while the
+  // blocks arrive)
+  TA xf[NC];
 #pragma unroll
-  for (int b = 0; b < N1; ++b) xf[b] = TA{};
+  for (int c = 0; c < NC; ++c) xf[c] = TA{};
   if (active) {
     const TV* __restrict__ v = (const TV*)a.v;
     const int ki = (side == 1 && oface == 0) ? i - 1 : i;
@@ -476,18 +482,24 @@ __global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
       for (int c = 0; c < M; ++c) mean += xa[c];
       mean *= TA(1.0 / M);
 #pragma unroll
-      for (int b = 0; b < N1; ++b) {
-        TA xv = xa[b];
+      for (int lf = 0; lf < FPW; ++lf)
 #pragma unroll
-        for (int g = 1; g < 4; ++g) xv = (f == g) ? xa[g * N1 + b] : xv;
-        xf[b] = xv - mean;
-      }
+        for (int b = 0; b < N1; ++b) {
+          TA xv = xa[b];
+#pragma unroll
+          for (int g = 1; g < 4; ++g) xv = (g0 + lf == g) ? xa[g * N1 + b] : xv;
+          xf[lf * N1 + b] = xv - mean;
+        }
     } else {
-      const int ef = f == 0 ? edge[0] : (f == 1 ? edge[1] : (f == 2 ? edge[2] : edge[3]));
-      const bool bf = f == 0 ? bnd[0] : (f == 1 ? bnd[1] : (f == 2 ? bnd[2] : bnd[3]));
-      if (!bf) {
 #pragma unroll
-        for (int b = 0; b < N1; ++b) xf[b] = to_acc(__ldg(&v[(size_t)ef * N1 + b]), TA{});
+      for (int lf = 0; lf < FPW; ++lf) {
+        const int gg = g0 + lf;
+        const int ef = gg == 0 ? edge[0] : (gg == 1 ? edge[1] : (gg == 2 ? edge[2] : edge[3]));
+        const bool bf = gg == 0 ? bnd[0] : (gg == 1 ? bnd[1] : (gg == 2 ? bnd[2] : bnd[3]));
+        if (!bf) {
+#pragma unroll
+          for (int b = 0; b < N1; ++b) xf[lf * N1 + b] = to_acc(__ldg(&v[(size_t)ef * N1 + b]), TA{});
+        }
       }
     }
   }
@@ -505,11 +517,11 @@ __global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
 #pragma unroll
   for (int q = 0; q < N1; ++q) acc[q] = TA{};
   if (active) {
-    const TS* rows = st + (size_t)((oface * 2 + side) * N1 * M + f * N1) * kSeg + t;
+    const TS* rows = st + (size_t)((oface * 2 + side) * N1 * M + g0 * N1) * kSeg + t;
 #pragma unroll
-    for (int b = 0; b < N1; ++b)
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-      for (int q = 0; q < N1; ++q) acc[q] = mac(to_acc(rows[(q * M + b) * kSeg], TA{}), xf[b], acc[q]);
+      for (int q = 0; q < N1; ++q) acc[q] = mac(to_acc(rows[(q * M + c) * kSeg], TA{}), xf[c], acc[q]);
   }
 #pragma unroll
   for (int q = 0; q < N1; ++q) part[(warp * N1 + q) * 32 + lane] = finish(acc[q]);
@@ -518,7 +530,10 @@ __global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
   const TV* __restrict__ cv = (const TV*)a.cvec;
   TV* __restrict__ y = (TV*)a.y;
   const TO al = (TO)a.alpha, be = (TO)a.beta;
-  for (int o = threadIdx.x; o < 32 * N1; o += kSegThreads) {
+  // y = A v, y = c - A v (the V-cycle's residuals) and y = c + A v take no multiply
+  const int form = (al == TO(1) && (!cv || be == TO(0))) ? 0
+                   : (cv && be == TO(1) && al == TO(-1)) ? 1 : (cv && be == TO(1) && al == TO(1)) ? 2 : 3;
+  for (int o = threadIdx.x; o < 32 * N1; o += 32 * NW) {
     const int q = o % N1, ln = o / N1;
     const int of = ln >> 4, ii = i0 + (ln & 15);
     if (ii >= nx) continue;
@@ -526,11 +541,16 @@ __global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
     const size_t eout = of == 0 ? (size_t)ii + (size_t)(nx + 1) * j : (size_t)nv + ii + (size_t)nx * j;
     TO sum = part[q * 32 + ln];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) sum += part[(w * N1 + q) * 32 + ln];
+    for (int w = 1; w < NW; ++w) sum += part[(w * N1 + q) * 32 + ln];
     TO val = TO(0);
     if (!br) {
-      val = al * sum;
-      if (cv) val = mac(be, (TO)cv[eout * N1 + q], val);
+      if (form == 0) val = sum;
+      else if (form == 1) val = (TO)cv[eout * N1 + q] - sum;
+      else if (form == 2) val = (TO)cv[eout * N1 + q] + sum;
+      else {
+        val = al * sum;
+        if (cv) val = mac(be, (TO)cv[eout * N1 + q], val);
+      }
     }
     y[eout * N1 + q] = (TV)val;
     // the E / N domain-boundary edges have no owner element: zero them here
@@ -539,20 +559,27 @@ __global__ void __launch_bounds__(kSegThreads) apply_seg_kernel(ApplyArgs a) {
   }
 }
 
+template <int N1, typename TS, typename TV, typename TA, bool DIFF, int NW>
+cudaError_t seg_launch(const Context* c, const ApplyArgs& a, cudaStream_t s) {
+  using TO = typename OutT<TA>::type;
+  const size_t smem = seg_smem_bytes<N1, TS, TO, NW>();
+  if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
+  auto kern = apply_seg_kernel<N1, TS, TV, TA, DIFF, NW>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
+  if (e != cudaSuccess) return e;
+  if (a.nseg <= 0) return cudaSuccess;
+  kern<<<a.nseg, 32 * NW, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 // Host-side launcher for one (degree, storage, vector) combination.
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
 cudaError_t apply_launch(const Context* c, const ApplyArgs& args0, cudaStream_t s) {
   using TO = typename OutT<TA>::type;
   ApplyArgs a = args0;
   if (a.tune & kTuneSeg) {
-    const size_t smem = seg_smem_bytes<N1, TS, TO>();
-    if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
-    auto kern = apply_seg_kernel<N1, TS, TV, TA, DIFF>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);
-    if (e != cudaSuccess) return e;
-    if (a.nseg <= 0) return cudaSuccess;
-    kern<<<a.nseg, kSegThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    if (a.tune & kTuneSeg4) return seg_launch<N1, TS, TV, TA, DIFF, 4>(c, a, s);
+    return seg_launch<N1, TS, TV, TA, DIFF, 8>(c, a, s);
   }
   a.stage_bytes = (unsigned)(16 * N1 * N1 * kSeg * sizeof(TS));
   int np = 0, NS = 0;

@@ -90,11 +90,12 @@ static size_t seg_bytes_of(int n1, int prec) {
 }
 
 cudaError_t autotune_applies(Context* c, cudaStream_t s) {
-  if (c->opt.autotune == 2) {   // the one-CTA-per-segment kernel wherever it fits
+  if (c->opt.autotune == 2 || c->opt.autotune == 3) {   // the segment kernel (8 / 4 warps) wherever it fits
+    const int code = c->opt.autotune == 2 ? kTuneSeg : (kTuneSeg | kTuneSeg4);
     for (int p = 0; p <= c->k; ++p)
       for (int prec = 0; prec < 4; ++prec)
         for (int which = 0; which < 2; ++which)
-          c->plev[p].tune[prec][which] = seg_bytes_of(c->plev[p].n1, prec) <= (size_t)c->smem_optin ? kTuneSeg : 0;
+          c->plev[p].tune[prec][which] = seg_bytes_of(c->plev[p].n1, prec) <= (size_t)c->smem_optin ? code : 0;
     return cudaSuccess;
   }
   const size_t n = (size_t)c->ndof;
@@ -139,17 +140,20 @@ cudaError_t autotune_applies(Context* c, cudaStream_t s) {
             HDG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
             if (ms < best) { best = ms; best_tune = nw * 16 + ns; }
           }
-        // the one-CTA-per-segment kernel (when its stage and partial sums fit)
+        // the one-CTA-per-segment kernel, 8 and 4 warps (when its stage and
+        // partial sums fit)
         if (seg_bytes_of(L.n1, prec) <= (size_t)c->smem_optin) {
-          L.tune[prec][which] = kTuneSeg;
-          HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
-          HDG_CUDA_TRY(cudaEventRecord(e0, s));
-          for (int r = 0; r < 3; ++r) HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
-          HDG_CUDA_TRY(cudaEventRecord(e1, s));
-          HDG_CUDA_TRY(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          HDG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-          if (ms < best) { best = ms; best_tune = kTuneSeg; }
+          for (const int cand : {kTuneSeg, kTuneSeg | kTuneSeg4}) {
+            L.tune[prec][which] = cand;
+            HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
+            HDG_CUDA_TRY(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
+            HDG_CUDA_TRY(cudaEventRecord(e1, s));
+            HDG_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            HDG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_tune = cand; }
+          }
         }
         L.tune[prec][which] = best_tune;
       }

@@ -1,7 +1,7 @@
-"""The one-CTA-per-segment apply kernel (forced with autotune = 2) against the
-FP64 oracle's assembled operator and against the ring kernel (autotune = 0), for
-every degree, all four precisions, ragged segments, and the residual form
-y = c - A x used inside the V-cycle; then a V-cycle and a solve built on it."""
+"""The one-CTA-per-segment apply kernel (forced with autotune = 2 / 3: 8 / 4
+warps) against the FP64 oracle's assembled operator and against the ring
+kernel (autotune = 0), for every degree, all four precisions and ragged
+segments; then the residual form y = c - A x inside a V-cycle, and a solve."""
 import numpy as np
 import pytest
 import torch
@@ -23,10 +23,11 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
+@pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32", "bf16"])
 @pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("nx,ny", [(37, 6), (16, 3)])
-def test_segment_apply_vs_assembled(prec, k, nx, ny):
+def test_segment_apply_vs_assembled(prec, k, nx, ny, mode):
     from paper_1705_09907_gb300 import hdg
     m = omesh.Mesh(nx, ny, 0.0, 0.0, 1.0, 0.7)
     kap = np.exp(inputs.gaussian_field(nx, seed=k, corr_len=0.3, ny=ny))
@@ -35,7 +36,7 @@ def test_segment_apply_vs_assembled(prec, k, nx, ny):
     dt = torch.float64 if prec in ("fp64", "f32x2") else torch.float32
     xd = cuda(inputs.random_trace(m.n_edges, k, seed=70 + k), dt)
     x = host(xd)
-    seg = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=2)
+    seg = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=mode)
     ring = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=0)
     y = host(seg.apply(xd, prec=prec))
     ref = np.zeros(prob.ndof)
@@ -51,8 +52,9 @@ def test_segment_apply_vs_assembled(prec, k, nx, ny):
     ring.close()
 
 
+@pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("k", [1, 3, 4])
-def test_segment_vcycle_and_solve(k):
+def test_segment_vcycle_and_solve(k, mode):
     """V-cycle (residual-form applies y = c - A x and Schwarz blocks) against the
     oracle's V-cycle, and a solve to 1e-12 against the oracle's direct solve."""
     from paper_1705_09907_gb300 import hdg
@@ -63,7 +65,7 @@ def test_segment_vcycle_and_solve(k):
     top = G.plevels[k]
     r = np.zeros(top.ndof)
     r[top.idx] = np.random.default_rng(21).normal(size=len(top.idx))
-    s = hdg.HDGSolver(nx, ny, k, cuda(kap), autotune=2)
+    s = hdg.HDGSolver(nx, ny, k, cuda(kap), autotune=mode)
     for prec, tol in (("fp64", 1e-11), ("f32x2", 1e-10)):
         z = host(s.vcycle(cuda(r), prec=prec))
         z_ref = G.vcycle(r)
