@@ -192,9 +192,12 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     if args.profile:
-        # short fixed sequence for profiler launch lists: one solve step, then
-        # three trace applies per precision; no other work
+        # short fixed sequence for profiler launch lists: one solve step (NVTX
+        # range fp64_step), then three trace applies per precision, then the
+        # batched work below
+        torch.cuda.nvtx.range_push("fp64_step")
         step()
+        torch.cuda.nvtx.range_pop()
         x64 = torch.as_tensor(inputs.random_trace(solver.n_edges, k, seed=1), device="cuda")
         x32 = x64.float()
         # each precision's applies inside an NVTX range named apply_<prec>
@@ -411,10 +414,11 @@ def run_ours(args):
     tflops = fp["flops"] / (apply_ms["fp64"] * 1e-3) / 1e12
     # FP64: 0.25 flop/byte needs more FP64 issue than the GPU has (1.25 TFLOP/s
     # nominal), so the FP64 apply is bound by the FP64 pipe, not by HBM.
-    # DRAM read+write of one FP64 level-k apply: ncu capture at 256 x 256 (218.8 MB)
-    # scaled by the element count to 512 x 512
-    traffic = 218.775e6 * (nel / 65536.0) if (N, k) == (512, 4) else None
-    roof = {"kernel": "apply_kernel<5,double,double,double> (FP64 trace apply, level k)",
+    # DRAM read+write of one FP64 level-k apply at 512 x 512, k = 4 (ncu, one-pass
+    # dram__bytes_read.sum + dram__bytes_write.sum, warm launches of the set-up
+    # autotuner's choice, the 4-warp segment kernel): 860.0 MB + 18.3 MB
+    traffic = 878.3e6 if (N, k) == (512, 4) else None
+    roof = {"kernel": "FP64 trace apply at level k (autotuned; apply_seg_kernel<5,double,double,double,0,4> on GB300)",
             "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": tflops / 1.25,
             "peak_source": "nominal FP64 rate of GB300 (recipe table); HBM fraction in trace_apply",
             "traffic": traffic, "algorithmic_bytes": fp["algorithmic_bytes"]}

@@ -90,6 +90,9 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
   const TV* __restrict__ cv = (const TV*)a.cvec;
   TV* __restrict__ y = (TV*)a.y;
   const TO al = (TO)a.alpha, be = (TO)a.beta;
+  // y = A v, y = c - A v and y = c + A v take no multiply (FP64 ops are slow here)
+  const int form = (al == TO(1) && (!cv || be == TO(0))) ? 0
+                   : (cv && be == TO(1) && al == TO(-1)) ? 1 : (cv && be == TO(1) && al == TO(1)) ? 2 : 3;
   for (int item = warp; item < 32 * nchunk; item += (kColsThreads >> 5)) {
     // warp-uniform: element t of the segment, owned face (W or S), column chunk
     const int chunk = item >> 5, face = (item >> 4) & 1, t = item & 15;
@@ -188,8 +191,14 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
         const size_t o = ((size_t)eout * N1 + q) * nb + col;
         TO val = TO(0);
         if (!bndrow) {
-          val = al * finish(acc[u][q]);
-          if (cv) val = mac(be, cpre[u][q], val);
+          const TO sum = finish(acc[u][q]);
+          if (form == 0) val = sum;
+          else if (form == 1) val = cpre[u][q] - sum;
+          else if (form == 2) val = cpre[u][q] + sum;
+          else {
+            val = al * sum;
+            if (cv) val = mac(be, cpre[u][q], val);
+          }
         }
         y[o] = (TV)val;
       }

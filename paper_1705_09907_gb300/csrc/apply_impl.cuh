@@ -62,11 +62,14 @@ struct dfloat {
 
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v, float) { return __bfloat162float(v); }
 __device__ __forceinline__ dfloat to_acc(float2 v, dfloat) { return dfloat{v.x, v.y}; }
-// double -> (hi, lo) with integer operations (the FP64 pipe is slow on this
-// GPU): hi keeps the leading 24 significant bits (truncated), lo the remaining
-// 29 bits rounded to 24 by the int->float conversion, so hi + lo = v to about
-// 2^-48 relative. Magnitudes below 2^-74 (where the scale 2^(e-1075) would
-// leave the normal float range), zero and huge values take the conversion path.
+// double -> (hi, lo) with integer operations and one FP32 subtraction (the FP64
+// pipe, which also runs int <-> float conversions, is slow on this GPU): hi
+// keeps the leading 24 significant bits (truncated); lo is the remaining 29
+// bits rounded to 24: the rounded bits are placed under the exponent 2^E of
+// lo's scale, and subtracting 2^E (exact, both operands in [2^E, 2^(E+1)])
+// leaves them as a float. hi + lo = v to about 2^-47 relative. Magnitudes below
+// 2^-74 (where lo would leave the normal float range), zero and huge values
+// take the conversion path.
 __device__ __forceinline__ dfloat split_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
@@ -78,11 +81,12 @@ __device__ __forceinline__ dfloat split_double(double v) {
   const unsigned long long mant = b & 0xfffffffffffffull;
   const unsigned int hib = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29);
   const unsigned int rem = (unsigned int)(mant & 0x1fffffffull);          // 29 bits below hi
-  // lo = rem * 2^(e - 1075) with the sign of v
-  const float scale = __int_as_float((unsigned int)(e - 1075 + 127) << 23);
-  float lo = __uint2float_rn(rem) * scale;
-  lo = __int_as_float(__float_as_int(lo) | (int)sign);
-  return dfloat{__int_as_float((int)hib), lo};
+  // lo = rem * 2^(e - 1075) = (2^E + rounded rem) - 2^E with E = e - 1046
+  const unsigned int eb = (unsigned int)(e - 919) << 23;                  // float bits of 2^E
+  const float top = __uint_as_float(eb + ((rem + 32u) >> 6));             // mantissa carry rounds up to 2^(E+1)
+  float lo = top - __uint_as_float(eb);
+  lo = __uint_as_float(__float_as_uint(lo) | sign);
+  return dfloat{__uint_as_float(hib), lo};
 }
 __device__ __forceinline__ dfloat to_acc(double v, dfloat) { return split_double(v); }
 // acc + s*x with an error-free product (FMA residual) and an error-free sum
@@ -100,8 +104,22 @@ __device__ __forceinline__ dfloat mac(dfloat s, dfloat x, dfloat acc) {
   const float err = (acc.hi - (sum - bb)) + (p - bb);
   return dfloat{sum, acc.lo + (err + e)};
 }
-// value of an accumulator in the output arithmetic
-__device__ __forceinline__ double finish(dfloat a) { return (double)a.hi + (double)a.lo; }
+// float -> double from the bits (exact for normal floats and zero): the
+// conversion instruction runs on the FP64 pipe, which is slow on this GPU
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int ex = (u >> 23) & 0xffu;
+  if (ex == 0u || ex == 255u) {
+    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+    return (double)f;                      // subnormal, inf, nan
+  }
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+// value of an accumulator in the output arithmetic (one FP64 add for hi + lo)
+__device__ __forceinline__ double finish(dfloat a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 __device__ __forceinline__ double finish(double a) { return a; }
 __device__ __forceinline__ float finish(float a) { return a; }
 template <typename TA> struct OutT { using type = TA; };
@@ -272,13 +290,21 @@ __device__ __forceinline__ void write_face(const TO (&sum)[N1], int seg, int lan
   const bool bndrow = face == 0 ? (i == 0) : (j == 0);
   const int eout = face == 0 ? i + (nx + 1) * j : nv + i + nx * j;
   const TO al = (TO)a.alpha, be = (TO)a.beta;
+  // y = A v, y = c - A v and y = c + A v take no multiply (FP64 ops are slow here)
+  const int form = (al == TO(1) && (!cv || be == TO(0))) ? 0
+                   : (cv && be == TO(1) && al == TO(-1)) ? 1 : (cv && be == TO(1) && al == TO(1)) ? 2 : 3;
 #pragma unroll
   for (int q = 0; q < N1; ++q) {
     const size_t o = ((size_t)eout * N1 + q) * nrhs + r;
     TO val = TO(0);
     if (!bndrow) {
-      val = al * sum[q];
-      if (cv) val = mac(be, (TO)cv[o], val);
+      if (form == 0) val = sum[q];
+      else if (form == 1) val = (TO)cv[o] - sum[q];
+      else if (form == 2) val = (TO)cv[o] + sum[q];
+      else {
+        val = al * sum[q];
+        if (cv) val = mac(be, (TO)cv[o], val);
+      }
     }
     y[o] = (TV)val;
   }

@@ -145,43 +145,66 @@ __global__ void cheb_step_kernel(size_t n, int nb, const T* __restrict__ dinv, c
 
 // ---------------------------------------------------------------------------
 // p-transfers per edge. P is [(pc+2) x (pc+1)] row-major: fine node a', coarse a.
-template <typename T>
-__global__ void restrict_p_kernel(int n_edges, int n1c, int nb, const T* __restrict__ P,
-                                  const T* __restrict__ rf, T* __restrict__ rc) {
-  const int n1f = n1c + 1;
-  const size_t total = (size_t)n_edges * n1c * nb;
+// One thread per (edge, column) loads the edge's NF fine (or NC coarse) values
+// once and writes all its outputs; NC = pc + 1 is a template constant so the
+// loads issue back to back.
+template <typename T, int NC>
+__global__ void restrict_p_kernel(int n_edges, int nb, const T* __restrict__ P, const T* __restrict__ rf,
+                                  T* __restrict__ rc) {
+  constexpr int NF = NC + 1;
+  const size_t total = (size_t)n_edges * nb;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    int col, a;
-    const size_t e = divmod(divmod(t, nb, &col), n1c, &a);
-    // fixed-trip loop: the n1f loads issue back to back instead of one per FMA
-    T v[kMaxDegree + 1];
+    int col;
+    const size_t e = divmod(t, nb, &col);
+    T v[NF];
 #pragma unroll
-    for (int b = 0; b < kMaxDegree + 1; ++b) v[b] = b < n1f ? rf[(e * n1f + b) * nb + col] : T(0);
-    T s = 0;
+    for (int b = 0; b < NF; ++b) v[b] = rf[(e * NF + b) * nb + col];
 #pragma unroll
-    for (int b = 0; b < kMaxDegree + 1; ++b)
-      if (b < n1f) s += P[b * n1c + a] * v[b];
-    rc[t] = s;
+    for (int a = 0; a < NC; ++a) {
+      T s = 0;
+#pragma unroll
+      for (int b = 0; b < NF; ++b) s += __ldg(&P[b * NC + a]) * v[b];
+      rc[(e * NC + a) * nb + col] = s;
+    }
+  }
+}
+template <typename T, int NC>
+__global__ void prolong_p_add_kernel(int n_edges, int nb, const T* __restrict__ P, const T* __restrict__ xc,
+                                     T* __restrict__ xf) {
+  constexpr int NF = NC + 1;
+  const size_t total = (size_t)n_edges * nb;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    int col;
+    const size_t e = divmod(t, nb, &col);
+    T v[NC], o[NF];
+#pragma unroll
+    for (int b = 0; b < NC; ++b) v[b] = xc[(e * NC + b) * nb + col];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) o[a] = xf[(e * NF + a) * nb + col];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+      T s = 0;
+#pragma unroll
+      for (int b = 0; b < NC; ++b) s += __ldg(&P[a * NC + b]) * v[b];
+      xf[(e * NF + a) * nb + col] = o[a] + s;
+    }
   }
 }
 template <typename T>
-__global__ void prolong_p_add_kernel(int n_edges, int n1c, int nb, const T* __restrict__ P,
-                                     const T* __restrict__ xc, T* __restrict__ xf) {
-  const int n1f = n1c + 1;
-  const size_t total = (size_t)n_edges * n1f * nb;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
-    int col, a;
-    const size_t e = divmod(divmod(t, nb, &col), n1f, &a);
-    T v[kMaxDegree];
-#pragma unroll
-    for (int b = 0; b < kMaxDegree; ++b) v[b] = b < n1c ? xc[(e * n1c + b) * nb + col] : T(0);
-    const T old = xf[t];
-    T s = 0;
-#pragma unroll
-    for (int b = 0; b < kMaxDegree; ++b)
-      if (b < n1c) s += P[a * n1c + b] * v[b];
-    xf[t] = old + s;
+static cudaError_t p_transfer(bool restrict_, int n1c, int n_edges, int nb, const T* P, const T* in, T* out,
+                              cudaStream_t s) {
+  const int g = grid_for((size_t)n_edges * nb);
+#define HDG_PT(NCv)                                                                              \
+  case NCv:                                                                                      \
+    if (restrict_) restrict_p_kernel<T, NCv><<<g, 256, 0, s>>>(n_edges, nb, P, in, out);         \
+    else prolong_p_add_kernel<T, NCv><<<g, 256, 0, s>>>(n_edges, nb, P, in, out);                \
+    break;
+  switch (n1c) {
+    HDG_PT(1) HDG_PT(2) HDG_PT(3) HDG_PT(4) HDG_PT(5) HDG_PT(6) HDG_PT(7)
+    default: return cudaErrorInvalidValue;
   }
+#undef HDG_PT
+  return cudaGetLastError();
 }
 
 // P_J^T: interior vertex (I, J) gets half the sum of its 4 edges' residuals.
@@ -608,12 +631,10 @@ static cudaError_t pmg(Context* c, VWork& w, int prec, int p, const T* r, T* x, 
   T* rc = (T*)w.pr[p - 1];
   T* xc = (T*)w.px[p - 1];
   const T* Pp = (const T*)(prec_double(prec) ? (const void*)L.Pp : (const void*)L.Pp32);
-  restrict_p_kernel<T><<<grid_for((size_t)c->n_edges * Lc.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, Pp, t, rc);
-  HDG_CUDA_TRY(cudaGetLastError());
+  HDG_CUDA_TRY(p_transfer<T>(true, Lc.n1, c->n_edges, nb, Pp, t, rc, s));
   if (p - 1 == 0) HDG_CUDA_TRY(hmg<T>(c, w, prec, -1, rc, xc, s));
   else HDG_CUDA_TRY(pmg<T>(c, w, prec, p - 1, rc, xc, s));
-  prolong_p_add_kernel<T><<<grid_for((size_t)c->n_edges * L.n1 * nb), 256, 0, s>>>(c->n_edges, Lc.n1, nb, Pp, xc, x);
-  HDG_CUDA_TRY(cudaGetLastError());
+  HDG_CUDA_TRY(p_transfer<T>(false, Lc.n1, c->n_edges, nb, Pp, xc, x, s));
   for (int i = 0; i < nu2; ++i) {
     HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, nb, s));
     HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, nb, s));
