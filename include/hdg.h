@@ -164,9 +164,10 @@ int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void*
 
 /*
  * The trace apply of Alg. 3 for n independent meshes (1 <= n <= 16 contexts,
- * uneven sizes, degrees 0..5) in ONE persistent kernel launch: the segments of
- * all meshes form a single work list, so small meshes do not leave SMs idle
- * behind large ones. y[q] = A_q x[q] for each q, same layouts and boundary rules
+ * uneven sizes, degrees 0..5) in ONE kernel launch: the record segments of all
+ * meshes form a single work list (one CTA per entry, each on its mesh's degree),
+ * so small meshes do not leave SMs idle behind large ones and the batch costs one
+ * launch. y[q] = A_q x[q] for each q, same layouts and boundary rules
  * as hdg_apply_trace (nrhs = 1). prec: HDG_PREC_FP64 (double vectors) or
  * HDG_PREC_FP32 (float vectors). All contexts must belong to the current device.
  * Errors: INVALID_ARG (count, pointers, degree, device), UNSUPPORTED (FP32 when a

@@ -44,6 +44,9 @@ struct alignas(4 * sizeof(TS)) Quad {
 template <typename TA>
 struct ColsPerLane { static constexpr int value = sizeof(TA) == 4 ? 2 : 1; };
 
+// registers sized for three CTAs per SM (85 per thread): at k >= 5 this spills a
+// few hundred bytes, and is still faster than two CTAs without spills (measured
+// at 256 x 256, k = 5, 64 right-hand sides, all precisions)
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
 __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a) {
   using TO = typename OutT<TA>::type;

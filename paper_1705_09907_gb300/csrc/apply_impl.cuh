@@ -453,29 +453,18 @@ constexpr size_t seg_smem_bytes() {
   return (size_t)16 * N1 * N1 * kSeg * sizeof(TS) + (size_t)NW * N1 * 32 * sizeof(TO) + 16;
 }
 
+// The segment's products, partial sums and outputs once its blocks are being
+// copied into `st` (completion on `bar`); `part` holds NW x N1 x 32 outputs.
+// Shared by the single-mesh kernel and the multi-mesh launch.
 template <int N1, typename TS, typename TV, typename TA, bool DIFF, int NW>
-__global__ void __launch_bounds__(32 * NW) apply_seg_kernel(ApplyArgs a) {
+__device__ __forceinline__ void seg_body(const ApplyArgs& a, int seg, const TS* st,
+                                         typename OutT<TA>::type* part, uint64_t* bar) {
   using TO = typename OutT<TA>::type;
-  constexpr int M = 4 * N1, R = 16 * N1 * N1;
+  constexpr int M = 4 * N1;
   constexpr int GPS = NW / 2;                  // face groups per side
   constexpr int FPW = 4 / GPS;                 // faces per warp
   constexpr int NC = FPW * N1;                 // block columns per warp
-  constexpr unsigned SB = (unsigned)(R * kSeg * sizeof(TS));
-  extern __shared__ __align__(128) unsigned char seg_smem[];
-  TS* st = reinterpret_cast<TS*>(seg_smem);
-  TO* part = reinterpret_cast<TO*>(seg_smem + SB);                          // [NW][N1][32]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(seg_smem + SB + (size_t)NW * N1 * 32 * sizeof(TO));
-  const int seg = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(bar, SB);
-    bulk_load(st, (const TS*)a.rec + (size_t)seg * (SB / sizeof(TS)), SB, bar);
-  }
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int j = seg / a.spr, i0 = (seg % a.spr) * kSeg;
   const int oface = lane >> 4, t = lane & 15, i = i0 + t;
@@ -583,6 +572,28 @@ __global__ void __launch_bounds__(32 * NW) apply_seg_kernel(ApplyArgs a) {
     if (of == 0 && ii == nx - 1) y[((size_t)nx + (size_t)(nx + 1) * j) * N1 + q] = TV(0);
     if (of == 1 && j == ny - 1) y[((size_t)nv + ii + (size_t)nx * ny) * N1 + q] = TV(0);
   }
+}
+
+template <int N1, typename TS, typename TV, typename TA, bool DIFF, int NW>
+__global__ void __launch_bounds__(32 * NW) apply_seg_kernel(ApplyArgs a) {
+  using TO = typename OutT<TA>::type;
+  constexpr int R = 16 * N1 * N1;
+  constexpr unsigned SB = (unsigned)(R * kSeg * sizeof(TS));
+  extern __shared__ __align__(128) unsigned char seg_smem[];
+  TS* st = reinterpret_cast<TS*>(seg_smem);
+  TO* part = reinterpret_cast<TO*>(seg_smem + SB);                          // [NW][N1][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(seg_smem + SB + (size_t)NW * N1 * 32 * sizeof(TO));
+  const int seg = blockIdx.x;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(bar, SB);
+    bulk_load(st, (const TS*)a.rec + (size_t)seg * (SB / sizeof(TS)), SB, bar);
+  }
+  seg_body<N1, TS, TV, TA, DIFF, NW>(a, seg, st, part, bar);
 }
 
 template <int N1, typename TS, typename TV, typename TA, bool DIFF, int NW>

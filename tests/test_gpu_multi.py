@@ -19,9 +19,9 @@ def test_multi_instance_apply(prec):
     dt = torch.float64 if prec == "fp64" else torch.float32
     for q, (nx, ny, k) in enumerate(CASES):
         kap = np.exp(inputs.gaussian_field(nx, seed=q, corr_len=0.3, ny=ny))
-        # autotune = 0: the single apply runs the ring kernel, whose per-segment
-        # arithmetic the multi-instance launch shares
-        s = hdg.HDGSolver(nx, ny, k, torch.as_tensor(kap, device="cuda"), autotune=0)
+        # autotune = 3: the single apply runs the 4-warp segment kernel, whose
+        # per-segment arithmetic the multi-instance launch shares
+        s = hdg.HDGSolver(nx, ny, k, torch.as_tensor(kap, device="cuda"), autotune=3)
         solvers.append(s)
         xs.append(torch.as_tensor(inputs.random_trace(s.n_edges, k, seed=50 + q), dtype=dt, device="cuda"))
     ys = hdg.apply_multi(solvers, xs, prec=prec)
