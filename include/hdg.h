@@ -83,8 +83,9 @@ typedef struct {
                                  launch shapes and the one-CTA-per-segment
                                  kernel) per level and precision at set-up and
                                  keep the fastest (default); 0: the ring kernel
-                                 with its default shape; 2 / 3: the segment
-                                 kernel with 8 / 4 warps wherever it fits. The
+                                 with its default shape; 2 / 3 / 4: the
+                                 segment kernel with 8 / 4 / 2 warps wherever it
+                                 fits. The
                                  choice changes only the
                                  order of the floating-point sums            */
 } hdg_options;

@@ -444,9 +444,10 @@ __global__ void __launch_bounds__(ApplyMaxThreads<TS>::value) apply_kernel(Apply
 // through shared memory. Several CTAs share an SM, so one CTA's copy overlaps
 // the others' arithmetic: the FP64 pipe stays fed without a deep ring. NW = 8
 // spreads the products widest; NW = 4 halves the partial sums (which also run
-// on the FP64 pipe in FP64).
+// on the FP64 pipe in FP64); NW = 2 (one warp per side) leaves one add per output.
 constexpr int kTuneSeg = 0x400;      // tune flag: this kernel, 8 warps
 constexpr int kTuneSeg4 = 0x800;     // with kTuneSeg: 4 warps
+constexpr int kTuneSeg2 = 0x1000;    // with kTuneSeg: 2 warps (one per side, all four faces)
 
 template <int N1, typename TS, typename TO, int NW>
 constexpr size_t seg_smem_bytes() {
@@ -616,6 +617,7 @@ cudaError_t apply_launch(const Context* c, const ApplyArgs& args0, cudaStream_t 
   ApplyArgs a = args0;
   if (a.tune & kTuneSeg) {
     if (a.tune & kTuneSeg4) return seg_launch<N1, TS, TV, TA, DIFF, 4>(c, a, s);
+    if (a.tune & kTuneSeg2) return seg_launch<N1, TS, TV, TA, DIFF, 2>(c, a, s);
     return seg_launch<N1, TS, TV, TA, DIFF, 8>(c, a, s);
   }
   a.stage_bytes = (unsigned)(16 * N1 * N1 * kSeg * sizeof(TS));

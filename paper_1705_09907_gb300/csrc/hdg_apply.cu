@@ -90,8 +90,8 @@ static size_t seg_bytes_of(int n1, int prec) {
 }
 
 cudaError_t autotune_applies(Context* c, cudaStream_t s) {
-  if (c->opt.autotune == 2 || c->opt.autotune == 3) {   // the segment kernel (8 / 4 warps) wherever it fits
-    const int code = c->opt.autotune == 2 ? kTuneSeg : (kTuneSeg | kTuneSeg4);
+  if (c->opt.autotune >= 2 && c->opt.autotune <= 4) {   // the segment kernel (8 / 4 / 2 warps) wherever it fits
+    const int code = c->opt.autotune == 2 ? kTuneSeg : (c->opt.autotune == 3 ? (kTuneSeg | kTuneSeg4) : (kTuneSeg | kTuneSeg2));
     for (int p = 0; p <= c->k; ++p)
       for (int prec = 0; prec < 4; ++prec)
         for (int which = 0; which < 2; ++which)
@@ -143,7 +143,7 @@ cudaError_t autotune_applies(Context* c, cudaStream_t s) {
         // the one-CTA-per-segment kernel, 8 and 4 warps (when its stage and
         // partial sums fit)
         if (seg_bytes_of(L.n1, prec) <= (size_t)c->smem_optin) {
-          for (const int cand : {kTuneSeg, kTuneSeg | kTuneSeg4}) {
+          for (const int cand : {kTuneSeg, kTuneSeg | kTuneSeg4, kTuneSeg | kTuneSeg2}) {
             L.tune[prec][which] = cand;
             HDG_CUDA_TRY(launch_apply(c, p, which, prec, x, nullptr, y, 1.0, 0.0, 1, s));
             HDG_CUDA_TRY(cudaEventRecord(e0, s));

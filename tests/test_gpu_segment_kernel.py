@@ -1,5 +1,5 @@
-"""The one-CTA-per-segment apply kernel (forced with autotune = 2 / 3: 8 / 4
-warps) against the FP64 oracle's assembled operator and against the ring
+"""The one-CTA-per-segment apply kernel (forced with autotune = 2 / 3 / 4:
+8 / 4 / 2 warps) against the FP64 oracle's assembled operator and against the ring
 kernel (autotune = 0), for every degree, all four precisions and ragged
 segments; then the residual form y = c - A x inside a V-cycle, and a solve."""
 import numpy as np
@@ -23,7 +23,7 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("mode", [2, 3, 4])
 @pytest.mark.parametrize("prec", ["fp64", "f32x2", "fp32", "bf16"])
 @pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("nx,ny", [(37, 6), (16, 3)])
@@ -52,7 +52,7 @@ def test_segment_apply_vs_assembled(prec, k, nx, ny, mode):
     ring.close()
 
 
-@pytest.mark.parametrize("mode", [2, 3])
+@pytest.mark.parametrize("mode", [2, 3, 4])
 @pytest.mark.parametrize("k", [1, 3, 4])
 def test_segment_vcycle_and_solve(k, mode):
     """V-cycle (residual-form applies y = c - A x and Schwarz blocks) against the
