@@ -75,8 +75,8 @@ struct HLevel {
   float* rsum32 = nullptr;                  // row sums (difference-form float apply)
   double* dinv64 = nullptr; float* dinv32 = nullptr;
   double lmax = 0.0;
-  double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
-  float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;
+  double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr, *e64 = nullptr;
+  float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr, *e32 = nullptr;   // e: second direction
 };
 
 // Work vectors of one V-cycle in one vector type (double for FP64 / F32X2
@@ -89,7 +89,7 @@ struct VWork {
   bool dbl = true;
   std::vector<void*> pr, px, pt;            // p-levels 0..k: residual, correction, scratch
   void* p0d = nullptr;                      // p = 0 Chebyshev direction
-  std::vector<void*> hr, hx, ht, hd;        // Q1 levels, finest first
+  std::vector<void*> hr, hx, ht, hd, hd2;   // Q1 levels, finest first (hd2: second Chebyshev direction)
   double* coarse_w = nullptr;               // [nb][coarse_dim] FP64 scratch
   cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};   // per precision
   cudaStream_t gstream[4] = {nullptr, nullptr, nullptr, nullptr};

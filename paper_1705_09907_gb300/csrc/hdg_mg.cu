@@ -288,6 +288,70 @@ __global__ void stencil_apply_kernel(int nx, int ny, int nb, const T* __restrict
   }
 }
 
+// (A x)_v for vertex t, column col of a Q1 stencil level (difference form with
+// row sums for float levels, as in stencil_apply_kernel)
+template <typename T>
+__device__ __forceinline__ T stencil_row(int nvx, int nvy, int nb, int t, int col, const T* __restrict__ st,
+                                         const T* __restrict__ x, const T* __restrict__ rsum) {
+  const int nvert = nvx * nvy;
+  const int I = t % nvx, J = t / nvx;
+  const T xc = x[(size_t)t * nb + col];
+  T s = rsum ? rsum[t] * xc : T(0);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int I2 = I + dx, J2 = J + dy;
+      if (I2 < 0 || J2 < 0 || I2 >= nvx || J2 >= nvy) continue;
+      const T a = st[((dy + 1) * 3 + dx + 1) * (size_t)nvert + t];
+      const T xn = x[((size_t)I2 + (size_t)nvx * J2) * nb + col];
+      if (rsum) {
+        if (dx != 0 || dy != 0) s += a * (xn - xc);
+      } else {
+        s += a * xn;
+      }
+    }
+  return s;
+}
+
+// Fused Chebyshev steps on a Q1 level (stencil A, Jacobi D), two launches per
+// degree-2 step instead of four:
+//   cheb_resid: r = f - A x, d = c0 D^-1 r             (x is not touched)
+//   cheb_next:  r' = rin - A d, d' = a1 d + a2 D^-1 r',
+//               x += d' (+ d when x does not hold d yet); d' goes to a second
+//               buffer, so no thread writes what its neighbours read
+template <typename T>
+__global__ void cheb_resid_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ rsum,
+                                  const T* __restrict__ dinv, const T* __restrict__ f, const T* __restrict__ x,
+                                  T* __restrict__ r, T* __restrict__ d, T c0) {
+  const int nvx = nx - 1, nvy = ny - 1;
+  const size_t total = (size_t)nvx * nvy * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
+    int col;
+    const int t = (int)divmod(tt, nb, &col);
+    const T rv = f[tt] - stencil_row<T>(nvx, nvy, nb, t, col, st, x, rsum);
+    r[tt] = rv;
+    d[tt] = c0 * dinv[t] * rv;
+  }
+}
+template <typename T>
+__global__ void cheb_next_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ rsum,
+                                 const T* __restrict__ dinv, const T* rin, T* rout, const T* __restrict__ d,
+                                 T* __restrict__ dn, T* __restrict__ x, T a1, T a2, int add_d) {
+  const int nvx = nx - 1, nvy = ny - 1;
+  const size_t total = (size_t)nvx * nvy * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
+    int col;
+    const int t = (int)divmod(tt, nb, &col);
+    const T rv = rin[tt] - stencil_row<T>(nvx, nvy, nb, t, col, st, d, rsum);
+    const T dv = d[tt];
+    const T dnv = a1 * dv + a2 * dinv[t] * rv;
+    rout[tt] = rv;
+    dn[tt] = dnv;
+    x[tt] += add_d ? dv + dnv : dnv;
+  }
+}
+
 // row sums of a stencil level (FP64), stored in float for the difference form
 __global__ void stencil_rowsum_kernel(int nvert, const double* __restrict__ st, float* __restrict__ rs) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nvert; t += gridDim.x * blockDim.x) {
@@ -535,9 +599,46 @@ static ChebCoef cheb_coefficients(double lmax, int degree) {
 
 // nu Chebyshev smoothing steps on one h-level (the p = 0 level when H == nullptr).
 template <typename T>
-static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x, T* t, T* d, bool x_zero,
+static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x, T* t, T* d, T* d2, bool x_zero,
                                int nu, int nb, cudaStream_t s) {
   const bool p0 = (H == nullptr);
+  if (!p0) {   // Q1 level: fused stencil + update kernels
+    const int n = H->nv * nb;
+    const int g = grid_for((size_t)n);
+    const T* dinv = (const T*)(prec_double(prec) ? (const void*)H->dinv64 : (const void*)H->dinv32);
+    const T* st = (const T*)(prec_double(prec) ? (const void*)H->st64 : (const void*)H->st32);
+    const T* rs = (sizeof(T) == 4) ? (const T*)(const void*)H->rsum32 : nullptr;
+    const ChebCoef cc = cheb_coefficients(H->lmax, c->opt.cheb_degree);
+    T* da = d;
+    T* db = d2;
+    for (int step = 0; step < nu; ++step) {
+      const T* rin;
+      bool add_d;
+      if (step == 0 && x_zero) {
+        cheb_first_zero_kernel<T><<<g, 256, 0, s>>>((size_t)n, nb, dinv, f, x, da, (T)cc.c0);
+        rin = f;
+        add_d = false;           // x already holds d
+      } else {
+        cheb_resid_kernel<T><<<g, 256, 0, s>>>(H->nx, H->ny, nb, st, rs, dinv, f, x, t, da, (T)cc.c0);
+        rin = t;
+        add_d = true;
+      }
+      HDG_CUDA_TRY(cudaGetLastError());
+      for (size_t i = 0; i < cc.a1.size(); ++i) {
+        cheb_next_kernel<T><<<g, 256, 0, s>>>(H->nx, H->ny, nb, st, rs, dinv, rin, t, da, db, x, (T)cc.a1[i],
+                                              (T)cc.a2[i], add_d ? 1 : 0);
+        HDG_CUDA_TRY(cudaGetLastError());
+        T* tmp = da; da = db; db = tmp;
+        rin = t;
+        add_d = false;
+      }
+      if (add_d) {               // degree 1: x += d
+        cheb_step_kernel<T><<<g, 256, 0, s>>>((size_t)n, nb, dinv, t, x, da, (T)1, (T)0);
+        HDG_CUDA_TRY(cudaGetLastError());
+      }
+    }
+    return cudaSuccess;
+  }
   PLevel& L0 = c->plev[0];
   const size_t n = (p0 ? (size_t)c->n_edges : (size_t)H->nv) * nb;
   const T* dinv = p0 ? (const T*)(prec_double(prec) ? (const void*)L0.dinv64 : (const void*)L0.dinv32)
@@ -586,7 +687,8 @@ static cudaError_t hmg(Context* c, VWork& w, int prec, int l, const T* r, T* x, 
   HLevel* H = p0 ? nullptr : &c->hlev[l];
   T* t = (T*)(p0 ? w.pt[0] : w.ht[l]);
   T* d = (T*)(p0 ? w.p0d : w.hd[l]);
-  HDG_CUDA_TRY(cheb_smooth<T>(c, prec, H, r, x, t, d, true, c->opt.nu1, nb, s));
+  T* d2 = p0 ? nullptr : (T*)w.hd2[l];
+  HDG_CUDA_TRY(cheb_smooth<T>(c, prec, H, r, x, t, d, d2, true, c->opt.nu1, nb, s));
   // residual and restriction to the next (coarser) Q1 level
   HLevel& Hc = c->hlev[l + 1];
   T* rc = (T*)w.hr[l + 1];
@@ -606,7 +708,7 @@ static cudaError_t hmg(Context* c, VWork& w, int prec, int l, const T* r, T* x, 
   else
     prolong_q_add_kernel<T><<<grid_for((size_t)H->nv * nb), 256, 0, s>>>(Hc.nx, Hc.ny, nb, xc, x);
   HDG_CUDA_TRY(cudaGetLastError());
-  return cheb_smooth<T>(c, prec, H, r, x, t, d, false, c->opt.nu2, nb, s);
+  return cheb_smooth<T>(c, prec, H, r, x, t, d, d2, false, c->opt.nu2, nb, s);
 }
 
 // Alg. 2 on p-level p >= 1 (zero initial guess): r, x are level-p vectors.
@@ -760,12 +862,13 @@ static void single_works(Context* c) {
       w.pt.push_back(dbl ? (void*)L.t64 : (void*)L.t32);
     }
     w.p0d = dbl ? (void*)c->plev[0].d64 : (void*)c->plev[0].d32;
-    w.hr.clear(); w.hx.clear(); w.ht.clear(); w.hd.clear();
+    w.hr.clear(); w.hx.clear(); w.ht.clear(); w.hd.clear(); w.hd2.clear();
     for (HLevel& H : c->hlev) {
       w.hr.push_back(dbl ? (void*)H.r64 : (void*)H.r32);
       w.hx.push_back(dbl ? (void*)H.x64 : (void*)H.x32);
       w.ht.push_back(dbl ? (void*)H.t64 : (void*)H.t32);
       w.hd.push_back(dbl ? (void*)H.d64 : (void*)H.d32);
+      w.hd2.push_back(dbl ? (void*)H.e64 : (void*)H.e32);
     }
     w.coarse_w = c->coarse_rhs;
   }
@@ -812,8 +915,9 @@ static cudaError_t batched_work(Context* c, int nb, bool dbl, VWork** out) {
   for (size_t l = 0; l < c->hlev.size() && ok; ++l) {
     const size_t n = (size_t)c->hlev[l].nv * nb * es;
     void *a = work_alloc(w, n), *b = work_alloc(w, n), *d = work_alloc(w, n), *e = work_alloc(w, n);
-    ok = a && b && d && e;
-    w->hr.push_back(a); w->hx.push_back(b); w->ht.push_back(d); w->hd.push_back(e);
+    void* e2 = work_alloc(w, n);
+    ok = a && b && d && e && e2;
+    w->hr.push_back(a); w->hx.push_back(b); w->ht.push_back(d); w->hd.push_back(e); w->hd2.push_back(e2);
   }
   if (ok) {
     w->coarse_w = (double*)work_alloc(w, (size_t)c->coarse_dim * nb * sizeof(double));
@@ -928,10 +1032,10 @@ cudaError_t build_hierarchy(Context* c, cudaStream_t s) {
     HLevel& H = c->hlev[l];
     const size_t n = (size_t)H.nv;
     HDG_CUDA_TRY(ctx_alloc(c, (void**)&H.st64, 9 * n * sizeof(double)));
-    HDG_CUDA_TRY(alloc_vecs_d(c, n, {&H.dinv64, &H.r64, &H.x64, &H.t64, &H.d64}));
+    HDG_CUDA_TRY(alloc_vecs_d(c, n, {&H.dinv64, &H.r64, &H.x64, &H.t64, &H.d64, &H.e64}));
     if (mixed) {
       HDG_CUDA_TRY(ctx_alloc(c, (void**)&H.st32, 9 * n * sizeof(float)));
-      HDG_CUDA_TRY(alloc_vecs_f(c, n, {&H.dinv32, &H.r32, &H.x32, &H.t32, &H.d32}));
+      HDG_CUDA_TRY(alloc_vecs_f(c, n, {&H.dinv32, &H.r32, &H.x32, &H.t32, &H.d32, &H.e32}));
     }
     if (l == 0) {
       q1_stencil_kernel<<<grid_for(n), 256, 0, s>>>(H.nx, H.ny, c->hx, c->hy, c->kappa, H.st64);
