@@ -95,16 +95,143 @@ constexpr int kWRows = 5, kWSlots = kBS + 2;
 constexpr uint32_t kSlotB = 1024u, kRowB = kWSlots * kSlotB;
 enum { RV1 = 0, RV0 = 1, RHM = 2, RH0 = 3, RH1 = 4 };
 
+// Gather one item's window (segment seg, right-hand sides chunk*64 ..): the
+// interior edges' node rows by cp.async (one commit group), zeros for edges
+// outside the mesh. Node rows nd >= k+1 are zero from the start and never written.
+__device__ __forceinline__ void gather_window(const BatchedArgs& a, unsigned char* W, int seg, int chunk, int tid) {
+  const int n1 = a.n1;
+  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+  const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
+  const int per = kWRows * kWSlots * 8 * n1;                // (row, slot, group, node < n1)
+  for (int idx = tid; idx < per; idx += kThreads) {
+    const int nd = idx % n1, rest = idx / n1;
+    const int g = rest & 7, rs = rest >> 3;
+    const int r = rs / kWSlots, sl = rs - r * kWSlots;
+    const int i = i0 - 1 + sl;
+    int edge = -1;
+    bool inb = false;
+    switch (r) {
+      case RV1: inb = j >= 1 && i >= 1 && i <= nx - 1; edge = i + (nx + 1) * (j - 1); break;
+      case RV0: inb = i >= 1 && i <= nx - 1; edge = i + (nx + 1) * j; break;
+      case RHM: inb = j >= 2 && i >= 0 && i < nx; edge = nv + i + nx * (j - 1); break;
+      case RH0: inb = j >= 1 && i >= 0 && i < nx; edge = nv + i + nx * j; break;
+      default: inb = j + 1 <= ny - 1 && i >= 0 && i < nx; edge = nv + i + nx * (j + 1); break;
+    }
+    unsigned char* dst = W + (uint32_t)(r * kWSlots + sl) * kSlotB + (uint32_t)g * 128u + (uint32_t)nd * 16u;
+    if (inb) {   // interior edges only (the boundary trace is zero)
+      const __nv_bfloat16* src = a.X + ((size_t)edge * n1 + nd) * a.nrhs + chunk * 64 + g * 8;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+    } else {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// The kBS tiles (kBS/2 W face pairs, kBS/2 S face pairs) x 4 K16 steps of one
+// item into the accumulator columns `tm` (one thread), completion on `bar`.
+__device__ __forceinline__ void issue_mmas(const unsigned char* W, const unsigned char* Bbuf, uint32_t tm,
+                                           uint64_t* bar) {
+  constexpr uint32_t tileB = kTileN * 64 * 2;
+  constexpr int kTiles = kBS;
+  const uint32_t wb = su32(W);
+  for (int t = 0; t < kTiles; ++t) {
+    const int type = t / (kTiles / 2), L = 2 * (t % (kTiles / 2));
+    const int sl = L + 1;                      // slot of the own element's W edge
+    const uint32_t bb = su32(Bbuf + type * tileB);
+    uint32_t start[4], lbo[4];
+    start[0] = wb + (uint32_t)(RV0 * kWSlots + sl) * kSlotB;  lbo[0] = kSlotB;   // own W, E
+    start[1] = wb + (uint32_t)(RH0 * kWSlots + sl) * kSlotB;  lbo[1] = kRowB;    // own S, N
+    if (type == 0) {                                                              // west neighbour
+      start[2] = wb + (uint32_t)(RV0 * kWSlots + sl - 1) * kSlotB;  lbo[2] = kSlotB;
+      start[3] = wb + (uint32_t)(RH0 * kWSlots + sl - 1) * kSlotB;  lbo[3] = kRowB;
+    } else {                                                                      // south neighbour
+      start[2] = wb + (uint32_t)(RV1 * kWSlots + sl) * kSlotB;  lbo[2] = kSlotB;
+      start[3] = wb + (uint32_t)(RHM * kWSlots + sl) * kSlotB;  lbo[3] = kRowB;
+    }
+    const uint32_t dcol = tm + (uint32_t)(t * kTileN);
+    for (int p = 0; p < 4; ++p) {
+      const uint64_t ad = smem_desc(start[p], lbo[p], 128u);
+      const uint64_t bd = smem_desc(bb + (uint32_t)p * 256u, 128u, 1024u);
+      const uint32_t acc = p > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+          "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+          : "memory");
+    }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+
+// Epilogue of one item: warp w reads lanes 32w..32w+31 of every tile from the
+// accumulator columns `tm` and writes the owned faces' outputs (contiguous runs
+// of 32 right-hand sides).
+__device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, int seg, int chunk, int warp,
+                                           int lane) {
+  constexpr int kTiles = kBS;
+  const int n1 = a.n1;
+  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+  const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
+  const int mrow = warp * 32 + lane;
+  const int s = mrow >> 6, r = mrow & 63;
+  float* ybase = a.Y + chunk * 64 + r;
+  for (int t0 = 0; t0 < kTiles; t0 += 2) {
+    // two tiles per wait: 32 columns of this warp's 32 lanes
+    uint32_t v[32];
+    const uint32_t taddr = tm + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t0 * kTileN);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int tt = 0; tt < 2; ++tt) {
+      const int t = t0 + tt;
+      const uint32_t* vt = v + tt * kTileN;
+      const int type = t / (kTiles / 2);
+      const int i = i0 + 2 * (t % (kTiles / 2)) + s;
+      if (i < nx) {
+        const bool bndrow = type == 0 ? (i == 0) : (j == 0);
+        const int eout = type == 0 ? i + (nx + 1) * j : nv + i + nx * j;
+        // fixed-trip loops over the tile's 16 columns keep v in registers
+#pragma unroll
+        for (int q = 0; q < kTileN; ++q)
+          if (q < n1) ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0f : __uint_as_float(vt[q]);
+        if (type == 0 && i == nx - 1) {
+          const int eb = nx + (nx + 1) * j;
+          for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
+        }
+        if (type == 1 && j == ny - 1) {
+          const int eb = nv + i + nx * ny;
+          for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
+        }
+      }
+    }
+  }
+}
+
+// Persistent CTAs, two-deep software pipeline over items (segment x 64
+// right-hand sides): while item n's MMAs run on the tensor cores, the CTA drains
+// item n-1 from tensor memory and item n+1's gather is in flight. Two windows
+// and two 128-column accumulators per CTA.
 __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t tileB = kTileN * 64 * 2;                // K = 64 (4 steps x 16)
-  unsigned char* W = sm;                                     // [5][18][1 KB]
-  unsigned char* Bbuf = sm + kWRows * kRowB;                 // [2][tileB]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-  constexpr int kTiles = kBS;                                // kBS/2 W pairs + kBS/2 S pairs
-  constexpr int kCols = kTiles * kTileN;                     // 8 tiles x 16 columns = 128
+  constexpr uint32_t winB = kWRows * kRowB;
+  // windows [2][5][kWSlots][1 KB] at sm and sm + winB
+  unsigned char* Bbuf = sm + 2 * winB;                       // [2][tileB]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);   // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  constexpr int kCols = 2 * kBS * kTileN;                    // two accumulators of 8 tiles x 16 columns
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -113,9 +240,12 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar)) : "memory");
+    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar + q)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // both windows zero (the node rows past k+1 stay zero), then the shared blocks
+  for (uint32_t o = (uint32_t)tid * 16u; o < 2u * winB; o += kThreads * 16u)
+    *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
   // shared blocks B (both face types), K-major core matrices: k = step*16 + h*8 + node
   for (int idx = tid; idx < 2 * kTileN * 64; idx += kThreads) {
     const int t = idx / (kTileN * 64), rem = idx % (kTileN * 64);
@@ -124,144 +254,74 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
                          (uint32_t)(k & 7) * 2u;
     *reinterpret_cast<__nv_bfloat16*>(Bbuf + t * tileB + off) = a.B[idx];
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-
-  const int n1 = a.n1;
-  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int chunks = a.nrhs / 64;
   const long items = (long)a.nseg * chunks;
-  unsigned phase = 0;
+  const long first = blockIdx.x, step = gridDim.x;
+  // per accumulator: mbarrier phase to wait for, and whether a commit is outstanding
+  unsigned ph0 = 0u, ph1 = 0u;
+  bool pend0 = false, pend1 = false;
   bool failed = false;
-  for (long item = blockIdx.x; item < items && !failed; item += gridDim.x) {
-    const int chunk = (int)(item % chunks);
-    const int seg = (int)(item / chunks);
-    const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
-    // ---- window: 5 rows x (kBS + 2) slots x 8 nodes x 8 groups of 16 bytes ----
-    for (int idx = tid; idx < kWRows * kWSlots * 64; idx += kThreads) {
-      const int g = idx & 7, nd = (idx >> 3) & 7, rs = idx >> 6;
-      const int r = rs / kWSlots, sl = rs - r * kWSlots;
-      const int i = i0 - 1 + sl;
-      long row = -1;
-      if (nd < n1) {
-        int edge = -1;
-        bool inb = false;
-        switch (r) {
-          case RV1: inb = j >= 1 && i >= 1 && i <= nx - 1; edge = i + (nx + 1) * (j - 1); break;
-          case RV0: inb = i >= 1 && i <= nx - 1; edge = i + (nx + 1) * j; break;
-          case RHM: inb = j >= 2 && i >= 0 && i < nx; edge = nv + i + nx * (j - 1); break;
-          case RH0: inb = j >= 1 && i >= 0 && i < nx; edge = nv + i + nx * j; break;
-          default: inb = j + 1 <= ny - 1 && i >= 0 && i < nx; edge = nv + i + nx * (j + 1); break;
-        }
-        // interior edges only (the boundary trace is zero)
-        if (inb) row = (long)edge * n1 + nd;
-      }
-      unsigned char* dst = W + (uint32_t)(r * kWSlots + sl) * kSlotB + (uint32_t)g * 128u + (uint32_t)nd * 16u;
-      if (row >= 0) {
-        const __nv_bfloat16* src = a.X + (size_t)row * a.nrhs + chunk * 64 + g * 8;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
-      } else {
-        *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
-      }
+  auto wait_acc = [&](int q) -> bool {          // wait for accumulator q's MMAs
+    const bool ok = mbar_wait_1s(bar + q, q ? ph1 : ph0);
+    if (ok) {
+      if (q) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    return ok;
+  };
+  if (first < items) gather_window(a, sm, (int)(first / chunks), (int)(first % chunks), tid);
+  long n = 0;
+  for (long item = first; item < items; item += step, ++n) {
+    const int buf = (int)(n & 1);
+    unsigned char* Wcur = sm + (buf ? winB : 0u);
+    unsigned char* Wnext = sm + (buf ? 0u : winB);
+    // this item's window is in shared memory (own cp.async groups + the others'
+    // zero stores), visible to the tensor cores
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- kBS tiles (kBS/2 W face pairs, kBS/2 S face pairs) x 4 K16 steps ----
-    if (tid == 0) {
-      const uint32_t wb = su32(W);
-      for (int t = 0; t < kTiles; ++t) {
-        const int type = t / (kTiles / 2), L = 2 * (t % (kTiles / 2));
-        const int sl = L + 1;                      // slot of the own element's W edge
-        const uint32_t bb = su32(Bbuf + type * tileB);
-        uint32_t start[4], lbo[4];
-        start[0] = wb + (uint32_t)(RV0 * kWSlots + sl) * kSlotB;  lbo[0] = kSlotB;   // own W, E
-        start[1] = wb + (uint32_t)(RH0 * kWSlots + sl) * kSlotB;  lbo[1] = kRowB;    // own S, N
-        if (type == 0) {                                                              // west neighbour
-          start[2] = wb + (uint32_t)(RV0 * kWSlots + sl - 1) * kSlotB;  lbo[2] = kSlotB;
-          start[3] = wb + (uint32_t)(RH0 * kWSlots + sl - 1) * kSlotB;  lbo[3] = kRowB;
-        } else {                                                                      // south neighbour
-          start[2] = wb + (uint32_t)(RV1 * kWSlots + sl) * kSlotB;  lbo[2] = kSlotB;
-          start[3] = wb + (uint32_t)(RHM * kWSlots + sl) * kSlotB;  lbo[3] = kRowB;
-        }
-        const uint32_t dcol = tmem + (uint32_t)(t * kTileN);
-        for (int p = 0; p < 4; ++p) {
-          const uint64_t ad = smem_desc(start[p], lbo[p], 128u);
-          const uint64_t bd = smem_desc(bb + (uint32_t)p * 256u, 128u, 1024u);
-          const uint32_t acc = p > 0 ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-              "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-              : "memory");
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
-                   : "memory");
-    }
-    const bool ok = mbar_wait_1s(bar, phase);
-    phase ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicExch(a.err, 2);
-        (void)mbar_wait_1s(bar, phase ^ 1u);
-      }
-      failed = true;
-    }
+    // the previous item's MMAs have finished: its window may be refilled and its
+    // accumulator drained
+    const bool ok = (n >= 1) ? wait_acc(buf ^ 1) : true;
+    if (__syncthreads_or(!ok)) { failed = true; break; }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!failed) {
-      // ---- epilogue: warp w reads lanes 32w..32w+31 of every tile ----
-      const int mrow = warp * 32 + lane;
-      const int s = mrow >> 6, r = mrow & 63;
-      float* ybase = a.Y + chunk * 64 + r;
-      for (int t0 = 0; t0 < kTiles; t0 += 2) {
-        // two tiles per wait: 32 columns of this warp's 32 lanes
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t0 * kTileN);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr)
-            : "memory");
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int tt = 0; tt < 2; ++tt) {
-        const int t = t0 + tt;
-        const uint32_t* vt = v + tt * kTileN;
-        const int type = t / (kTiles / 2);
-        const int i = i0 + 2 * (t % (kTiles / 2)) + s;
-        if (i < nx) {
-          const bool bndrow = type == 0 ? (i == 0) : (j == 0);
-          const int eout = type == 0 ? i + (nx + 1) * j : nv + i + nx * j;
-          for (int q = 0; q < n1; ++q)
-            ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0f : __uint_as_float(vt[q]);
-          if (type == 0 && i == nx - 1) {
-            const int eb = nx + (nx + 1) * j;
-            for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
-          }
-          if (type == 1 && j == ny - 1) {
-            const int eb = nv + i + nx * ny;
-            for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
-          }
-        }
-        }
-      }
+    if (tid == 0) issue_mmas(Wcur, Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), bar + buf);
+    if (buf) pend1 = true; else pend0 = true;
+    const long next = item + step;
+    if (next < items) gather_window(a, Wnext, (int)(next / chunks), (int)(next % chunks), tid);
+    if (n >= 1) {
+      const long prev = item - step;
+      drain_item(a, tmem + (uint32_t)((buf ^ 1) * kBS * kTileN), (int)(prev / chunks), (int)(prev % chunks), warp,
+                 lane);
     }
+    // the drained accumulator is free for item n+1 only after every warp's reads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
   }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!failed && n >= 1) {      // drain the last item
+    const int buf = (int)((n - 1) & 1);
+    const bool ok = wait_acc(buf);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+    } else {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const long last = first + (n - 1) * step;
+      drain_item(a, tmem + (uint32_t)(buf * kBS * kTileN), (int)(last / chunks), (int)(last % chunks), warp, lane);
+    }
+  }
+  if (failed) {
+    // an MMA commit did not arrive within the bound: flag it, let this thread's
+    // copies land, and give each outstanding commit one more bounded wait
+    if (tid == 0) atomicExch(a.err, 2);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (pend0) (void)wait_acc(0);
+    if (pend1) (void)wait_acc(1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
@@ -302,7 +362,7 @@ cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s) {
 
 size_t batched_smem_bytes(int n1) {
   (void)n1;
-  return (size_t)kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 16;
+  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 32;
 }
 
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s) {
@@ -314,8 +374,8 @@ cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, 
   if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
   HDG_CUDA_TRY(cudaFuncSetAttribute(batched_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin));
   const long items = (long)a.nseg * (nrhs / 64);
-  // four resident CTAs per SM (128 TMEM columns and ~54 KB shared memory each)
-  long blocks = (long)c->num_sms * 4;
+  // two resident CTAs per SM (256 TMEM columns and ~104 KB shared memory each)
+  long blocks = (long)c->num_sms * 2;
   if (blocks > items) blocks = items;
   batched_apply_kernel<<<(int)blocks, kThreads, smem, s>>>(a);
   return cudaGetLastError();
