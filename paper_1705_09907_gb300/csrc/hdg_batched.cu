@@ -102,10 +102,11 @@ __device__ __forceinline__ void gather_window(const BatchedArgs& a, unsigned cha
   const int n1 = a.n1;
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
-  const int per = kWRows * kWSlots * 8 * n1;                // (row, slot, group, node < n1)
-  for (int idx = tid; idx < per; idx += kThreads) {
-    const int nd = idx % n1, rest = idx / n1;
-    const int g = rest & 7, rs = rest >> 3;
+  const size_t rstride = (size_t)a.nrhs;                      // elements between node rows of X
+  // one thread per (row, slot, 16-byte group): the edge is found once, then its
+  // k+1 node rows follow with an address step
+  for (int idx = tid; idx < kWRows * kWSlots * 8; idx += kThreads) {
+    const int g = idx & 7, rs = idx >> 3;
     const int r = rs / kWSlots, sl = rs - r * kWSlots;
     const int i = i0 - 1 + sl;
     int edge = -1;
@@ -117,12 +118,16 @@ __device__ __forceinline__ void gather_window(const BatchedArgs& a, unsigned cha
       case RH0: inb = j >= 1 && i >= 0 && i < nx; edge = nv + i + nx * j; break;
       default: inb = j + 1 <= ny - 1 && i >= 0 && i < nx; edge = nv + i + nx * (j + 1); break;
     }
-    unsigned char* dst = W + (uint32_t)(r * kWSlots + sl) * kSlotB + (uint32_t)g * 128u + (uint32_t)nd * 16u;
+    const uint32_t dst = su32(W + (uint32_t)(r * kWSlots + sl) * kSlotB + (uint32_t)g * 128u);
     if (inb) {   // interior edges only (the boundary trace is zero)
-      const __nv_bfloat16* src = a.X + ((size_t)edge * n1 + nd) * a.nrhs + chunk * 64 + g * 8;
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+      const __nv_bfloat16* src = a.X + (size_t)edge * n1 * rstride + chunk * 64 + g * 8;
+      for (int nd = 0; nd < n1; ++nd)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)nd * 16u),
+                     "l"(src + (size_t)nd * rstride)
+                     : "memory");
     } else {
-      *reinterpret_cast<uint4*>(dst) = make_uint4(0u, 0u, 0u, 0u);
+      for (int nd = 0; nd < n1; ++nd)
+        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + (uint32_t)nd * 16u), "r"(0u) : "memory");
     }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
