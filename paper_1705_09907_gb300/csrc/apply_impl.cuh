@@ -519,7 +519,9 @@ __device__ __forceinline__ void seg_body(const ApplyArgs& a, int seg, const TS* 
       }
     }
   }
-  if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+  // one thread polls the copy's mbarrier (bounded) while the others sleep in the
+  // block barrier, leaving the issue slots to the SM's other CTAs
+  if (__syncthreads_or(threadIdx.x == 0 ? !mbar_wait_bounded(bar, 0) : 0)) {
     // the copy did not land within the bound: flag it, give it one more bounded
     // wait (it writes this CTA's shared memory), and leave together
     if (threadIdx.x == 0) {

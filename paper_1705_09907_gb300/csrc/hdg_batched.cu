@@ -268,8 +268,12 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
   unsigned ph0 = 0u, ph1 = 0u;
   bool pend0 = false, pend1 = false;
   bool failed = false;
-  auto wait_acc = [&](int q) -> bool {          // wait for accumulator q's MMAs
-    const bool ok = mbar_wait_1s(bar + q, q ? ph1 : ph0);
+  // wait for accumulator q's MMAs: one thread polls (bounded) while the others
+  // sleep in the block barrier; the result reaches every thread through it
+  auto wait_acc = [&](int q) -> bool {
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait_1s(bar + q, q ? ph1 : ph0);
+    ok = !__syncthreads_or(!ok);
     if (ok) {
       if (q) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
     }
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
     // the previous item's MMAs have finished: its window may be refilled and its
     // accumulator drained
     const bool ok = (n >= 1) ? wait_acc(buf ^ 1) : true;
-    if (__syncthreads_or(!ok)) { failed = true; break; }
+    if (!ok) { failed = true; break; }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (tid == 0) issue_mmas(Wcur, Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), bar + buf);
     if (buf) pend1 = true; else pend0 = true;
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
   if (!failed && n >= 1) {      // drain the last item
     const int buf = (int)((n - 1) & 1);
     const bool ok = wait_acc(buf);
-    if (__syncthreads_or(!ok)) {
+    if (!ok) {
       failed = true;
     } else {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
