@@ -255,6 +255,11 @@ def run_ours(args):
         apply_ms["bf16"] = timed_events(lambda: solver.apply(x32, "bf16", out=y32), args.apply_reps, torch)
         apply_ms["f32x2"] = timed_events(lambda: solver.apply(x64, "f32x2", out=y64), args.apply_reps, torch)
     clk = clocks.summary()
+    # the element-local operations of the step, timed alone
+    b_loc = solver.condense_rhs(fq_d)
+    local_ms = {"condense_rhs": timed_events(lambda: solver.condense_rhs(fq_d), 10, torch),
+                "recover_local": timed_events(lambda: solver.recover(lam, fq_d), 10, torch)}
+    del b_loc
     # mixed-precision solves on the same mesh (outside the clock window: reported, not the headline)
     lam64 = lam.clone()
     mixed = {}
@@ -438,7 +443,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (FP64 S + Schwarz blocks %.0f MB)" % (2 * nel * 16 * n1 * n1 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
-        "roofline": roof, "trace_apply": tra, "mixed": mixed, "mixed_1024_k3": m3, "batched_solve": bs,
+        "roofline": roof, "trace_apply": tra, "local_ops_ms": local_ms, "mixed": mixed, "mixed_1024_k3": m3,
+        "batched_solve": bs,
         "shared_batched_apply": sb, "multi_instance_apply": mi,
         "e2e": {"value": 1000.0 / e2e_ms, "unit": "solve/s", "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(fq_h.nbytes), "d2h_bytes_per_step": int(solver.ndof * 8 + u.numel() * 8)},

@@ -78,6 +78,29 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   c->off_P = put(c->ref.P); c->off_Mb = put(c->ref.Mb); c->off_Z = put(c->ref.Z); c->off_Eb = put(c->ref.Eb);
   c->off_Y = put(c->ref.Y); c->off_Ml = put(c->ref.Ml); c->off_MiBt = put(c->ref.MiBt); c->off_MiC = put(c->ref.MiC);
   c->off_Vf = put(c->ref.Vf); c->off_wJf = put(c->ref.wJf); c->off_M = put(c->ref.M);
+  // transposed copies: the warp-per-element kernels read a matrix's column
+  // (one entry per lane) as one contiguous row of the transpose
+  {
+    const RefTables& r = c->ref;
+    auto tr = [](const double* a, int rows, int cols) {
+      std::vector<double> t((size_t)rows * cols);
+      for (int i = 0; i < rows; ++i)
+        for (int j = 0; j < cols; ++j) t[(size_t)j * rows + i] = a[(size_t)i * cols + j];
+      return t;
+    };
+    c->off_ZT = put(tr(r.Z.data(), r.n, r.m));
+    c->off_EbT = put(tr(r.Eb.data(), r.n, r.m));
+    std::vector<double> mibt, mic;
+    for (int cmp = 0; cmp < 2; ++cmp) {
+      const std::vector<double> a = tr(r.MiBt.data() + (size_t)cmp * r.n * r.n, r.n, r.n);
+      const std::vector<double> b = tr(r.MiC.data() + (size_t)cmp * r.n * r.m, r.n, r.m);
+      mibt.insert(mibt.end(), a.begin(), a.end());
+      mic.insert(mic.end(), b.begin(), b.end());
+    }
+    c->off_MiBtT = put(mibt);
+    c->off_MiCT = put(mic);
+    c->off_VfT = put(tr(r.Vf.data(), r.nf, r.n));
+  }
   TRY(ctx_alloc(c, (void**)&c->d_ref, pack.size() * sizeof(double)));
   TRY(cudaMemcpyAsync(c->d_ref, pack.data(), pack.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   TRY(ctx_alloc(c, (void**)&c->err_flag, sizeof(int)));
@@ -94,8 +117,8 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   TRY(ctx_alloc(c, (void**)&c->edge_face, (size_t)c->n_edges * 2 * sizeof(int32_t)));
   TRY(launch_maps(c, s));
   const int n = c->ref.n, m = c->ref.m;
-  TRY(ctx_alloc(c, (void**)&c->Lfac, (size_t)c->nel * (n * (n + 1) / 2) * sizeof(double)));
-  TRY(ctx_alloc(c, (void**)&c->Vfac, (size_t)c->nel * n * m * sizeof(double)));
+  TRY(ctx_alloc(c, (void**)&c->Ainv, (size_t)c->nel * n * n * sizeof(double)));
+  TRY(ctx_alloc(c, (void**)&c->Gfac, (size_t)c->nel * n * m * sizeof(double)));
   TRY(ctx_alloc(c, (void**)&c->elem_scratch, (size_t)c->nel * m * sizeof(double)));
   // p-levels
   c->plev.resize(k + 1);

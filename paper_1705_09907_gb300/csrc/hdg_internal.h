@@ -116,10 +116,11 @@ struct Context {
   double* d_ref = nullptr;                  // device copy of the finest tables
   size_t off_P = 0, off_Mb = 0, off_Z = 0, off_Eb = 0, off_Y = 0, off_Ml = 0,
          off_MiBt = 0, off_MiC = 0, off_Vf = 0, off_wJf = 0, off_M = 0;
+  size_t off_ZT = 0, off_EbT = 0, off_MiBtT = 0, off_MiCT = 0, off_VfT = 0;   // transposes
   double* elem_scratch = nullptr;           // [nel][m] per-element partial results
-  // finest-level local factors: Cholesky L of A_u (packed lower) and V = L^-1 W
-  double* Lfac = nullptr;                   // [nel][n(n+1)/2]
-  double* Vfac = nullptr;                   // [nel][n][m]
+  // finest-level local operators: A_u^-1 (symmetric, stored full) and G = A_u^-1 W
+  double* Ainv = nullptr;                   // [nel][n][n]
+  double* Gfac = nullptr;                   // [nel][n][m]
   std::vector<PLevel> plev;                 // index p = 0..k
   std::vector<HLevel> hlev;                 // finest Q1 first
   double* coarse_L = nullptr;               // dense FP64 Cholesky factor [nc][nc]

@@ -25,19 +25,22 @@ __device__ __forceinline__ int hedge(int i, int j, int nx, int ny) { return (nx 
 // ---------------------------------------------------------------------------
 // Local solver on the finest level: one warp per element.
 //   A_u = kappa P + tau Mb, W = kappa Z + tau Eb, A_u = L L^T,
-//   V = L^-1 W, S = kappa Y + tau diag(Ml) - V^T V.
+//   V = L^-1 W, S = kappa Y + tau diag(Ml) - V^T V,
+// and for the element-local operations around the solve A_u^-1 = L^-T L^-1 and
+// G = A_u^-1 W = L^-T V (no triangular solves are left for those kernels).
 struct LocalTables {
   const double *P, *Mb, *Z, *Eb, *Y, *Ml;
 };
 
 __global__ void local_setup_kernel(int nel, int n, int m, double tau, const double* __restrict__ kappa,
-                                   LocalTables tb, double* __restrict__ Sout, double* __restrict__ Lout,
-                                   double* __restrict__ Vout, int* err) {
+                                   LocalTables tb, double* __restrict__ Sout, double* __restrict__ Ainv_out,
+                                   double* __restrict__ Gout, int* err) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  double* A = sm + (size_t)wid * (n * n + n * m);
+  double* A = sm + (size_t)wid * (2 * n * n + n * m);
   double* W = A + n * n;
+  double* X = W + n * m;                     // A_u^-1, one column per lane
   for (int e = blockIdx.x * wpb + wid; e < nel; e += gridDim.x * wpb) {
     const double kap = kappa[e];
     for (int idx = lane; idx < n * n; idx += 32) A[idx] = kap * tb.P[idx] + tau * tb.Mb[idx];
@@ -77,20 +80,37 @@ __global__ void local_setup_kernel(int nel, int n, int m, double tau, const doub
       for (int i = 0; i < n; ++i) s -= W[i * m + r] * W[i * m + c];
       S[idx] = s;
     }
-    if (Lout) {
-      double* L = Lout + (size_t)e * (n * (n + 1) / 2);
-      for (int idx = lane; idx < n * (n + 1) / 2; idx += 32) {
-        // packed row-major lower triangle: row i holds i+1 entries
-        int i = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
-        while ((i + 1) * (i + 2) / 2 <= idx) ++i;
-        while (i * (i + 1) / 2 > idx) --i;
-        const int l = idx - i * (i + 1) / 2;
-        L[idx] = A[i * n + l];
+    // A_u^-1 column j (lane j, j + 32): L^-1 e_j forward, then L^-T backward
+    for (int j = lane; j < n; j += 32) {
+      for (int i = 0; i < n; ++i) {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int l = j; l < i; ++l) s -= A[i * n + l] * X[l * n + j];
+        X[i * n + j] = i < j ? 0.0 : s / A[i * n + i];
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        double s = X[i * n + j];
+        for (int l = i + 1; l < n; ++l) s -= A[l * n + i] * X[l * n + j];
+        X[i * n + j] = s / A[i * n + i];
       }
     }
-    if (Vout) {
-      double* V = Vout + (size_t)e * n * m;
-      for (int idx = lane; idx < n * m; idx += 32) V[idx] = W[idx];
+    // G = L^-T V, one column per lane, in place (after every lane's S entries
+    // have read V)
+    __syncwarp();
+    for (int c = lane; c < m; c += 32) {
+      for (int i = n - 1; i >= 0; --i) {
+        double s = W[i * m + c];
+        for (int l = i + 1; l < n; ++l) s -= A[l * n + i] * W[l * m + c];
+        W[i * m + c] = s / A[i * n + i];
+      }
+    }
+    __syncwarp();
+    if (Ainv_out) {
+      double* Ao = Ainv_out + (size_t)e * n * n;
+      for (int idx = lane; idx < n * n; idx += 32) Ao[idx] = X[idx];
+    }
+    if (Gout) {
+      double* G = Gout + (size_t)e * n * m;
+      for (int idx = lane; idx < n * m; idx += 32) G[idx] = W[idx];
     }
     __syncwarp();
   }
@@ -98,7 +118,7 @@ __global__ void local_setup_kernel(int nel, int n, int m, double tau, const doub
 
 cudaError_t launch_local_setup(Context* c, cudaStream_t s) {
   const int n = c->ref.n, m = c->ref.m;
-  const size_t per_warp = (size_t)(n * n + n * m) * sizeof(double);
+  const size_t per_warp = (size_t)(2 * n * n + n * m) * sizeof(double);
   int wpb = (int)((96 * 1024) / per_warp);
   if (wpb < 1) wpb = 1;
   if (wpb > 8) wpb = 8;
@@ -110,7 +130,7 @@ cudaError_t launch_local_setup(Context* c, cudaStream_t s) {
   const int cap = c->num_sms * 16;
   if (blocks > cap) blocks = cap;
   local_setup_kernel<<<blocks, 32 * wpb, smem, s>>>(c->nel, n, m, c->opt.tau, c->kappa, tb,
-                                                    c->plev[c->k].Sdense, c->Lfac, c->Vfac, c->err_flag);
+                                                    c->plev[c->k].Sdense, c->Ainv, c->Gfac, c->err_flag);
   return cudaGetLastError();
 }
 
