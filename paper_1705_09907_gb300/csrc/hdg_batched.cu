@@ -25,7 +25,6 @@ namespace {
 
 constexpr int kTileM = 128;
 constexpr int kTileN = 16;
-constexpr int kThreads = 128;
 
 struct BatchedArgs {
   const __nv_bfloat16* X;     // [ndof][nrhs]
@@ -98,14 +97,15 @@ enum { RV1 = 0, RV0 = 1, RHM = 2, RH0 = 3, RH1 = 4 };
 // Gather one item's window (segment seg, right-hand sides chunk*64 ..): the
 // interior edges' node rows by cp.async (one commit group), zeros for edges
 // outside the mesh. Node rows nd >= k+1 are zero from the start and never written.
-__device__ __forceinline__ void gather_window(const BatchedArgs& a, unsigned char* W, int seg, int chunk, int tid) {
+__device__ __forceinline__ void gather_window(const BatchedArgs& a, unsigned char* W, int seg, int chunk, int tid,
+                                              int nthreads) {
   const int n1 = a.n1;
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
   const size_t rstride = (size_t)a.nrhs;                      // elements between node rows of X
   // one thread per (row, slot, 16-byte group): the edge is found once, then its
   // k+1 node rows follow with an address step
-  for (int idx = tid; idx < kWRows * kWSlots * 8; idx += kThreads) {
+  for (int idx = tid; idx < kWRows * kWSlots * 8; idx += nthreads) {
     const int g = idx & 7, rs = idx >> 3;
     const int r = rs / kWSlots, sl = rs - r * kWSlots;
     const int i = i0 - 1 + sl;
@@ -139,30 +139,34 @@ __device__ __forceinline__ void issue_mmas(const unsigned char* W, const unsigne
                                            uint64_t* bar) {
   constexpr uint32_t tileB = kTileN * 64 * 2;
   constexpr int kTiles = kBS;
-  const uint32_t wb = su32(W);
+  // descriptors = fixed fields + (address >> 4); shared addresses stay below 256 KB,
+  // so the 14-bit address field never carries into the next field
+  const uint64_t dslot = smem_desc(0u, kSlotB, 128u), drow = smem_desc(0u, kRowB, 128u);
+  const uint32_t wb4 = su32(W) >> 4;
+  const uint64_t db0 = smem_desc(su32(Bbuf), 128u, 1024u), db1 = smem_desc(su32(Bbuf + tileB), 128u, 1024u);
+#pragma unroll
   for (int t = 0; t < kTiles; ++t) {
     const int type = t / (kTiles / 2), L = 2 * (t % (kTiles / 2));
     const int sl = L + 1;                      // slot of the own element's W edge
-    const uint32_t bb = su32(Bbuf + type * tileB);
-    uint32_t start[4], lbo[4];
-    start[0] = wb + (uint32_t)(RV0 * kWSlots + sl) * kSlotB;  lbo[0] = kSlotB;   // own W, E
-    start[1] = wb + (uint32_t)(RH0 * kWSlots + sl) * kSlotB;  lbo[1] = kRowB;    // own S, N
-    if (type == 0) {                                                              // west neighbour
-      start[2] = wb + (uint32_t)(RV0 * kWSlots + sl - 1) * kSlotB;  lbo[2] = kSlotB;
-      start[3] = wb + (uint32_t)(RH0 * kWSlots + sl - 1) * kSlotB;  lbo[3] = kRowB;
-    } else {                                                                      // south neighbour
-      start[2] = wb + (uint32_t)(RV1 * kWSlots + sl) * kSlotB;  lbo[2] = kSlotB;
-      start[3] = wb + (uint32_t)(RHM * kWSlots + sl) * kSlotB;  lbo[3] = kRowB;
+    const uint64_t bd0 = type ? db1 : db0;
+    uint64_t ad[4];
+    ad[0] = dslot + wb4 + (uint32_t)(RV0 * kWSlots + sl) * (kSlotB >> 4);   // own W, E
+    ad[1] = drow + wb4 + (uint32_t)(RH0 * kWSlots + sl) * (kSlotB >> 4);    // own S, N
+    if (type == 0) {                                                         // west neighbour
+      ad[2] = dslot + wb4 + (uint32_t)(RV0 * kWSlots + sl - 1) * (kSlotB >> 4);
+      ad[3] = drow + wb4 + (uint32_t)(RH0 * kWSlots + sl - 1) * (kSlotB >> 4);
+    } else {                                                                 // south neighbour
+      ad[2] = dslot + wb4 + (uint32_t)(RV1 * kWSlots + sl) * (kSlotB >> 4);
+      ad[3] = drow + wb4 + (uint32_t)(RHM * kWSlots + sl) * (kSlotB >> 4);
     }
     const uint32_t dcol = tm + (uint32_t)(t * kTileN);
+#pragma unroll
     for (int p = 0; p < 4; ++p) {
-      const uint64_t ad = smem_desc(start[p], lbo[p], 128u);
-      const uint64_t bd = smem_desc(bb + (uint32_t)p * 256u, 128u, 1024u);
-      const uint32_t acc = p > 0 ? 1u : 0u;
+      const uint64_t bd = bd0 + (uint32_t)p * 16u;            // next 256 bytes of B
       asm volatile(
           "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-          "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+          "l"(ad[p]), "l"(bd), "r"(kIdesc), "r"(p > 0 ? 1u : 0u)
           : "memory");
     }
   }
@@ -223,19 +227,34 @@ __device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, in
   }
 }
 
-// Persistent CTAs, two-deep software pipeline over items (segment x 64
-// right-hand sides): while item n's MMAs run on the tensor cores, the CTA drains
-// item n-1 from tensor memory and item n+1's gather is in flight. Two windows
-// and two 128-column accumulators per CTA.
-__global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) {
+// Persistent CTAs with two warp groups and a two-deep pipeline over items
+// (segment x 64 right-hand sides):
+//   producer warps 4..7 gather item n into window n%2 (cp.async), and one thread
+//     issues its 32 MMAs into accumulator n%2, committing to mma_done[n%2];
+//   drain warps 0..3 (one TMEM lane quadrant each) wait for mma_done[n%2], write
+//     the item's faces and release the accumulator through tmem_free[n%2].
+// A window is refilled only after the MMAs that read it completed, an accumulator
+// only after it was drained. Every wait is bounded (1 s) and polled by one thread
+// of its group while the others wait in the group's named barrier.
+constexpr int kDrainWarps = 4, kProdWarps = 4;
+constexpr int kSpecThreads = 32 * (kDrainWarps + kProdWarps);
+
+__device__ __forceinline__ void group_sync(int id) {
+  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+
+__global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t tileB = kTileN * 64 * 2;                // K = 64 (4 steps x 16)
   constexpr uint32_t winB = kWRows * kRowB;
   // windows [2][5][kWSlots][1 KB] at sm and sm + winB
   unsigned char* Bbuf = sm + 2 * winB;                       // [2][tileB]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);   // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* mma_done = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);   // [2]
+  uint64_t* tmem_free = mma_done + 2;                                     // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_free + 2);
+  volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 1);  // [0] drain failed, [1] producer failed,
+                                                                         // [2], [3] commits issued per buffer
   constexpr int kCols = 2 * kBS * kTileN;                    // two accumulators of 8 tiles x 16 columns
 
   if (warp == 0) {
@@ -245,91 +264,99 @@ __global__ void __launch_bounds__(kThreads) batched_apply_kernel(BatchedArgs a) 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int q = 0; q < 2; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bar + q)) : "memory");
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mma_done + q)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(tmem_free + q)), "r"(kDrainWarps) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    flags[0] = 0; flags[1] = 0; flags[2] = 0; flags[3] = 0;
   }
   // both windows zero (the node rows past k+1 stay zero), then the shared blocks
-  for (uint32_t o = (uint32_t)tid * 16u; o < 2u * winB; o += kThreads * 16u)
+  for (uint32_t o = (uint32_t)tid * 16u; o < 2u * winB; o += kSpecThreads * 16u)
     *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
-  // shared blocks B (both face types), K-major core matrices: k = step*16 + h*8 + node
-  for (int idx = tid; idx < 2 * kTileN * 64; idx += kThreads) {
+  for (int idx = tid; idx < 2 * kTileN * 64; idx += kSpecThreads) {
     const int t = idx / (kTileN * 64), rem = idx % (kTileN * 64);
     const int n = rem / 64, k = rem % 64;
     const uint32_t off = (uint32_t)(n >> 3) * 1024u + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u +
                          (uint32_t)(k & 7) * 2u;
     *reinterpret_cast<__nv_bfloat16*>(Bbuf + t * tileB + off) = a.B[idx];
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const int chunks = a.nrhs / 64;
   const long items = (long)a.nseg * chunks;
   const long first = blockIdx.x, step = gridDim.x;
-  // per accumulator: mbarrier phase to wait for, and whether a commit is outstanding
-  unsigned ph0 = 0u, ph1 = 0u;
-  bool pend0 = false, pend1 = false;
-  bool failed = false;
-  // wait for accumulator q's MMAs: one thread polls (bounded) while the others
-  // sleep in the block barrier; the result reaches every thread through it
-  auto wait_acc = [&](int q) -> bool {
-    bool ok = true;
-    if (tid == 0) ok = mbar_wait_1s(bar + q, q ? ph1 : ph0);
-    ok = !__syncthreads_or(!ok);
-    if (ok) {
-      if (q) { ph1 ^= 1u; pend1 = false; } else { ph0 ^= 1u; pend0 = false; }
-    }
-    return ok;
-  };
-  if (first < items) gather_window(a, sm, (int)(first / chunks), (int)(first % chunks), tid);
-  long n = 0;
-  for (long item = first; item < items; item += step, ++n) {
-    const int buf = (int)(n & 1);
-    unsigned char* Wcur = sm + (buf ? winB : 0u);
-    unsigned char* Wnext = sm + (buf ? 0u : winB);
-    // this item's window is in shared memory (own cp.async groups + the others'
-    // zero stores), visible to the tensor cores
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // the previous item's MMAs have finished: its window may be refilled and its
-    // accumulator drained
-    const bool ok = (n >= 1) ? wait_acc(buf ^ 1) : true;
-    if (!ok) { failed = true; break; }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) issue_mmas(Wcur, Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), bar + buf);
-    if (buf) pend1 = true; else pend0 = true;
-    const long next = item + step;
-    if (next < items) gather_window(a, Wnext, (int)(next / chunks), (int)(next % chunks), tid);
-    if (n >= 1) {
-      const long prev = item - step;
-      drain_item(a, tmem + (uint32_t)((buf ^ 1) * kBS * kTileN), (int)(prev / chunks), (int)(prev % chunks), warp,
-                 lane);
-    }
-    // the drained accumulator is free for item n+1 only after every warp's reads
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  }
-  if (!failed && n >= 1) {      // drain the last item
-    const int buf = (int)((n - 1) & 1);
-    const bool ok = wait_acc(buf);
-    if (!ok) {
-      failed = true;
-    } else {
+
+  if (warp >= kDrainWarps) {
+    // ---------------- producer group ----------------
+    const int ptid = tid - 32 * kDrainWarps;
+    unsigned pd0 = 0u, pd1 = 0u, pf0 = 0u, pf1 = 0u;   // phases to wait for, per buffer
+    bool failed = false;
+    long n = 0;
+    for (long item = first; item < items; item += step, ++n) {
+      const int buf = (int)(n & 1);
+      unsigned char* Wcur = sm + (buf ? winB : 0u);
+      if (n >= 2) {
+        // window buf was read by item n-2's MMAs; accumulator buf was drained after them
+        bool ok = true;
+        if (ptid == 0) {
+          ok = mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0);
+          if (ok) ok = mbar_wait_1s(tmem_free + buf, buf ? pf1 : pf0);
+          if (!ok) flags[1] = 1;
+        }
+        group_sync(1);
+        if (flags[1]) { failed = true; break; }
+        if (buf) { pd1 ^= 1u; pf1 ^= 1u; } else { pd0 ^= 1u; pf0 ^= 1u; }
+      }
+      gather_window(a, Wcur, (int)(item / chunks), (int)(item % chunks), ptid, kProdWarps * 32);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      group_sync(1);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const long last = first + (n - 1) * step;
-      drain_item(a, tmem + (uint32_t)(buf * kBS * kTileN), (int)(last / chunks), (int)(last % chunks), warp, lane);
+      if (ptid == 0) {
+        issue_mmas(Wcur, Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), mma_done + buf);
+        flags[2 + buf] = flags[2 + buf] + 1;
+      }
     }
-  }
-  if (failed) {
-    // an MMA commit did not arrive within the bound: flag it, let this thread's
-    // copies land, and give each outstanding commit one more bounded wait
-    if (tid == 0) atomicExch(a.err, 2);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (pend0) (void)wait_acc(0);
-    if (pend1) (void)wait_acc(1);
+    if (failed) asm volatile("cp.async.wait_all;" ::: "memory");
+  } else {
+    // ---------------- drain group ----------------
+    unsigned pd0 = 0u, pd1 = 0u;
+    long n = 0;
+    for (long item = first; item < items; item += step, ++n) {
+      const int buf = (int)(n & 1);
+      bool ok = true;
+      if (tid == 0) {
+        ok = mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0);
+        if (!ok) flags[0] = 1;
+      }
+      group_sync(2);
+      if (flags[0]) break;
+      if (buf) pd1 ^= 1u; else pd0 ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      drain_item(a, tmem + (uint32_t)(buf * kBS * kTileN), (int)(item / chunks), (int)(item % chunks), warp, lane);
+      // this warp's reads of the accumulator are complete: release it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(tmem_free + buf)) : "memory");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (flags[0] || flags[1]) {
+    // a wait ran out: flag it, and give the last commit issued on each
+    // accumulator (at most one is outstanding per accumulator) one more bounded
+    // wait before its tensor memory is freed
+    if (tid == 0) {
+      atomicExch(a.err, 2);
+      for (int q = 0; q < 2; ++q)
+        if (flags[2 + q] > 0) (void)mbar_wait_1s(mma_done + q, (unsigned)((flags[2 + q] - 1) & 1));
+    }
+    __syncthreads();
+  }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
@@ -371,7 +398,7 @@ cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s) {
 
 size_t batched_smem_bytes(int n1) {
   (void)n1;
-  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 32;
+  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 64;   // + 4 mbarriers, TMEM slot, 4 flags
 }
 
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s) {
@@ -386,7 +413,7 @@ cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, 
   // two resident CTAs per SM (256 TMEM columns and ~104 KB shared memory each)
   long blocks = (long)c->num_sms * 2;
   if (blocks > items) blocks = items;
-  batched_apply_kernel<<<(int)blocks, kThreads, smem, s>>>(a);
+  batched_apply_kernel<<<(int)blocks, kSpecThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
