@@ -178,18 +178,18 @@ __device__ __forceinline__ void issue_mmas(const unsigned char* W, const unsigne
 // accumulator columns `tm` and writes the owned faces' outputs (contiguous runs
 // of 32 right-hand sides).
 __device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, int seg, int chunk, int warp,
-                                           int lane) {
+                                           int lane, int tbeg, int tend) {
   constexpr int kTiles = kBS;
   const int n1 = a.n1;
   const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
   const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
-  const int mrow = warp * 32 + lane;
+  const int mrow = (warp & 3) * 32 + lane;                   // TMEM lane quadrant of this warp
   const int s = mrow >> 6, r = mrow & 63;
   float* ybase = a.Y + chunk * 64 + r;
-  for (int t0 = 0; t0 < kTiles; t0 += 2) {
+  for (int t0 = tbeg; t0 < tend; t0 += 2) {
     // two tiles per wait: 32 columns of this warp's 32 lanes
     uint32_t v[32];
-    const uint32_t taddr = tm + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t0 * kTileN);
+    const uint32_t taddr = tm + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(t0 * kTileN);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -227,20 +227,25 @@ __device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, in
   }
 }
 
-// Persistent CTAs with two warp groups and a two-deep pipeline over items
+// Persistent CTAs with warp-specialized roles and a two-deep pipeline over items
 // (segment x 64 right-hand sides):
-//   producer warps 4..7 gather item n into window n%2 (cp.async), and one thread
-//     issues its 32 MMAs into accumulator n%2, committing to mma_done[n%2];
-//   drain warps 0..3 (one TMEM lane quadrant each) wait for mma_done[n%2], write
-//     the item's faces and release the accumulator through tmem_free[n%2].
+//   gather warps 8..10 fill window n%2 by cp.async; each thread's copies arrive
+//     on full[n%2] when they land (cp.async.mbarrier.arrive);
+//   warp 11 (one thread) waits for full[n%2], issues the item's 32 MMAs into
+//     accumulator n%2 and commits them to mma_done[n%2];
+//   drain warps 0..7 wait for mma_done[n%2] and write the item's faces (warp w
+//     reads TMEM lane quadrant w%4, tiles 4(w/4) .. 4(w/4)+3), then release the
+//     accumulator through tmem_free[n%2].
 // A window is refilled only after the MMAs that read it completed, an accumulator
-// only after it was drained. Every wait is bounded (1 s) and polled by one thread
-// of its group while the others wait in the group's named barrier.
-constexpr int kDrainWarps = 4, kProdWarps = 4;
-constexpr int kSpecThreads = 32 * (kDrainWarps + kProdWarps);
+// only after it was drained. Every wait is bounded (1 s); a role whose wait runs
+// out stops, and the others then run out of their own waits.
+constexpr int kDrainWarps = 8, kGatherWarps = 3;
+constexpr int kSpecThreads = 32 * (kDrainWarps + kGatherWarps + 1);
+constexpr int kGatherThreads = 32 * kGatherWarps;
+constexpr int kIssueWarp = kDrainWarps + kGatherWarps;
 
-__device__ __forceinline__ void group_sync(int id) {
-  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs a) {
@@ -250,11 +255,12 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
   constexpr uint32_t winB = kWRows * kRowB;
   // windows [2][5][kWSlots][1 KB] at sm and sm + winB
   unsigned char* Bbuf = sm + 2 * winB;                       // [2][tileB]
-  uint64_t* mma_done = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);   // [2]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);       // [2]
+  uint64_t* mma_done = full + 2;                                          // [2]
   uint64_t* tmem_free = mma_done + 2;                                     // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_free + 2);
-  volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 1);  // [0] drain failed, [1] producer failed,
-                                                                         // [2], [3] commits issued per buffer
+  // [0] drain, [1] gather, [2] issuer failed; [3], [4] commits issued per accumulator
+  volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 1);
   constexpr int kCols = 2 * kBS * kTileN;                    // two accumulators of 8 tiles x 16 columns
 
   if (warp == 0) {
@@ -265,11 +271,12 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
   }
   if (tid == 0) {
     for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(full + q)), "r"(kGatherThreads) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mma_done + q)) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(tmem_free + q)), "r"(kDrainWarps) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    flags[0] = 0; flags[1] = 0; flags[2] = 0; flags[3] = 0;
+    for (int q = 0; q < 5; ++q) flags[q] = 0;
   }
   // both windows zero (the node rows past k+1 stay zero), then the shared blocks
   for (uint32_t o = (uint32_t)tid * 16u; o < 2u * winB; o += kSpecThreads * 16u)
@@ -281,6 +288,7 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
                          (uint32_t)(k & 7) * 2u;
     *reinterpret_cast<__nv_bfloat16*>(Bbuf + t * tileB + off) = a.B[idx];
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -289,71 +297,71 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
   const long items = (long)a.nseg * chunks;
   const long first = blockIdx.x, step = gridDim.x;
 
-  if (warp >= kDrainWarps) {
-    // ---------------- producer group ----------------
-    const int ptid = tid - 32 * kDrainWarps;
-    unsigned pd0 = 0u, pd1 = 0u, pf0 = 0u, pf1 = 0u;   // phases to wait for, per buffer
-    bool failed = false;
-    long n = 0;
-    for (long item = first; item < items; item += step, ++n) {
-      const int buf = (int)(n & 1);
-      unsigned char* Wcur = sm + (buf ? winB : 0u);
-      if (n >= 2) {
-        // window buf was read by item n-2's MMAs; accumulator buf was drained after them
-        bool ok = true;
-        if (ptid == 0) {
-          ok = mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0);
-          if (ok) ok = mbar_wait_1s(tmem_free + buf, buf ? pf1 : pf0);
-          if (!ok) flags[1] = 1;
-        }
-        group_sync(1);
-        if (flags[1]) { failed = true; break; }
-        if (buf) { pd1 ^= 1u; pf1 ^= 1u; } else { pd0 ^= 1u; pf0 ^= 1u; }
-      }
-      gather_window(a, Wcur, (int)(item / chunks), (int)(item % chunks), ptid, kProdWarps * 32);
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      group_sync(1);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (ptid == 0) {
-        issue_mmas(Wcur, Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), mma_done + buf);
-        flags[2 + buf] = flags[2 + buf] + 1;
-      }
-    }
-    if (failed) asm volatile("cp.async.wait_all;" ::: "memory");
-  } else {
-    // ---------------- drain group ----------------
+  if (warp < kDrainWarps) {
+    // ---------------- drain ----------------
     unsigned pd0 = 0u, pd1 = 0u;
+    const int tbeg = (warp >> 2) * (kBS / 2);
     long n = 0;
     for (long item = first; item < items; item += step, ++n) {
       const int buf = (int)(n & 1);
-      bool ok = true;
-      if (tid == 0) {
-        ok = mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0);
-        if (!ok) flags[0] = 1;
-      }
-      group_sync(2);
+      if (tid == 0 && !mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0)) flags[0] = 1;
+      named_sync(1, 32 * kDrainWarps);
       if (flags[0]) break;
       if (buf) pd1 ^= 1u; else pd0 ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      drain_item(a, tmem + (uint32_t)(buf * kBS * kTileN), (int)(item / chunks), (int)(item % chunks), warp, lane);
-      // this warp's reads of the accumulator are complete: release it
+      drain_item(a, tmem + (uint32_t)(buf * kBS * kTileN), (int)(item / chunks), (int)(item % chunks), warp, lane,
+                 tbeg, tbeg + kBS / 2);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(tmem_free + buf)) : "memory");
     }
+  } else if (warp < kIssueWarp) {
+    // ---------------- gather ----------------
+    const int gtid = tid - 32 * kDrainWarps;
+    unsigned pd0 = 0u, pd1 = 0u;
+    long n = 0;
+    for (long item = first; item < items; item += step, ++n) {
+      const int buf = (int)(n & 1);
+      if (n >= 2) {      // window buf was read by item n-2's MMAs
+        if (gtid == 0 && !mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0)) flags[1] = 1;
+        named_sync(2, kGatherThreads);
+        if (flags[1]) break;
+        if (buf) pd1 ^= 1u; else pd0 ^= 1u;
+      }
+      gather_window(a, sm + (buf ? winB : 0u), (int)(item / chunks), (int)(item % chunks), gtid, kGatherThreads);
+      // zero stores visible to the tensor cores; the copies arrive when they land
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(full + buf)) : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (lane == 0) {
+    // ---------------- MMA issue ----------------
+    unsigned pf0 = 0u, pf1 = 0u, pt0 = 0u, pt1 = 0u;
+    long n = 0;
+    for (long item = first; item < items; item += step, ++n) {
+      const int buf = (int)(n & 1);
+      if (!mbar_wait_1s(full + buf, buf ? pf1 : pf0)) { flags[2] = 1; break; }
+      if (buf) pf1 ^= 1u; else pf0 ^= 1u;
+      if (n >= 2) {      // accumulator buf was drained
+        if (!mbar_wait_1s(tmem_free + buf, buf ? pt1 : pt0)) { flags[2] = 1; break; }
+        if (buf) pt1 ^= 1u; else pt0 ^= 1u;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue_mmas(sm + (buf ? winB : 0u), Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), mma_done + buf);
+      flags[3 + buf] = flags[3 + buf] + 1;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (flags[0] || flags[1]) {
+  if (flags[0] || flags[1] || flags[2]) {
     // a wait ran out: flag it, and give the last commit issued on each
     // accumulator (at most one is outstanding per accumulator) one more bounded
     // wait before its tensor memory is freed
     if (tid == 0) {
       atomicExch(a.err, 2);
       for (int q = 0; q < 2; ++q)
-        if (flags[2 + q] > 0) (void)mbar_wait_1s(mma_done + q, (unsigned)((flags[2 + q] - 1) & 1));
+        if (flags[3 + q] > 0) (void)mbar_wait_1s(mma_done + q, (unsigned)((flags[3 + q] - 1) & 1));
     }
     __syncthreads();
   }
@@ -398,7 +406,7 @@ cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s) {
 
 size_t batched_smem_bytes(int n1) {
   (void)n1;
-  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 64;   // + 4 mbarriers, TMEM slot, 4 flags
+  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 80;   // + 6 mbarriers, TMEM slot, 5 flags
 }
 
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s) {
