@@ -63,21 +63,24 @@ struct dfloat {
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v, float) { return __bfloat162float(v); }
 __device__ __forceinline__ dfloat to_acc(float2 v, dfloat) { return dfloat{v.x, v.y}; }
 // double -> (hi, lo) with integer operations and one FP32 subtraction (the FP64
-// pipe, which also runs int <-> float conversions, is slow on this GPU): hi
-// keeps the leading 24 significant bits (truncated); lo is the remaining 29
-// bits rounded to 24: the rounded bits are placed under the exponent 2^E of
-// lo's scale, and subtracting 2^E (exact, both operands in [2^E, 2^(E+1)])
-// leaves them as a float. hi + lo = v to about 2^-47 relative. Magnitudes below
-// 2^-74 (where lo would leave the normal float range), zero and huge values
-// take the conversion path.
+// pipe, which also runs int <-> float and float <-> double conversions, is slow on
+// this GPU): hi keeps the leading 24 significant bits (truncated); lo is the
+// remaining 29 bits rounded to 24: the rounded bits are placed under the exponent
+// 2^E of lo's scale, and subtracting 2^E (exact, both operands in [2^E, 2^(E+1)])
+// leaves them as a float. hi + lo = v to about 2^-47 relative. Zero is built from
+// its bits; magnitudes below 2^-103 (where lo would leave the normal float range)
+// and above 2^127 take a conversion path kept out of line, so it is a real branch
+// and its conversions are not executed (predicated) for every value.
+static __device__ __noinline__ dfloat split_double_rare(double v) {
+  const float h = __double2float_rn(v);
+  return dfloat{h, __double2float_rn(v - (double)h)};
+}
 __device__ __forceinline__ dfloat split_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
   const int e = (int)((b >> 52) & 0x7ff);
-  if (e < 949 || e > 1150) {              // |v| < 2^-74, zero, huge: conversion path
-    const float h = __double2float_rn(v);
-    return dfloat{h, __double2float_rn(v - (double)h)};
-  }
+  if ((b << 1) == 0ull) return dfloat{__uint_as_float(sign), 0.0f};            // +-0
+  if (__builtin_expect(e < 920 || e > 1150, 0)) return split_double_rare(v);
   const unsigned long long mant = b & 0xfffffffffffffull;
   const unsigned int hib = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29);
   const unsigned int rem = (unsigned int)(mant & 0x1fffffffull);          // 29 bits below hi
@@ -106,13 +109,12 @@ __device__ __forceinline__ dfloat mac(dfloat s, dfloat x, dfloat acc) {
 }
 // float -> double from the bits (exact for normal floats and zero): the
 // conversion instruction runs on the FP64 pipe, which is slow on this GPU
+static __device__ __noinline__ double f2d_rare(float f) { return (double)f; }   // subnormal, inf, nan
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned int u = __float_as_uint(f);
   const unsigned int ex = (u >> 23) & 0xffu;
-  if (ex == 0u || ex == 255u) {
-    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
-    return (double)f;                      // subnormal, inf, nan
-  }
+  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+  if (__builtin_expect(ex == 0u || ex == 255u, 0)) return f2d_rare(f);
   const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
                                ((unsigned long long)(ex + 896u) << 52) |
                                ((unsigned long long)(u & 0x7fffffu) << 29);
