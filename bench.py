@@ -42,6 +42,28 @@ N_DEFAULT, K_DEFAULT, SEED = 512, 4, 0
 METRIC = "trace-apply GB/s and %HBM peak; GMG solve time to 1e-10 rel residual, mixed vs FP64 on GPU"
 
 
+def rank_env():
+    """(world, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (every rank gets it); the step time of a
+    replica job is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, ms_per_step):
+    """Whole-job solves per second: every rank solves one system per step."""
+    return world * 1000.0 / ms_per_step
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -161,9 +183,7 @@ def run_ours(args):
 
     from paper_1705_09907_gb300 import hdg, inputs
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -397,10 +417,7 @@ def run_ours(args):
     per_it = 1 + 2 + 1 + 2 + vk + 2 + 1 + 1
     launches_per_step = 3 + (2 + vk + 2) + per_it * its - (vk + 4)
     # timing max over ranks
-    t_all = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    t_ms = float(t_all.item())
+    t_ms = max_over_ranks(t_ms, world, "cuda")
     if rank != 0:
         solver.close()
         if world > 1:
@@ -434,7 +451,7 @@ def run_ours(args):
         except Exception as ex:  # reported, not fatal
             cpu = {"error": str(ex)[:300]}
     line = {
-        "metric": METRIC, "value": world * 1000.0 / t_ms, "unit": "solve/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC, "value": job_throughput(world, t_ms), "unit": "solve/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "hdg_trace_gmg_pcg", "mesh": "%dx%d" % (N, N), "k": k,
@@ -459,8 +476,8 @@ def run_ours(args):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    _, rank, _ = rank_env()
+    if rank != 0:          # the oracle runs once, on rank 0; other ranks exit without work
         return
     N, k = args.n, args.k
     n_sub = 32
