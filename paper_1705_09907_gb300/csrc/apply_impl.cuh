@@ -67,29 +67,29 @@ __device__ __forceinline__ dfloat to_acc(float2 v, dfloat) { return dfloat{v.x, 
 // this GPU): hi keeps the leading 24 significant bits (truncated); lo is the
 // remaining 29 bits rounded to 24: the rounded bits are placed under the exponent
 // 2^E of lo's scale, and subtracting 2^E (exact, both operands in [2^E, 2^(E+1)])
-// leaves them as a float. hi + lo = v to about 2^-47 relative. Zero is built from
-// its bits; magnitudes below 2^-103 (where lo would leave the normal float range)
-// and above 2^127 take a conversion path kept out of line, so it is a real branch
-// and its conversions are not executed (predicated) for every value.
-static __device__ __noinline__ dfloat split_double_rare(double v) {
-  const float h = __double2float_rn(v);
-  return dfloat{h, __double2float_rn(v - (double)h)};
-}
+// leaves them as a float. hi + lo = v to about 2^-47 relative for 2^-103 <= |v| <
+// 2^128. Outside that range, still with integer operations only: below 2^-103 hi
+// keeps 24 bits and lo is 0, below 2^-126 the value becomes +-0, beyond 2^128 +-inf,
+// and inf / nan keep their class.
 __device__ __forceinline__ dfloat split_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
   const int e = (int)((b >> 52) & 0x7ff);
-  if ((b << 1) == 0ull) return dfloat{__uint_as_float(sign), 0.0f};            // +-0
-  if (__builtin_expect(e < 920 || e > 1150, 0)) return split_double_rare(v);
   const unsigned long long mant = b & 0xfffffffffffffull;
-  const unsigned int hib = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29);
-  const unsigned int rem = (unsigned int)(mant & 0x1fffffffull);          // 29 bits below hi
-  // lo = rem * 2^(e - 1075) = (2^E + rounded rem) - 2^E with E = e - 1046
-  const unsigned int eb = (unsigned int)(e - 919) << 23;                  // float bits of 2^E
-  const float top = __uint_as_float(eb + ((rem + 32u) >> 6));             // mantissa carry rounds up to 2^(E+1)
-  float lo = top - __uint_as_float(eb);
-  lo = __uint_as_float(__float_as_uint(lo) | sign);
-  return dfloat{__uint_as_float(hib), lo};
+  if (e >= 920 && e <= 1150) {
+    const unsigned int hib = sign | ((unsigned int)(e - 1023 + 127) << 23) | (unsigned int)(mant >> 29);
+    const unsigned int rem = (unsigned int)(mant & 0x1fffffffull);        // 29 bits below hi
+    // lo = rem * 2^(e - 1075) = (2^E + rounded rem) - 2^E with E = e - 1046
+    const unsigned int eb = (unsigned int)(e - 919) << 23;                // float bits of 2^E
+    const float top = __uint_as_float(eb + ((rem + 32u) >> 6));           // mantissa carry rounds up to 2^(E+1)
+    float lo = top - __uint_as_float(eb);
+    lo = __uint_as_float(__float_as_uint(lo) | sign);
+    return dfloat{__uint_as_float(hib), lo};
+  }
+  unsigned int hib = sign;                                                // |v| < 2^-126 and zero
+  if (e >= 897 && e < 920) hib = sign | ((unsigned int)(e - 896) << 23) | (unsigned int)(mant >> 29);
+  else if (e > 1150) hib = sign | 0x7f800000u | ((e == 2047 && mant) ? 0x400000u : 0u);
+  return dfloat{__uint_as_float(hib), 0.0f};
 }
 __device__ __forceinline__ dfloat to_acc(double v, dfloat) { return split_double(v); }
 // acc + s*x with an error-free product (FMA residual) and an error-free sum
@@ -107,17 +107,26 @@ __device__ __forceinline__ dfloat mac(dfloat s, dfloat x, dfloat acc) {
   const float err = (acc.hi - (sum - bb)) + (p - bb);
   return dfloat{sum, acc.lo + (err + e)};
 }
-// float -> double from the bits (exact for normal floats and zero): the
-// conversion instruction runs on the FP64 pipe, which is slow on this GPU
-static __device__ __noinline__ double f2d_rare(float f) { return (double)f; }   // subnormal, inf, nan
+// float -> double from the bits, exactly, with integer operations only (the
+// conversion instruction runs on the FP64 pipe, which is slow on this GPU):
+// normal floats re-biased, subnormals normalised by a leading-zero count, zero,
+// inf and nan keeping their class
 __device__ __forceinline__ double f2d_bits(float f) {
   const unsigned int u = __float_as_uint(f);
-  const unsigned int ex = (u >> 23) & 0xffu;
-  if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
-  if (__builtin_expect(ex == 0u || ex == 255u, 0)) return f2d_rare(f);
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(ex + 896u) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned int ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  unsigned long long b;
+  if (ex != 0u && ex != 255u) {
+    b = sign | ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (ex == 255u) {
+    b = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0u) {
+    b = sign;
+  } else {
+    const int p = 31 - __clz((int)m);                       // leading one of the subnormal mantissa
+    b = sign | ((unsigned long long)(p - 149 + 1023) << 52) |
+        (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+  }
   return __longlong_as_double((long long)b);
 }
 // value of an accumulator in the output arithmetic (one FP64 add for hi + lo)
