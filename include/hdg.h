@@ -164,6 +164,18 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
 
 /*
+ * Set up n independent problems of uneven size and degree in one call (the
+ * instances of hdg_apply_multi): out[q] receives the context of mesh meshes[q],
+ * degree k[q] and coefficient kappa[q] (device, [nx*ny] doubles each), with the
+ * same options for all (opt may be NULL). Same validation and errors as
+ * hdg_setup for each instance; on any error every context created by this call
+ * is destroyed, all out[q] are NULL, and the first failing instance's status is
+ * returned. 1 <= n <= 16.
+ */
+int hdg_setup_batch(int n, const hdg_mesh* meshes, const int* k, const double* const* kappa,
+                    const hdg_options* opt, void* stream, void** out);
+
+/*
  * The trace apply of Alg. 3 for n independent meshes (1 <= n <= 16 contexts,
  * uneven sizes, degrees 0..5) in ONE kernel launch: the record segments of all
  * meshes form a single work list (one CTA per entry, each on its mesh's degree),

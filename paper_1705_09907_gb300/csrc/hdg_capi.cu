@@ -288,6 +288,23 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
   return HDG_OK;
 }
 
+int hdg_setup_batch(int n, const hdg_mesh* meshes, const int* k, const double* const* kappa,
+                    const hdg_options* opt, void* stream, void** out) {
+  if (n < 1 || n > 16 || !meshes || !k || !kappa || !out) return HDG_ERR_INVALID_ARG;
+  for (int q = 0; q < n; ++q) out[q] = nullptr;
+  for (int q = 0; q < n; ++q) {
+    const int st = hdg_setup(&meshes[q], k[q], kappa[q], opt, stream, &out[q]);
+    if (st != HDG_OK) {
+      for (int r = 0; r < q; ++r) {
+        hdg_destroy(out[r]);
+        out[r] = nullptr;
+      }
+      return st;
+    }
+  }
+  return HDG_OK;
+}
+
 int hdg_apply_multi(int n, void* const* ctxs, const void* const* x, void* const* y, int prec, void* stream) {
   if (n < 1 || !ctxs) return HDG_ERR_INVALID_ARG;
   return apply_multi(reinterpret_cast<Context* const*>(ctxs), n, x, y, prec, (cudaStream_t)stream);

@@ -75,6 +75,8 @@ def _load():
         "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_shared_batched": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_multi": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
+        "hdg_setup_batch": (i, [i, ctypes.POINTER(hdg_mesh), ctypes.POINTER(i), ctypes.POINTER(vp),
+                                ctypes.POINTER(hdg_options), vp, ctypes.POINTER(vp)]),
         "hdg_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -101,6 +103,23 @@ hdg_adjoint_grad = _lib.hdg_adjoint_grad
 hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
 hdg_apply_shared_batched = _lib.hdg_apply_shared_batched
 hdg_apply_multi = _lib.hdg_apply_multi
+hdg_setup_batch = _lib.hdg_setup_batch
+
+
+def setup_batch(problems, **options):
+    """Set up several uneven problems in one call (hdg_setup_batch).
+    problems: list of (nx, ny, k, kappa) with kappa a CUDA tensor of nx*ny
+    entries (unit square meshes). Returns one HDGSolver per problem."""
+    n = len(problems)
+    meshes = (hdg_mesh * n)(*[hdg_mesh(int(nx), int(ny), 0.0, 0.0, 1.0, 1.0) for nx, ny, _, _ in problems])
+    ks = (ctypes.c_int * n)(*[int(k) for _, _, k, _ in problems])
+    kaps = [kap.to(device="cuda", dtype=torch.float64).contiguous() for _, _, _, kap in problems]
+    kp = (ctypes.c_void_p * n)(*[_ptr(kap, torch.float64).value for kap in kaps])
+    out = (ctypes.c_void_p * n)()
+    opt = default_options(**options)
+    _check(_lib.hdg_setup_batch(n, meshes, ks, kp, ctypes.byref(opt), _stream(), out), "hdg_setup_batch")
+    return [HDGSolver._adopt(ctypes.c_void_p(out[q]), problems[q][0], problems[q][1], problems[q][2], meshes[q], opt)
+            for q in range(n)]
 
 
 def apply_multi(solvers, xs, prec="fp64", outs=None):
@@ -171,6 +190,18 @@ class HDGSolver:
         _check(_lib.hdg_get_info(self.ctx, ctypes.byref(inf)), "hdg_get_info")
         self.info = {f: getattr(inf, f) for f, _ in hdg_info._fields_}
         self.nel, self.n_edges, self.ndof = inf.nel, inf.n_edges, inf.ndof
+
+    @classmethod
+    def _adopt(cls, ctx, nx, ny, k, mesh, opt):
+        """Wrap a context created by hdg_setup_batch."""
+        self = cls.__new__(cls)
+        self.nx, self.ny, self.k = int(nx), int(ny), int(k)
+        self.mesh, self.opt, self.ctx = mesh, opt, ctx
+        inf = hdg_info()
+        _check(_lib.hdg_get_info(self.ctx, ctypes.byref(inf)), "hdg_get_info")
+        self.info = {f: getattr(inf, f) for f, _ in hdg_info._fields_}
+        self.nel, self.n_edges, self.ndof = inf.nel, inf.n_edges, inf.ndof
+        return self
 
     def get_info(self):
         inf = hdg_info()

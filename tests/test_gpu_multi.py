@@ -53,3 +53,27 @@ def test_multi_instance_rejects_bad_input():
         hdg.apply_multi([s], [x])
     assert e.value.status == hdg.HDG_ERR_INVALID_ARG
     s.close()
+
+
+def test_setup_batch_and_multi_apply():
+    """hdg_setup_batch builds the uneven instances in one call; their multi apply
+    equals the instances' own applies, and a bad instance fails the whole call."""
+    from paper_1705_09907_gb300 import hdg
+    problems = []
+    for q, (nx, ny, k) in enumerate([(16, 16, 2), (24, 24, 4), (32, 32, 3)]):
+        kap = np.exp(inputs.gaussian_field(nx, seed=q, corr_len=0.3, ny=ny))
+        problems.append((nx, ny, k, torch.as_tensor(kap, device="cuda")))
+    sols = hdg.setup_batch(problems, autotune=3)
+    xs = [torch.as_tensor(inputs.random_trace(s.n_edges, s.k, seed=80 + q), device="cuda") for q, s in enumerate(sols)]
+    ys = hdg.apply_multi(sols, xs)
+    for s, x, y in zip(sols, xs, ys):
+        y1 = s.apply(x)
+        torch.cuda.synchronize()
+        assert torch.allclose(y, y1, rtol=0, atol=1e-12 * float(y1.abs().max()))
+    for s in sols:
+        s.close()
+    bad = list(problems)
+    bad[1] = (24, 24, 4, -torch.ones(24 * 24, dtype=torch.float64, device="cuda"))
+    with pytest.raises(hdg.HDGError) as e:
+        hdg.setup_batch(bad)
+    assert e.value.status == hdg.HDG_ERR_INVALID_ARG

@@ -27,8 +27,8 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for required in ("hdg_setup", "hdg_condense_rhs", "hdg_apply_trace", "hdg_gmg_vcycle", "hdg_solve",
-                     "hdg_recover_local", "hdg_adjoint_grad", "hdg_destroy"):
+    for required in ("hdg_setup", "hdg_setup_batch", "hdg_get_maps", "hdg_condense_rhs", "hdg_apply_trace",
+                     "hdg_gmg_vcycle", "hdg_solve", "hdg_recover_local", "hdg_adjoint_grad", "hdg_destroy"):
         assert required in names
 
 
@@ -56,3 +56,17 @@ def test_invalid_arguments_rejected_before_any_device_work(lib):
     assert hdg.hdg_setup(ctypes.byref(m), 1, None, None, None, ctypes.byref(ctx)) == hdg.HDG_ERR_INVALID_ARG
     assert hdg.hdg_apply_trace(None, None, None, 1, 0, None) == hdg.HDG_ERR_INVALID_ARG
     assert hdg.hdg_solve(None, None, None, 1, 1e-10, 10, 0, None, None) == hdg.HDG_ERR_INVALID_ARG
+
+
+def test_setup_batch_rejects_bad_arguments_before_any_device_work(lib):
+    from paper_1705_09907_gb300 import hdg
+    out = (ctypes.c_void_p * 2)()
+    ms = (hdg.hdg_mesh * 2)(hdg.hdg_mesh(1, 4, 0.0, 0.0, 1.0, 1.0), hdg.hdg_mesh(4, 4, 0.0, 0.0, 1.0, 1.0))
+    ks = (ctypes.c_int * 2)(1, 1)
+    kp = (ctypes.c_void_p * 2)(16, 16)
+    assert hdg.hdg_setup_batch(0, ms, ks, kp, None, None, out) == hdg.HDG_ERR_INVALID_ARG
+    assert hdg.hdg_setup_batch(17, ms, ks, kp, None, None, out) == hdg.HDG_ERR_INVALID_ARG
+    assert hdg.hdg_setup_batch(2, None, ks, kp, None, None, out) == hdg.HDG_ERR_INVALID_ARG
+    # the first instance is invalid (nx < 2): rejected before anything is set up
+    assert hdg.hdg_setup_batch(2, ms, ks, kp, None, None, out) == hdg.HDG_ERR_INVALID_ARG
+    assert out[0] is None and out[1] is None
