@@ -375,11 +375,10 @@ def run_ours(args):
     mi = {}
     if not args.profile:
         mix = inputs.instance_mix(12, seed=4)
-        sols, xs = [], []
-        for q, (Nq, kq) in enumerate(mix):
-            sq = hdg.HDGSolver(Nq, Nq, kq, torch.ones(Nq * Nq, dtype=torch.float64, device="cuda"), mixed=0)
-            sols.append(sq)
-            xs.append(torch.as_tensor(inputs.random_trace(sq.n_edges, kq, seed=60 + q), device="cuda"))
+        sols = hdg.setup_batch([(Nq, Nq, kq, torch.ones(Nq * Nq, dtype=torch.float64, device="cuda"))
+                                for Nq, kq in mix], mixed=0)
+        xs = [torch.as_tensor(inputs.random_trace(sq.n_edges, sq.k, seed=60 + q), device="cuda")
+              for q, sq in enumerate(sols)]
         ys = [torch.empty_like(x) for x in xs]
         hdg.apply_multi(sols, xs, outs=ys)
         ms_multi = timed_events(lambda: hdg.apply_multi(sols, xs, outs=ys), args.apply_reps, torch)

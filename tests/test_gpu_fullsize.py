@@ -114,3 +114,34 @@ def test_fullsize_batched_solve_sampled():
     lam0, _ = s.solve(B[:, 0].contiguous(), rtol=rtol, maxit=400, inner="fp64")
     assert float(torch.linalg.norm(lam[:, 0] - lam0) / torch.linalg.norm(lam0)) <= 1e-7
     s.close()
+
+
+def test_fullsize_uneven_instances_sampled():
+    """12 uneven meshes (N in {64, 128, 256, 512}, k in {2, 3, 4}, seed 4),
+    kappa = 1, set up in one hdg_setup_batch call and applied in one
+    hdg_apply_multi launch as the benchmark does: every instance agrees with its
+    own single apply, and at 40 sampled interior edges per instance with the
+    oracle's element blocks (FP64 bound of an 8(k+1)-term sum)."""
+    from paper_1705_09907_gb300 import hdg
+    mix = inputs.instance_mix(12, seed=4)
+    sols = hdg.setup_batch([(N, N, k, torch.ones(N * N, dtype=torch.float64, device="cuda")) for N, k in mix],
+                           mixed=0)
+    xs = [torch.as_tensor(inputs.random_trace(s.n_edges, s.k, seed=60 + q), device="cuda")
+          for q, s in enumerate(sols)]
+    ys = hdg.apply_multi(sols, xs)
+    for q, ((N, k), s, x, y) in enumerate(zip(mix, sols, xs, ys)):
+        y1 = s.apply(x)
+        yh, y1h = y.cpu().numpy(), y1.cpu().numpy()
+        m = omesh.Mesh(N, N)
+        edges = np.random.default_rng(100 + q).choice(m.interior_edges(), size=40, replace=False)
+        rows, prob = _oracle_edge_rows(m, k, np.ones(m.nel), inputs.constant_f(N, k), edges)
+        xm = x.cpu().numpy()
+        xm[np.setdiff1d(np.arange(prob.ndof), prob.interior_dofs())] = 0.0
+        n1 = k + 1
+        for e, rr in zip(edges, rows):
+            ref = sum(S @ xm[d] for S, d, _ in rr)
+            scale = sum(np.abs(S) @ np.abs(xm[d]) for S, d, _ in rr)
+            assert np.all(np.abs(yh[e * n1:(e + 1) * n1] - ref) <= 1e-12 * scale), (q, N, k, e)
+            assert np.all(np.abs(yh[e * n1:(e + 1) * n1] - y1h[e * n1:(e + 1) * n1]) <= 2e-12 * scale)
+    for s in sols:
+        s.close()
