@@ -88,6 +88,12 @@ typedef struct {
                                  fits. The
                                  choice changes only the
                                  order of the floating-point sums            */
+  int reduced;                /* 1: one-vector applies of the condensed blocks
+                                 use each S_K reduced by the element's two
+                                 reflection symmetries (four symmetric blocks,
+                                 61 numbers instead of 400 at k = 4, two
+                                 launches; default); 0: the dense owner
+                                 records (kernel chosen by `autotune`)       */
 } hdg_options;
 
 typedef struct {
@@ -98,6 +104,8 @@ typedef struct {
   double setup_ms;            /* wall time of hdg_setup                      */
   int vcycle_kernels;         /* kernel launches in one V-cycle (0 until the
                                  first V-cycle has been captured or run)     */
+  int apply_kernels;          /* kernel launches of one hdg_apply_trace of
+                                 one vector (2 with `reduced`, else 1)       */
 } hdg_info;
 
 typedef struct {

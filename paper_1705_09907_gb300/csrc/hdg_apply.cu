@@ -6,6 +6,8 @@ namespace hdg {
 cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, const void* cvec, void* y,
                          double alpha, double beta, int nrhs, cudaStream_t s) {
   PLevel& L = c->plev[p];
+  if (which == 0 && nrhs == 1 && c->opt.reduced)
+    return launch_reduced_apply(c, p, prec, v, cvec, y, alpha, beta, s);
   const void* rec = nullptr;
   if (prec == HDG_PREC_FP64) rec = which ? (const void*)L.M64 : (const void*)L.S64;
   else if (prec == HDG_PREC_FP32) rec = which ? (const void*)L.M32 : (const void*)L.S32;
@@ -118,6 +120,7 @@ cudaError_t autotune_applies(Context* c, cudaStream_t s) {
       if (prec != HDG_PREC_FP64 && !c->opt.mixed) continue;
       for (int which = 0; which < 2; ++which) {
         if (which == 1 && p == 0) continue;       // no Schwarz blocks at p = 0
+        if (which == 0 && c->opt.reduced) continue;   // condensed blocks: the reduced apply
         const unsigned sb = stage_bytes_of(L.n1, prec);
         const int total = (int)((220u * 1024u) / sb);
         const void* x = prec_double(prec) ? (const void*)xd : (const void*)xf;

@@ -55,6 +55,9 @@ struct PLevel {
   double* S64 = nullptr; float* S32 = nullptr; __nv_bfloat16* S16 = nullptr;
   double* M64 = nullptr; float* M32 = nullptr; __nv_bfloat16* M16 = nullptr;
   float2* S2 = nullptr; float2* M2 = nullptr;   // double-float (hi, lo) copies
+  // condensed blocks reduced by the element's reflection symmetry: packed
+  // upper triangles of the four character blocks, [Q][nel] (apply_reduced.cu)
+  double* R64 = nullptr; float* R32 = nullptr;
   double* Sdense = nullptr;                 // [nel][m][m] FP64 element blocks
   double* Pp = nullptr;                     // prolongation from p-1 [(p+1) x p] (device)
   float* Pp32 = nullptr;                    // the same in float (float V-cycles)
@@ -118,6 +121,7 @@ struct Context {
          off_MiBt = 0, off_MiC = 0, off_Vf = 0, off_wJf = 0, off_M = 0;
   size_t off_ZT = 0, off_EbT = 0, off_MiBtT = 0, off_MiCT = 0, off_VfT = 0;   // transposes
   double* elem_scratch = nullptr;           // [nel][m] per-element partial results
+  void* red_z = nullptr;                    // [m][nel] element products of the reduced apply
   // finest-level local operators: A_u^-1 (symmetric, stored full) and G = A_u^-1 W
   double* Ainv = nullptr;                   // [nel][n][n]
   double* Gfac = nullptr;                   // [nel][n][m]
@@ -165,6 +169,14 @@ cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s);
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s);
 // one persistent launch over several contexts (apply_multi.cu); returns hdg_status
 int apply_multi(Context* const* ctx, int n, const void* const* x, void* const* y, int prec, cudaStream_t s);
+
+// Reduced-block apply (apply_reduced.cu): entries per element of the packed
+// blocks, their set-up from the dense blocks, and y = beta c + alpha S v for one
+// vector (two launches).
+int reduced_entries(int n1);
+cudaError_t launch_reduced_blocks(Context* c, int p, cudaStream_t s);
+cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, const void* cvec, void* y,
+                                 double alpha, double beta, cudaStream_t s);
 
 // Trace-operator apply on the record layout of level p:
 //   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)

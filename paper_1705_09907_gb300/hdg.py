@@ -35,13 +35,14 @@ class hdg_mesh(ctypes.Structure):
 class hdg_options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_n", ctypes.c_int), ("tau", ctypes.c_double),
                 ("cheb_degree", ctypes.c_int), ("mixed", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("reduced", ctypes.c_int)]
 
 
 class hdg_info(ctypes.Structure):
     _fields_ = [("nel", ctypes.c_int), ("n_edges", ctypes.c_int), ("ndof", ctypes.c_int), ("k", ctypes.c_int),
                 ("n_plevels", ctypes.c_int), ("n_hlevels", ctypes.c_int), ("coarse_dim", ctypes.c_int),
-                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double), ("vcycle_kernels", ctypes.c_int)]
+                ("device_bytes", ctypes.c_size_t), ("setup_ms", ctypes.c_double), ("vcycle_kernels", ctypes.c_int),
+                ("apply_kernels", ctypes.c_int)]
 
 
 class hdg_solve_info(ctypes.Structure):

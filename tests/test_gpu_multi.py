@@ -19,9 +19,9 @@ def test_multi_instance_apply(prec):
     dt = torch.float64 if prec == "fp64" else torch.float32
     for q, (nx, ny, k) in enumerate(CASES):
         kap = np.exp(inputs.gaussian_field(nx, seed=q, corr_len=0.3, ny=ny))
-        # autotune = 3: the single apply runs the 4-warp segment kernel, whose
-        # per-segment arithmetic the multi-instance launch shares
-        s = hdg.HDGSolver(nx, ny, k, torch.as_tensor(kap, device="cuda"), autotune=3)
+        # autotune = 3, reduced = 0: the single apply runs the 4-warp segment
+        # kernel, whose per-segment arithmetic the multi-instance launch shares
+        s = hdg.HDGSolver(nx, ny, k, torch.as_tensor(kap, device="cuda"), autotune=3, reduced=0)
         solvers.append(s)
         xs.append(torch.as_tensor(inputs.random_trace(s.n_edges, k, seed=50 + q), dtype=dt, device="cuda"))
     ys = hdg.apply_multi(solvers, xs, prec=prec)
@@ -63,7 +63,7 @@ def test_setup_batch_and_multi_apply():
     for q, (nx, ny, k) in enumerate([(16, 16, 2), (24, 24, 4), (32, 32, 3)]):
         kap = np.exp(inputs.gaussian_field(nx, seed=q, corr_len=0.3, ny=ny))
         problems.append((nx, ny, k, torch.as_tensor(kap, device="cuda")))
-    sols = hdg.setup_batch(problems, autotune=3)
+    sols = hdg.setup_batch(problems, autotune=3, reduced=0)
     xs = [torch.as_tensor(inputs.random_trace(s.n_edges, s.k, seed=80 + q), device="cuda") for q, s in enumerate(sols)]
     ys = hdg.apply_multi(sols, xs)
     for s, x, y in zip(sols, xs, ys):

@@ -46,31 +46,39 @@ def test_maps_exact(H, nx, ny):
     s.close()
 
 
+@pytest.mark.parametrize("reduced", [1, 0])
 @pytest.mark.parametrize("prec", ["fp64", "f32x2"])
-@pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("nx,ny", [(2, 2), (37, 6), (16, 3)])
-def test_apply_fp64_vs_assembled(H, k, nx, ny, prec):
+def test_apply_fp64_vs_assembled(H, k, nx, ny, prec, reduced):
+    """reduced = 1: the symmetry-reduced element blocks (two launches); 0: the
+    dense owner records. Rectangular elements (hy = 0.7 hx)."""
     m = omesh.Mesh(nx, ny, 0.0, 0.0, 1.0, 0.7)
     kap = np.exp(inputs.gaussian_field(nx, seed=k, corr_len=0.3, ny=ny))
     prob = ohdg.HDGProblem(m, k, kap)
     x = inputs.random_trace(m.n_edges, k, seed=100 + k)    # boundary entries nonzero: must be ignored
     y_ref = prob.apply_assembled(x)
-    s = H.HDGSolver(nx, ny, k, cuda(kap), y1=0.7)
+    s = H.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, reduced=reduced)
+    assert s.info["apply_kernels"] == (2 if reduced else 1)
     y = host(s.apply(cuda(x), prec=prec))
     bound = abs_bound(prob, x)
     # FP64 rounding of a 8(k+1)-term sum plus the two codes' different S_K
-    # rounding; F32X2 keeps ~48 bits per product and sum (error ~40 * 2^-48)
+    # rounding (the reduced form adds the roundings of F x and F^T u, sums of
+    # at most 4 terms each); F32X2 keeps ~48 bits per product and sum (error
+    # ~40 * 2^-48)
     assert np.all(np.abs(y - y_ref) <= 1e-12 * bound + 1e-300)
     bnd = np.setdiff1d(np.arange(prob.ndof), prob.interior_dofs())
     assert np.all(y[bnd] == 0.0)
     s.close()
 
 
+@pytest.mark.parametrize("reduced", [1, 0])
 @pytest.mark.parametrize("prec,tol", [("fp32", 3e-6), ("bf16", 1.2e-2)])
-@pytest.mark.parametrize("k", [1, 3, 4])
-def test_apply_low_precision(H, prec, tol, k):
+@pytest.mark.parametrize("k", [0, 1, 3, 4, 7])
+def test_apply_low_precision(H, prec, tol, k, reduced):
     """FP32 blocks: entry rounding 2^-24 plus float accumulation; BF16 blocks:
-    entry rounding 2^-9 relative, float accumulation. Bound relative to |A||x|."""
+    entry rounding 2^-9 relative, float accumulation. Bound relative to |A||x|.
+    With reduced blocks both float precisions apply the FP32 reduced blocks."""
     nx, ny = 37, 5
     m = omesh.Mesh(nx, ny)
     kap = np.exp(inputs.gaussian_field(nx, seed=7, corr_len=0.3, ny=ny))
@@ -78,7 +86,7 @@ def test_apply_low_precision(H, prec, tol, k):
     x = inputs.random_trace(m.n_edges, k, seed=3)
     xf = x.astype(np.float32)
     y_ref = prob.apply_assembled(xf.astype(np.float64))
-    s = H.HDGSolver(nx, ny, k, cuda(kap))
+    s = H.HDGSolver(nx, ny, k, cuda(kap), reduced=reduced)
     y = host(s.apply(cuda(xf, torch.float32), prec=prec)).astype(np.float64)
     bound = abs_bound(prob, xf.astype(np.float64))
     assert np.all(np.abs(y - y_ref) <= tol * bound + 1e-30)

@@ -1,7 +1,8 @@
 """The one-CTA-per-segment apply kernel (forced with autotune = 2 / 3 / 4:
 8 / 4 / 2 warps) against the FP64 oracle's assembled operator and against the ring
 kernel (autotune = 0), for every degree, all four precisions and ragged
-segments; then the residual form y = c - A x inside a V-cycle, and a solve."""
+segments; then the residual form y = c - A x inside a V-cycle, and a solve.
+reduced = 0 throughout, so the condensed blocks also go through these kernels."""
 import numpy as np
 import pytest
 import torch
@@ -36,8 +37,8 @@ def test_segment_apply_vs_assembled(prec, k, nx, ny, mode):
     dt = torch.float64 if prec in ("fp64", "f32x2") else torch.float32
     xd = cuda(inputs.random_trace(m.n_edges, k, seed=70 + k), dt)
     x = host(xd)
-    seg = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=mode)
-    ring = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=0)
+    seg = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=mode, reduced=0)
+    ring = hdg.HDGSolver(nx, ny, k, cuda(kap), y1=0.7, autotune=0, reduced=0)
     y = host(seg.apply(xd, prec=prec))
     ref = np.zeros(prob.ndof)
     ref[idx] = A @ x[idx]
@@ -65,7 +66,7 @@ def test_segment_vcycle_and_solve(k, mode):
     top = G.plevels[k]
     r = np.zeros(top.ndof)
     r[top.idx] = np.random.default_rng(21).normal(size=len(top.idx))
-    s = hdg.HDGSolver(nx, ny, k, cuda(kap), autotune=mode)
+    s = hdg.HDGSolver(nx, ny, k, cuda(kap), autotune=mode, reduced=0)
     for prec, tol in (("fp64", 1e-11), ("f32x2", 1e-10)):
         z = host(s.vcycle(cuda(r), prec=prec))
         z_ref = G.vcycle(r)

@@ -53,6 +53,34 @@ def test_schur_invariants(p):
         assert (w > 1e-10 * scale).sum() == 4 * (p + 1) - 1   # kernel = constants only
 
 
+@pytest.mark.parametrize("p", range(0, 8))
+def test_schur_reflection_symmetry(p):
+    """A rectangle with constant kappa and tau is mapped to itself by the
+    reflections about its centre lines, and the Gauss-Legendre trace nodes are
+    symmetric, so S_K commutes with both reflections on the face dofs [W|E|S|N]
+    (x-reflection: W <-> E, S and N reversed; y-reflection: S <-> N, W and E
+    reversed). Fails if a face or node ordering, a normal sign or a tau term is
+    wrong in the oracle (the square case also commutes with swapping x and y)."""
+    rng = np.random.default_rng(40 + p)
+    n = p + 1
+    R = np.arange(n)[::-1]
+    W, E, S_, N = (np.arange(f * n, (f + 1) * n) for f in range(4))
+    sx = np.concatenate([E, W, S_[R], N[R]])
+    sy = np.concatenate([W[R], E[R], N, S_])
+    swap = np.concatenate([S_, N, W, E])
+    for hx, hy in ((0.1, 0.1), (0.3, 0.07)):
+        for tau in (1.0, 3.5):
+            kappa = float(np.exp(2 * rng.normal()))
+            S = hdg.schur_block(hdg.element_matrices(hdg.RefElement(p, hx, hy), kappa, tau))
+            scale = np.abs(S).max()
+            assert np.abs(S[np.ix_(sx, sx)] - S).max() < 1e-13 * scale
+            assert np.abs(S[np.ix_(sy, sy)] - S).max() < 1e-13 * scale
+            if hx == hy:
+                assert np.abs(S[np.ix_(swap, swap)] - S).max() < 1e-13 * scale
+            elif p > 0:
+                assert np.abs(S[np.ix_(swap, swap)] - S).max() > 1e-3 * scale
+
+
 @pytest.mark.parametrize("p", range(0, 5))
 def test_schur_energy_identity(p):
     """Independent second formula: lambda^T S mu = (kappa^-1 q_l, q_m)_K
