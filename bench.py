@@ -177,6 +177,43 @@ def timed_events(fn, reps, torch):
     return s.elapsed_time(e) / reps
 
 
+def flushed_time(fn, torch, n=8, reps=3):
+    """Device time of fn with a cold L2: one CUDA graph of n x (L2 flush, fn)
+    and one of n x (L2 flush) alone, each replayed `reps` times between CUDA
+    events; the difference per call. The flush writes twice the L2 size, so no
+    input of fn is served from L2 (used where fn's data is smaller than L2)."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    l2 = int(getattr(props, "L2_cache_size", 0) or (132 << 20))
+    buf = torch.empty(2 * l2 // 4, dtype=torch.float32, device="cuda")
+
+    def flush():
+        buf.fill_(1.0)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):          # warm-up outside the capture
+        flush()
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graphs = []
+    for with_fn in (True, False):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            for _ in range(n):
+                flush()
+                if with_fn:
+                    fn()
+        graphs.append(g)
+    times = []
+    for g in graphs:
+        g.replay()
+        torch.cuda.synchronize()
+        times.append(timed_events(g.replay, reps, torch))
+    del graphs
+    return max(times[0] - times[1], 0.0) / n
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -217,6 +254,11 @@ def run_ours(args):
         # batched work below
         torch.cuda.nvtx.range_push("fp64_step")
         step()
+        torch.cuda.nvtx.range_pop()
+        # the same step with the FP32 V-cycle (outer CG in FP64)
+        step("fp32")
+        torch.cuda.nvtx.range_push("fp32_step")
+        step("fp32")
         torch.cuda.nvtx.range_pop()
         x64 = torch.as_tensor(inputs.random_trace(solver.n_edges, k, seed=1), device="cuda")
         x32 = x64.float()
@@ -267,13 +309,22 @@ def run_ours(args):
         # the dominant kernel: trace apply at level k, timed alone (inputs >> L2)
         x64 = torch.as_tensor(inputs.random_trace(solver.n_edges, k, seed=1), device="cuda")
         y64 = torch.empty_like(x64)
-        apply_ms = {}
-        apply_ms["fp64"] = timed_events(lambda: solver.apply(x64, "fp64", out=y64), args.apply_reps, torch)
         x32 = x64.float()
         y32 = torch.empty_like(x32)
-        apply_ms["fp32"] = timed_events(lambda: solver.apply(x32, "fp32", out=y32), args.apply_reps, torch)
-        apply_ms["bf16"] = timed_events(lambda: solver.apply(x32, "bf16", out=y32), args.apply_reps, torch)
-        apply_ms["f32x2"] = timed_events(lambda: solver.apply(x64, "f32x2", out=y64), args.apply_reps, torch)
+        # the reduced blocks (128 MB FP64 / 64 MB FP32 at 512^2, k = 4) are about
+        # the size of L2: each apply is timed after an L2 flush, inside a CUDA
+        # graph (device time only)
+        apply_ms = {}
+        for p_, xx, yy in (("fp64", x64, y64), ("fp32", x32, y32), ("bf16", x32, y32), ("f32x2", x64, y64)):
+            apply_ms[p_] = flushed_time(lambda: solver.apply(xx, p_, out=yy), torch)
+        # the dense owner-record kernels (reduced = 0): the kernel that applies the
+        # Schwarz blocks in every V-cycle, here timed on the condensed blocks (the
+        # same kernel and the same bytes per launch)
+        dense = hdg.HDGSolver(N, N, k, kap_d, reduced=0)
+        dense_ms = {}
+        for p_, xx, yy in (("fp64", x64, y64), ("fp32", x32, y32), ("bf16", x32, y32), ("f32x2", x64, y64)):
+            dense_ms[p_] = flushed_time(lambda: dense.apply(xx, p_, out=yy), torch)
+        dense.close()
     clk = clocks.summary()
     # the element-local operations of the step, timed alone
     b_loc = solver.condense_rhs(fq_d)
@@ -370,8 +421,9 @@ def run_ours(args):
             m3[inner] = {"ms_per_solve": ms3, "iterations": inf["iterations"], "relres": inf["relres"],
                          "rel_diff_vs_fp64_solution": float(torch.linalg.norm(l3 - l64) / torch.linalg.norm(l64))}
         s3.close()
-    # uneven instances in one persistent launch: 12 meshes N in {64..512}, k in {2,3,4}
-    # (seeded mix), kappa = 1, FP64 blocks; one hdg_apply_multi vs 12 single applies
+    # uneven instances in one batch: 12 meshes N in {64..512}, k in {2,3,4} (seeded
+    # mix), kappa = 1, FP64 reduced blocks; one hdg_apply_multi (one launch per
+    # pass for all meshes) vs 12 single applies
     mi = {}
     if not args.profile:
         mix = inputs.instance_mix(12, seed=4)
@@ -381,17 +433,24 @@ def run_ours(args):
               for q, sq in enumerate(sols)]
         ys = [torch.empty_like(x) for x in xs]
         hdg.apply_multi(sols, xs, outs=ys)
-        ms_multi = timed_events(lambda: hdg.apply_multi(sols, xs, outs=ys), args.apply_reps, torch)
+        ms_multi = flushed_time(lambda: hdg.apply_multi(sols, xs, outs=ys), torch)
 
         def singles():
             for sq, x, y in zip(sols, xs, ys):
                 sq.apply(x, out=y)
 
-        ms_single = timed_events(singles, args.apply_reps, torch)
-        algo = sum(sq.nel * 16 * (sq.k + 1) ** 2 * 8 + 2 * sq.n_edges * (sq.k + 1) * 8 for sq in sols)
-        mi = {"instances": [[int(a_), int(b_)] for a_, b_ in mix], "ms_one_launch": ms_multi,
-              "ms_12_launches": ms_single, "GBps_one_launch": algo / (ms_multi * 1e-3) / 1e9,
-              "algorithmic_bytes": algo}
+        ms_single = flushed_time(singles, torch)
+        def red_q(n1):        # entries of the reduced blocks per element
+            a_, b_ = n1 // 2 + n1 % 2, n1 // 2
+            return sum(d * (d + 1) // 2 for d in (2 * a_, a_ + b_, a_ + b_, 2 * b_))
+        algo = sum(sq.nel * red_q(sq.k + 1) * 8 + 2 * sq.n_edges * (sq.k + 1) * 8 for sq in sols)
+        mi = {"instances": [[int(a_), int(b_)] for a_, b_ in mix],
+              "kernels": "multi_red_elem_kernel + multi_red_face_kernel (reduced blocks, all 12 meshes)",
+              "ms_batch": ms_multi, "launches_batch": 2, "ms_separate": ms_single,
+              "launches_separate": sum(sq.get_info()["apply_kernels"] for sq in sols),
+              "GBps_batch": algo / (ms_multi * 1e-3) / 1e9,
+              "frac_hbm_batch": algo / (ms_multi * 1e-3) / 1e9 / peaks["hbm_gbs"],
+              "algorithmic_bytes": algo, "timing": "cold L2, device time (CUDA graph)"}
         for sq in sols:
             sq.close()
     # end to end through the public API with host buffers
@@ -411,9 +470,10 @@ def run_ours(args):
     e2e_ms = timed_events(e2e_step, max(1, args.steps // 2), torch)
     # launches in the timed region: condense 2 + recover 1 + CG
     vk = solver.get_info()["vcycle_kernels"]
+    ak = solver.get_info()["apply_kernels"]
     # per CG iteration: apply, 2 dots kernels, x/r update, 2 dots, V-cycle, 2 dots, p update, commit;
     # the last iteration stops after the convergence check (no V-cycle, dots, p, commit)
-    per_it = 1 + 2 + 1 + 2 + vk + 2 + 1 + 1
+    per_it = ak + 2 + 1 + 2 + vk + 2 + 1 + 1
     launches_per_step = 3 + (2 + vk + 2) + per_it * its - (vk + 4)
     # timing max over ranks
     t_ms = max_over_ranks(t_ms, world, "cuda")
@@ -425,23 +485,46 @@ def run_ours(args):
     nel, ne, n1 = solver.nel, solver.n_edges, k + 1
     bytes_S = {"fp64": 8, "fp32": 4, "bf16": 2, "f32x2": 8}
     bytes_x = {"fp64": 8, "fp32": 4, "bf16": 4, "f32x2": 8}
+    # reduced blocks: packed upper triangles of the four character blocks
+    hh, se_, so_ = n1 // 2, n1 // 2 + n1 % 2, n1 // 2
+    dims = (2 * se_, so_ + se_, se_ + so_, 2 * so_)
+    q_red = sum(d * (d + 1) // 2 for d in dims)
+    red_w = {"fp64": 8, "fp32": 4, "bf16": 4, "f32x2": 8}            # float cycles use the FP32 reduced blocks
+    # FP64 operations per element: F x and F^T u (8 n1 + 16 h additions), the
+    # block products (sum d^2 multiply-adds), the face sums of the second pass (2 n1)
+    red_add = 8 * n1 + 16 * hh + 2 * n1
+    red_fma = sum(d * d for d in dims)
     tra = {}
     for p_, ms in apply_ms.items():
+        algo = nel * q_red * red_w[p_] + 2 * ne * n1 * bytes_x[p_]
+        dense_eq = nel * 16 * n1 * n1 * bytes_S[p_] + 2 * ne * n1 * bytes_x[p_]
+        gbs = algo / (ms * 1e-3) / 1e9
+        tra[p_] = {"ms": ms, "kernels": "reduced_elem_kernel + reduced_face_kernel (cold L2, device time)", "GBps": gbs,
+                   "frac_hbm": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
+                   "scratch_bytes": 2 * nel * 4 * n1 * red_w[p_],
+                   "dense_equivalent_GBps": dense_eq / (ms * 1e-3) / 1e9,
+                   "fp64_ops_per_element": {"fma": red_fma, "add": red_add} if p_ in ("fp64", "f32x2") else None}
+    tra["fp64"]["fp64_pipe_frac"] = nel * (red_fma + red_add) / (apply_ms["fp64"] * 1e-3) / (1.25e12 / 2)
+    trd = {}
+    for p_, ms in dense_ms.items():
         algo = nel * 16 * n1 * n1 * bytes_S[p_] + 2 * ne * n1 * bytes_x[p_]
         gbs = algo / (ms * 1e-3) / 1e9
-        tra[p_] = {"ms": ms, "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
+        trd[p_] = {"ms": ms, "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
                    "flops": 2 * nel * 16 * n1 * n1}
-    fp = tra["fp64"]
-    tflops = fp["flops"] / (apply_ms["fp64"] * 1e-3) / 1e12
+    fp = trd["fp64"]
+    tflops = fp["flops"] / (dense_ms["fp64"] * 1e-3) / 1e12
+    # The step's dominant kernel is the dense owner-record apply of the Schwarz
+    # blocks (4 launches per V-cycle at each p-level, no symmetry to reduce).
     # FP64: 0.25 flop/byte needs more FP64 issue than the GPU has (1.25 TFLOP/s
-    # nominal), so the FP64 apply is bound by the FP64 pipe, not by HBM.
-    # DRAM read+write of one FP64 level-k apply at 512 x 512, k = 4 (ncu, one-pass
-    # dram__bytes_read.sum + dram__bytes_write.sum, warm launches of the set-up
-    # autotuner's choice, the 4-warp segment kernel): 860.0 MB + 18.3 MB
+    # nominal), so it is bound by the FP64 pipe, not by HBM.
+    # DRAM read+write of one such FP64 level-k launch at 512 x 512, k = 4 (ncu,
+    # one-pass dram__bytes_read.sum + dram__bytes_write.sum, warm launches of
+    # the set-up autotuner's choice, the 4-warp segment kernel): 860.0 MB + 18.3 MB
     traffic = 878.3e6 if (N, k) == (512, 4) else None
-    roof = {"kernel": "FP64 trace apply at level k (autotuned; apply_seg_kernel<5,double,double,double,0,4> on GB300)",
+    roof = {"kernel": "FP64 Schwarz-block apply at level k (autotuned; apply_seg_kernel<5,double,double,double,0,4> "
+                      "on GB300), timed on the condensed blocks of a reduced=0 context (same kernel, same bytes)",
             "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": tflops / 1.25,
-            "peak_source": "nominal FP64 rate of GB300 (recipe table); HBM fraction in trace_apply",
+            "peak_source": "nominal FP64 rate of GB300 (recipe table); HBM fraction in trace_apply_dense",
             "traffic": traffic, "algorithmic_bytes": fp["algorithmic_bytes"]}
     cpu = None
     if not args.no_cpu_baseline:
@@ -456,10 +539,11 @@ def run_ours(args):
         "config": {"workload": "hdg_trace_gmg_pcg", "mesh": "%dx%d" % (N, N), "k": k,
                    "kappa": "lognormal sigma^2=1 l=0.05 seed 0", "f": 1, "rtol": rtol,
                    "ndof": solver.ndof, "cg_iterations": its, "final_relres": relres,
-                   "l2": "inputs larger than L2 (FP64 S + Schwarz blocks %.0f MB)" % (2 * nel * 16 * n1 * n1 * 8 / 1e6),
+                   "l2": "inputs larger than L2 (FP64 reduced S %.0f MB + Schwarz blocks %.0f MB)"
+                         % (nel * q_red * 8 / 1e6, nel * 16 * n1 * n1 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
-        "roofline": roof, "trace_apply": tra, "local_ops_ms": local_ms, "mixed": mixed, "mixed_1024_k3": m3,
+        "roofline": roof, "trace_apply": tra, "trace_apply_dense": trd, "local_ops_ms": local_ms, "mixed": mixed, "mixed_1024_k3": m3,
         "batched_solve": bs,
         "shared_batched_apply": sb, "multi_instance_apply": mi,
         "e2e": {"value": 1000.0 / e2e_ms, "unit": "solve/s", "ms_per_step": e2e_ms,

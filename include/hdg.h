@@ -91,9 +91,13 @@ typedef struct {
   int reduced;                /* 1: one-vector applies of the condensed blocks
                                  use each S_K reduced by the element's two
                                  reflection symmetries (four symmetric blocks,
-                                 61 numbers instead of 400 at k = 4, two
-                                 launches; default); 0: the dense owner
-                                 records (kernel chosen by `autotune`)       */
+                                 61 numbers instead of 400 at k = 4), in two
+                                 launches: element products, then faces
+                                 (default); 2: the same arithmetic and results
+                                 with one CTA per 32 x 8 element tile plus a
+                                 small launch for the faces on tile edges;
+                                 0: the dense owner records (kernel chosen by
+                                 `autotune`)                                 */
 } hdg_options;
 
 typedef struct {
@@ -105,7 +109,8 @@ typedef struct {
   int vcycle_kernels;         /* kernel launches in one V-cycle (0 until the
                                  first V-cycle has been captured or run)     */
   int apply_kernels;          /* kernel launches of one hdg_apply_trace of
-                                 one vector (2 with `reduced`, else 1)       */
+                                 one vector (2 with `reduced` = 1, and with 2
+                                 on meshes of more than one tile; else 1)    */
 } hdg_info;
 
 typedef struct {

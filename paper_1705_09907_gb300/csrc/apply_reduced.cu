@@ -23,254 +23,206 @@
 // plus 16(k+1) additions for F and F^T instead of 16(k+1)^2 multiply-adds.
 //
 // The apply y = beta c + alpha sum_{K} A_K^T S_K A_K v (boundary dofs of v
-// ignored, boundary rows of y zero) runs in two launches:
-//   1. one thread per element: gather the element's four faces of v, form
-//      z_K = S_K v_K by the reduced product and store z (face-major [4n][nel]);
-//   2. one thread per element: each owned face (W and S) adds its two element
-//      contributions, own first, and writes y once (E / N domain-boundary
-//      edges are zeroed by their only element).
-// Both orders of summation are fixed, so results are deterministic.
-#include "hdg_internal.h"
+// ignored, boundary rows of y zero) writes every face once, as its own
+// element's output plus its neighbour's (W face: own + west neighbour's E; S
+// face: own + south neighbour's N), with no atomics. One thread computes one
+// element product at a time. Two forms with identical results:
+//   reduced = 1: every element product to a scratch [4n][nel], then every face
+//      (the faster form on GB300: many small independent CTAs keep more loads
+//      in flight; the scratch round trip mostly stays in L2).
+//   reduced = 2: one CTA per 32 x kTileRows tile finishes every face inside the
+//      tile (shuffles across the row, registers and shared memory up the
+//      column); the faces on tile edges go through a small second launch.
+// The blocks are read once, directly from HBM with coalesced streaming loads
+// ([Q][nel]: the 32 lanes of a warp read 32 consecutive elements' entry q).
+#include "reduced_impl.cuh"
 
 namespace hdg {
 
 namespace {
 
-template <int N1>
-struct Red {
-  static constexpr int n = N1, h = N1 / 2, se = N1 / 2 + (N1 & 1), so = N1 / 2;
-  static constexpr int d0 = 2 * se, d1 = so + se, d2 = se + so, d3 = 2 * so;
-  static constexpr int q0 = 0, q1 = d0 * (d0 + 1) / 2, q2 = q1 + d1 * (d1 + 1) / 2, q3 = q2 + d2 * (d2 + 1) / 2;
-  static constexpr int Q = q3 + d3 * (d3 + 1) / 2;
-};
-
-// u = B t for one symmetric block of dimension D stored as a packed upper
-// triangle (row-major) at R[(qoff + idx) * nel + K]
-template <int D, typename T, typename TS>
-__device__ __forceinline__ void sym_block(const TS* __restrict__ R, int qoff, long nel, long K, const T (&t)[D > 0 ? D : 1],
-                                          T (&u)[D > 0 ? D : 1]) {
-#pragma unroll
-  for (int i = 0; i < D; ++i) u[i] = T(0);
-  int q = qoff;
-#pragma unroll
-  for (int i = 0; i < D; ++i) {
-#pragma unroll
-    for (int j = i; j < D; ++j, ++q) {
-      const T b = (T)__ldcs(R + (size_t)q * nel + K);
-      if (j == i) {
-        u[i] = fma(b, t[i], u[i]);
-      } else {
-        u[i] = fma(b, t[j], u[i]);
-        u[j] = fma(b, t[i], u[j]);
-      }
-    }
-  }
-}
-
-// even / odd node parts of a face vector (see the file comment)
-template <int N1, typename T>
-__device__ __forceinline__ void split_nodes(const T (&v)[N1], T* ev, T* od) {
-  constexpr int h = N1 / 2;
-#pragma unroll
-  for (int i = 0; i < h; ++i) {
-    ev[i] = v[i] + v[N1 - 1 - i];
-    od[i] = v[i] - v[N1 - 1 - i];
-  }
-  if (N1 & 1) ev[h] = v[h];
-}
-
-// transpose of split_nodes
-template <int N1, typename T>
-__device__ __forceinline__ void join_nodes(const T* ev, const T* od, T (&v)[N1]) {
-  constexpr int h = N1 / 2;
-#pragma unroll
-  for (int i = 0; i < h; ++i) {
-    v[i] = ev[i] + od[i];
-    v[N1 - 1 - i] = ev[i] - od[i];
-  }
-  if (N1 & 1) v[h] = ev[h];
-}
-
-struct RedArgs {
-  const void* R;       // reduced blocks [Q][nel] (type TS)
-  const void* v;       // input vector (type T)
-  const void* cvec;    // addend or nullptr
-  void* y;             // output
-  void* z;             // element products [4 n1][nel] (type T)
-  double alpha, beta;
-  int nx, ny;
-};
+using namespace red;
 
 template <int N1, typename TS, typename T, bool DIFF>
-__global__ void __launch_bounds__(128) reduced_elem_kernel(const RedArgs a) {
-  using RD = Red<N1>;
-  constexpr int se = RD::se, so = RD::so;
+__global__ void __launch_bounds__(kElemThreads) reduced_elem_kernel(const RedArgs a) {
+  elem_body<N1, TS, T, DIFF>(a, blockIdx.x * (long)kElemThreads + threadIdx.x);
+}
+
+template <int N1, typename T>
+__global__ void __launch_bounds__(kFaceThreads) reduced_face_kernel(const RedArgs a) {
+  __shared__ T sw[kFaceThreads * N1], ss[kFaceThreads * N1];
+  face_body<N1, T>(a, blockIdx.x * (long)kFaceThreads, threadIdx.x, sw, ss);
+}
+
+// One tile per CTA (reduced = 2): 32 columns (the lanes) x kTileRows rows;
+// warp w walks rows w*kRowsPerWarp.. upwards. Each face that has both of its
+// elements in the tile is finished here: the W face takes the E output of the
+// lane to its left (shuffle), the S face the N output of the row below (the
+// same thread's previous row, or the warp below through shared memory). The
+// faces on the tile's left column and bottom row park their own contribution
+// in the scratch, as do the tile's right column (E) and top row (N) for the
+// neighbouring tiles; reduced_fix_kernel finishes those faces. The sums are
+// taken in the same order as in the two-launch form (own element first), so
+// both forms give identical results.
+constexpr int kTileWarps = 2, kRowsPerWarp = 4, kTileRows = kTileWarps * kRowsPerWarp;
+
+template <int N1, typename TS, typename T, bool DIFF>
+__global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const RedArgs a) {
+  __shared__ T north[kTileWarps][N1][32];
   const int nx = a.nx, ny = a.ny;
   const long nel = (long)nx * ny;
-  const long K = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (K >= nel) return;
-  const int i = (int)(K % nx), j = (int)(K / nx);
-  const T* __restrict__ v = (const T*)a.v;
-  const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
-  const bool hW = i > 0, hE = i < nx - 1, hS = j > 0, hN = j < ny - 1;
-  T xw[N1], xe[N1], xs[N1], xn[N1];
-#pragma unroll
-  for (int q = 0; q < N1; ++q) {
-    xw[q] = hW ? v[eW * N1 + q] : T(0);
-    xe[q] = hE ? v[(eW + 1) * N1 + q] : T(0);
-    xs[q] = hS ? v[eS * N1 + q] : T(0);
-    xn[q] = hN ? v[(eS + nx) * N1 + q] : T(0);
-  }
-  if (DIFF) {   // S_K has zero row sums: apply it to v_K - mean(v_K)
-    T sum = T(0);
-#pragma unroll
-    for (int q = 0; q < N1; ++q) sum += (xw[q] + xe[q]) + (xs[q] + xn[q]);
-    const T mu = sum * (T(1) / T(4 * N1));
-#pragma unroll
-    for (int q = 0; q < N1; ++q) { xw[q] -= mu; xe[q] -= mu; xs[q] -= mu; xn[q] -= mu; }
-  }
-  T P[N1], M[N1], Pp[N1], Mp[N1];
-#pragma unroll
-  for (int q = 0; q < N1; ++q) {
-    P[q] = xw[q] + xe[q]; M[q] = xw[q] - xe[q];
-    Pp[q] = xs[q] + xn[q]; Mp[q] = xs[q] - xn[q];
-  }
-  // t-coordinates of the four blocks
-  T t0[RD::d0 > 0 ? RD::d0 : 1], t1[RD::d1 > 0 ? RD::d1 : 1], t2[RD::d2 > 0 ? RD::d2 : 1],
-      t3[RD::d3 > 0 ? RD::d3 : 1];
-  {
-    T ev[se > 0 ? se : 1], od[so > 0 ? so : 1];
-    split_nodes<N1>(P, ev, od);
-#pragma unroll
-    for (int q = 0; q < se; ++q) t0[q] = ev[q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) t1[q] = od[q];
-    split_nodes<N1>(Pp, ev, od);
-#pragma unroll
-    for (int q = 0; q < se; ++q) t0[se + q] = ev[q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) t2[se + q] = od[q];
-    split_nodes<N1>(M, ev, od);
-#pragma unroll
-    for (int q = 0; q < se; ++q) t2[q] = ev[q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) t3[q] = od[q];
-    split_nodes<N1>(Mp, ev, od);
-#pragma unroll
-    for (int q = 0; q < se; ++q) t1[so + q] = ev[q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) t3[so + q] = od[q];
-  }
-  const TS* __restrict__ R = (const TS*)a.R;
-  T u0[RD::d0 > 0 ? RD::d0 : 1], u1[RD::d1 > 0 ? RD::d1 : 1], u2[RD::d2 > 0 ? RD::d2 : 1],
-      u3[RD::d3 > 0 ? RD::d3 : 1];
-  sym_block<RD::d0, T>(R, RD::q0, nel, K, t0, u0);
-  sym_block<RD::d1, T>(R, RD::q1, nel, K, t1, u1);
-  sym_block<RD::d2, T>(R, RD::q2, nel, K, t2, u2);
-  sym_block<RD::d3, T>(R, RD::q3, nel, K, t3, u3);
-  // back to face dofs: z = F^T u
-  T Po[N1], Mo[N1], Ppo[N1], Mpo[N1];
-  {
-    T ev[se > 0 ? se : 1], od[so > 0 ? so : 1];
-#pragma unroll
-    for (int q = 0; q < se; ++q) ev[q] = u0[q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) od[q] = u1[q];
-    join_nodes<N1>(ev, od, Po);
-#pragma unroll
-    for (int q = 0; q < se; ++q) ev[q] = u2[q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) od[q] = u3[q];
-    join_nodes<N1>(ev, od, Mo);
-#pragma unroll
-    for (int q = 0; q < se; ++q) ev[q] = u0[se + q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) od[q] = u2[se + q];
-    join_nodes<N1>(ev, od, Ppo);
-#pragma unroll
-    for (int q = 0; q < se; ++q) ev[q] = u1[so + q];
-#pragma unroll
-    for (int q = 0; q < so; ++q) od[q] = u3[so + q];
-    join_nodes<N1>(ev, od, Mpo);
-  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tiles_x = (nx + 31) >> 5;
+  const int bx = blockIdx.x % tiles_x, by = blockIdx.x / tiles_x;
+  const int i = bx * 32 + lane;
+  const int j0 = by * kTileRows + w * kRowsPerWarp;
+  const bool col = i < nx;
   T* __restrict__ z = (T*)a.z;
+  T* __restrict__ y = (T*)a.y;
+  const Form<T> form(a);
+  const long nv = (long)(nx + 1) * ny;
+  T zn_prev[N1], zs_first[N1];
 #pragma unroll
-  for (int q = 0; q < N1; ++q) {
-    z[(size_t)(0 * N1 + q) * nel + K] = Po[q] + Mo[q];     // W
-    z[(size_t)(1 * N1 + q) * nel + K] = Po[q] - Mo[q];     // E
-    z[(size_t)(2 * N1 + q) * nel + K] = Ppo[q] + Mpo[q];   // S
-    z[(size_t)(3 * N1 + q) * nel + K] = Ppo[q] - Mpo[q];   // N
+  for (int q = 0; q < N1; ++q) { zn_prev[q] = T(0); zs_first[q] = T(0); }
+  int rows = 0;
+#pragma unroll 1
+  for (int r = 0; r < kRowsPerWarp; ++r) {
+    const int j = j0 + r;
+    if (j >= ny) break;                                   // warp-uniform
+    ++rows;
+    const long K = i + (long)nx * j;
+    T zw[N1], ze[N1], zs[N1], zn[N1];
+    if (col) {
+      elem_product<N1, TS, T, DIFF>(a, nel, K, i, j, zw, ze, zs, zn);
+    } else {
+#pragma unroll
+      for (int q = 0; q < N1; ++q) { zw[q] = T(0); ze[q] = T(0); zs[q] = T(0); zn[q] = T(0); }
+    }
+    T ew[N1];                                             // E output of the element to the left
+#pragma unroll
+    for (int q = 0; q < N1; ++q) ew[q] = __shfl_up_sync(0xffffffffu, ze[q], 1);
+    if (col) {
+      const long eW = i + (long)(nx + 1) * j, eS = nv + i + (long)nx * j;
+      // W face
+      if (i == 0) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[eW * N1 + q] = T(0);
+      } else if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) z[(size_t)(0 * N1 + q) * nel + K] = zw[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[eW * N1 + q] = form(zw[q] + ew[q], (size_t)eW * N1 + q);
+      }
+      if (lane == 31 && i < nx - 1) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) z[(size_t)(1 * N1 + q) * nel + K] = ze[q];
+      }
+      if (i == nx - 1) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[(eW + 1) * N1 + q] = T(0);
+      }
+      // S face
+      if (j == 0) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[eS * N1 + q] = T(0);
+      } else if (r > 0) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[eS * N1 + q] = form(zs[q] + zn_prev[q], (size_t)eS * N1 + q);
+      } else if (w > 0) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) zs_first[q] = zs[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) z[(size_t)(2 * N1 + q) * nel + K] = zs[q];
+      }
+      if (j == ny - 1) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[(eS + nx) * N1 + q] = T(0);
+      } else if (w == kTileWarps - 1 && r == kRowsPerWarp - 1) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) z[(size_t)(3 * N1 + q) * nel + K] = zn[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < N1; ++q) zn_prev[q] = zn[q];
+  }
+  // the N outputs of each warp's last row, for the first row of the warp above
+  if (rows == kRowsPerWarp) {
+#pragma unroll
+    for (int q = 0; q < N1; ++q) north[w][q][lane] = zn_prev[q];
+  }
+  __syncthreads();
+  if (w > 0 && rows > 0 && col && j0 > 0) {
+    const long eS = nv + i + (long)nx * j0;
+#pragma unroll
+    for (int q = 0; q < N1; ++q) y[eS * N1 + q] = form(zs_first[q] + north[w - 1][q][lane], (size_t)eS * N1 + q);
   }
 }
 
+// The faces on tile edges: W faces of columns 32, 64, .. and S faces of rows
+// kTileRows, 2 kTileRows, .. (own contribution + the neighbour's, as above).
 template <int N1, typename T>
-__global__ void __launch_bounds__(256) reduced_face_kernel(const RedArgs a) {
+__global__ void __launch_bounds__(256) reduced_fix_kernel(const RedArgs a) {
   const int nx = a.nx, ny = a.ny;
   const long nel = (long)nx * ny;
-  const long K = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (K >= nel) return;
-  const int i = (int)(K % nx), j = (int)(K / nx);
+  const int tiles_x = (nx + 31) >> 5, tiles_y = (ny + kTileRows - 1) / kTileRows;
+  const long nvert = (long)(tiles_x - 1) * ny, total = nvert + (long)(tiles_y - 1) * nx;
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t >= total) return;
   const T* __restrict__ z = (const T*)a.z;
-  const T* __restrict__ cv = (const T*)a.cvec;
   T* __restrict__ y = (T*)a.y;
-  const T al = (T)a.alpha, be = (T)a.beta;
-  // y = A v, y = c - A v and y = c + A v take no multiply
-  const int form = (al == T(1) && (!cv || be == T(0))) ? 0
-                   : (cv && be == T(1) && al == T(-1)) ? 1 : (cv && be == T(1) && al == T(1)) ? 2 : 3;
-  const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const bool bnd = side == 0 ? (i == 0) : (j == 0);
-    const long e = side == 0 ? eW : eS;
-    const int fo = side == 0 ? 0 : 2;                    // own face W / S
-    const long Kn = side == 0 ? K - 1 : K - nx;           // neighbour across it
-#pragma unroll
-    for (int q = 0; q < N1; ++q) {
-      const size_t o = (size_t)e * N1 + q;
-      T val = T(0);
-      if (!bnd) {
-        const T s = z[(size_t)(fo * N1 + q) * nel + K] + z[(size_t)((fo + 1) * N1 + q) * nel + Kn];
-        if (form == 0) val = s;
-        else if (form == 1) val = cv[o] - s;
-        else if (form == 2) val = cv[o] + s;
-        else {
-          val = al * s;
-          if (cv) val = fma(be, cv[o], val);
-        }
-      }
-      y[o] = val;
-    }
+  const Form<T> form(a);
+  long e, K, Kn;
+  int fo;
+  if (t < nvert) {
+    const int j = (int)(t / (tiles_x - 1)), i = 32 * (int)(t % (tiles_x - 1) + 1);
+    K = i + (long)nx * j; Kn = K - 1; fo = 0;
+    e = i + (long)(nx + 1) * j;
+  } else {
+    const long u = t - nvert;
+    const int i = (int)(u % nx), j = kTileRows * (int)(u / nx + 1);
+    K = i + (long)nx * j; Kn = K - nx; fo = 2;
+    e = (long)(nx + 1) * ny + i + (long)nx * j;
   }
-  if (i == nx - 1) {
 #pragma unroll
-    for (int q = 0; q < N1; ++q) y[(eW + 1) * N1 + q] = T(0);
-  }
-  if (j == ny - 1) {
-#pragma unroll
-    for (int q = 0; q < N1; ++q) y[(eS + nx) * N1 + q] = T(0);
-  }
+  for (int q = 0; q < N1; ++q)
+    y[e * N1 + q] = form(z[(size_t)(fo * N1 + q) * nel + K] + z[(size_t)((fo + 1) * N1 + q) * nel + Kn],
+                         (size_t)e * N1 + q);
 }
 
 template <int N1, typename TS, typename T, bool DIFF>
-cudaError_t red_launch(const RedArgs& a, long nel, cudaStream_t s) {
-  const unsigned g1 = (unsigned)((nel + 127) / 128), g2 = (unsigned)((nel + 255) / 256);
-  reduced_elem_kernel<N1, TS, T, DIFF><<<g1, 128, 0, s>>>(a);
+cudaError_t red_launch(const RedArgs& a, long nel, int mode, cudaStream_t s) {
+  if (mode == 1) {
+    const unsigned g1 = (unsigned)((nel + kElemThreads - 1) / kElemThreads),
+                   g2 = (unsigned)((nel + kFaceThreads - 1) / kFaceThreads);
+    reduced_elem_kernel<N1, TS, T, DIFF><<<g1, kElemThreads, 0, s>>>(a);
+    HDG_CUDA_TRY(cudaGetLastError());
+    reduced_face_kernel<N1, T><<<g2, kFaceThreads, 0, s>>>(a);
+    return cudaGetLastError();
+  }
+  const int tiles_x = (a.nx + 31) / 32, tiles_y = (a.ny + kTileRows - 1) / kTileRows;
+  reduced_tile_kernel<N1, TS, T, DIFF><<<(unsigned)(tiles_x * tiles_y), 32 * kTileWarps, 0, s>>>(a);
   HDG_CUDA_TRY(cudaGetLastError());
-  reduced_face_kernel<N1, T><<<g2, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  const long fix = (long)(tiles_x - 1) * a.ny + (long)(tiles_y - 1) * a.nx;
+  if (fix > 0) {
+    reduced_fix_kernel<N1, T><<<(unsigned)((fix + 255) / 256), 256, 0, s>>>(a);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
 }
 
 template <typename TS, typename T, bool DIFF>
-cudaError_t red_dispatch(int n1, const RedArgs& a, long nel, cudaStream_t s) {
+cudaError_t red_dispatch(int n1, const RedArgs& a, long nel, int mode, cudaStream_t s) {
   switch (n1) {
-    case 1: return red_launch<1, TS, T, DIFF>(a, nel, s);
-    case 2: return red_launch<2, TS, T, DIFF>(a, nel, s);
-    case 3: return red_launch<3, TS, T, DIFF>(a, nel, s);
-    case 4: return red_launch<4, TS, T, DIFF>(a, nel, s);
-    case 5: return red_launch<5, TS, T, DIFF>(a, nel, s);
-    case 6: return red_launch<6, TS, T, DIFF>(a, nel, s);
-    case 7: return red_launch<7, TS, T, DIFF>(a, nel, s);
-    case 8: return red_launch<8, TS, T, DIFF>(a, nel, s);
+    case 1: return red_launch<1, TS, T, DIFF>(a, nel, mode, s);
+    case 2: return red_launch<2, TS, T, DIFF>(a, nel, mode, s);
+    case 3: return red_launch<3, TS, T, DIFF>(a, nel, mode, s);
+    case 4: return red_launch<4, TS, T, DIFF>(a, nel, mode, s);
+    case 5: return red_launch<5, TS, T, DIFF>(a, nel, mode, s);
+    case 6: return red_launch<6, TS, T, DIFF>(a, nel, mode, s);
+    case 7: return red_launch<7, TS, T, DIFF>(a, nel, mode, s);
+    case 8: return red_launch<8, TS, T, DIFF>(a, nel, mode, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -346,6 +298,8 @@ __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict
 
 }  // namespace
 
+int reduced_tile_rows() { return kTileRows; }
+
 int reduced_entries(int n1) {
   const int h = n1 / 2, se = h + (n1 & 1), so = h;
   const int d[4] = {2 * se, so + se, se + so, 2 * so};
@@ -374,12 +328,12 @@ cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, con
   if (prec_double(prec)) {   // FP64 (and the double-vector F32X2 cycles): FP64 blocks
     if (!L.R64) return cudaErrorInvalidValue;
     a.R = L.R64;
-    return red_dispatch<double, double, false>(L.n1, a, nel, s);
+    return red_dispatch<double, double, false>(L.n1, a, nel, c->opt.reduced, s);
   }
   // FP32 / BF16 cycles (float vectors): FP32 blocks applied to v - mean
   if (!L.R32) return cudaErrorInvalidValue;
   a.R = L.R32;
-  return red_dispatch<float, float, true>(L.n1, a, nel, s);
+  return red_dispatch<float, float, true>(L.n1, a, nel, c->opt.reduced, s);
 }
 
 }  // namespace hdg

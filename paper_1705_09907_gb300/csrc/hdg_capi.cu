@@ -207,7 +207,7 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
   hdg_default_options(&o);
   if (opt) o = *opt;
   if (o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.coarse_n < 2 || !(o.tau > 0.0) ||
-      o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 1)
+      o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);
@@ -242,7 +242,10 @@ int hdg_get_info(void* ctx, hdg_info* info) {
   info->nel = c->nel; info->n_edges = c->n_edges; info->ndof = c->ndof; info->k = c->k;
   info->n_plevels = c->k + 1; info->n_hlevels = (int)c->hlev.size(); info->coarse_dim = c->coarse_dim;
   info->device_bytes = c->bytes; info->setup_ms = c->setup_ms; info->vcycle_kernels = c->vcycle_kernels;
-  info->apply_kernels = c->opt.reduced ? 2 : 1;
+  {
+    const bool one_tile = c->mesh.nx <= 32 && c->mesh.ny <= reduced_tile_rows();
+    info->apply_kernels = c->opt.reduced == 1 ? 2 : (c->opt.reduced == 2 && !one_tile) ? 2 : 1;
+  }
   return HDG_OK;
 }
 

@@ -174,6 +174,7 @@ int apply_multi(Context* const* ctx, int n, const void* const* x, void* const* y
 // blocks, their set-up from the dense blocks, and y = beta c + alpha S v for one
 // vector (two launches).
 int reduced_entries(int n1);
+int reduced_tile_rows();                  // rows of one tile of the reduced apply
 cudaError_t launch_reduced_blocks(Context* c, int p, cudaStream_t s);
 cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, const void* cvec, void* y,
                                  double alpha, double beta, cudaStream_t s);

@@ -1,0 +1,262 @@
+// Device code of the reduced-block apply shared by the one-mesh launches
+// (apply_reduced.cu, where the method is described) and the one-launch apply
+// over several meshes (apply_multi.cu).
+#pragma once
+#include "hdg_internal.h"
+
+namespace hdg {
+namespace red {
+
+template <int N1>
+struct Red {
+  static constexpr int se = N1 / 2 + (N1 & 1), so = N1 / 2;                 // even / odd node parts
+  static constexpr int d0 = 2 * se, d1 = so + se, d2 = se + so, d3 = 2 * so;   // block dimensions
+  static constexpr int q0 = 0, q1 = d0 * (d0 + 1) / 2, q2 = q1 + d1 * (d1 + 1) / 2, q3 = q2 + d2 * (d2 + 1) / 2;
+};
+
+// u = B t for one symmetric block of dimension D stored as a packed upper
+// triangle (row-major) at R[(qoff + idx) * nel + K]
+template <int D, typename T, typename TS>
+__device__ __forceinline__ void sym_block(const TS* __restrict__ R, int qoff, long nel, long K, const T (&t)[D > 0 ? D : 1],
+                                          T (&u)[D > 0 ? D : 1]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = T(0);
+  int q = qoff;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = i; j < D; ++j, ++q) {
+      const T b = (T)__ldcs(R + (size_t)q * nel + K);
+      if (j == i) {
+        u[i] = fma(b, t[i], u[i]);
+      } else {
+        u[i] = fma(b, t[j], u[i]);
+        u[j] = fma(b, t[i], u[j]);
+      }
+    }
+  }
+}
+
+// even / odd node parts of a face vector (see the file comment)
+template <int N1, typename T>
+__device__ __forceinline__ void split_nodes(const T (&v)[N1], T* ev, T* od) {
+  constexpr int h = N1 / 2;
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    ev[i] = v[i] + v[N1 - 1 - i];
+    od[i] = v[i] - v[N1 - 1 - i];
+  }
+  if (N1 & 1) ev[h] = v[h];
+}
+
+// transpose of split_nodes
+template <int N1, typename T>
+__device__ __forceinline__ void join_nodes(const T* ev, const T* od, T (&v)[N1]) {
+  constexpr int h = N1 / 2;
+#pragma unroll
+  for (int i = 0; i < h; ++i) {
+    v[i] = ev[i] + od[i];
+    v[N1 - 1 - i] = ev[i] - od[i];
+  }
+  if (N1 & 1) v[h] = ev[h];
+}
+
+struct RedArgs {
+  const void* R;       // reduced blocks [Q][nel] (type TS)
+  const void* v;       // input vector (type T)
+  const void* cvec;    // addend or nullptr
+  void* y;             // output
+  void* z;             // element products [4 n1][nel] (type T)
+  double alpha, beta;
+  int nx, ny;
+};
+
+// z_K = S_K v_K for element K = (i, j) by the reduced product; the four face
+// outputs in zw, ze, zs, zn (boundary faces of v read as zero)
+template <int N1, typename TS, typename T, bool DIFF>
+__device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K, int i, int j, T (&zw)[N1],
+                                             T (&ze)[N1], T (&zs)[N1], T (&zn)[N1]) {
+  using RD = Red<N1>;
+  constexpr int se = RD::se, so = RD::so;
+  const int nx = a.nx, ny = a.ny;
+  const T* __restrict__ v = (const T*)a.v;
+  const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
+  const bool hW = i > 0, hE = i < nx - 1, hS = j > 0, hN = j < ny - 1;
+  T xw[N1], xe[N1], xs[N1], xn[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    xw[q] = hW ? v[eW * N1 + q] : T(0);
+    xe[q] = hE ? v[(eW + 1) * N1 + q] : T(0);
+    xs[q] = hS ? v[eS * N1 + q] : T(0);
+    xn[q] = hN ? v[(eS + nx) * N1 + q] : T(0);
+  }
+  if (DIFF) {   // S_K has zero row sums: apply it to v_K - mean(v_K)
+    T sum = T(0);
+#pragma unroll
+    for (int q = 0; q < N1; ++q) sum += (xw[q] + xe[q]) + (xs[q] + xn[q]);
+    const T mu = sum * (T(1) / T(4 * N1));
+#pragma unroll
+    for (int q = 0; q < N1; ++q) { xw[q] -= mu; xe[q] -= mu; xs[q] -= mu; xn[q] -= mu; }
+  }
+  T P[N1], M[N1], Pp[N1], Mp[N1];
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    P[q] = xw[q] + xe[q]; M[q] = xw[q] - xe[q];
+    Pp[q] = xs[q] + xn[q]; Mp[q] = xs[q] - xn[q];
+  }
+  // t-coordinates of the four blocks
+  T t0[RD::d0 > 0 ? RD::d0 : 1], t1[RD::d1 > 0 ? RD::d1 : 1], t2[RD::d2 > 0 ? RD::d2 : 1],
+      t3[RD::d3 > 0 ? RD::d3 : 1];
+  {
+    T ev[se > 0 ? se : 1], od[so > 0 ? so : 1];
+    split_nodes<N1>(P, ev, od);
+#pragma unroll
+    for (int q = 0; q < se; ++q) t0[q] = ev[q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) t1[q] = od[q];
+    split_nodes<N1>(Pp, ev, od);
+#pragma unroll
+    for (int q = 0; q < se; ++q) t0[se + q] = ev[q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) t2[se + q] = od[q];
+    split_nodes<N1>(M, ev, od);
+#pragma unroll
+    for (int q = 0; q < se; ++q) t2[q] = ev[q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) t3[q] = od[q];
+    split_nodes<N1>(Mp, ev, od);
+#pragma unroll
+    for (int q = 0; q < se; ++q) t1[so + q] = ev[q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) t3[so + q] = od[q];
+  }
+  const TS* __restrict__ R = (const TS*)a.R;
+  T u0[RD::d0 > 0 ? RD::d0 : 1], u1[RD::d1 > 0 ? RD::d1 : 1], u2[RD::d2 > 0 ? RD::d2 : 1],
+      u3[RD::d3 > 0 ? RD::d3 : 1];
+  sym_block<RD::d0, T>(R, RD::q0, nel, K, t0, u0);
+  sym_block<RD::d1, T>(R, RD::q1, nel, K, t1, u1);
+  sym_block<RD::d2, T>(R, RD::q2, nel, K, t2, u2);
+  sym_block<RD::d3, T>(R, RD::q3, nel, K, t3, u3);
+  // back to face dofs: z = F^T u
+  T Po[N1], Mo[N1], Ppo[N1], Mpo[N1];
+  {
+    T ev[se > 0 ? se : 1], od[so > 0 ? so : 1];
+#pragma unroll
+    for (int q = 0; q < se; ++q) ev[q] = u0[q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) od[q] = u1[q];
+    join_nodes<N1>(ev, od, Po);
+#pragma unroll
+    for (int q = 0; q < se; ++q) ev[q] = u2[q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) od[q] = u3[q];
+    join_nodes<N1>(ev, od, Mo);
+#pragma unroll
+    for (int q = 0; q < se; ++q) ev[q] = u0[se + q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) od[q] = u2[se + q];
+    join_nodes<N1>(ev, od, Ppo);
+#pragma unroll
+    for (int q = 0; q < se; ++q) ev[q] = u1[so + q];
+#pragma unroll
+    for (int q = 0; q < so; ++q) od[q] = u3[so + q];
+    join_nodes<N1>(ev, od, Mpo);
+  }
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    zw[q] = Po[q] + Mo[q];
+    ze[q] = Po[q] - Mo[q];
+    zs[q] = Ppo[q] + Mpo[q];
+    zn[q] = Ppo[q] - Mpo[q];
+  }
+}
+
+// epilogue y = beta c + alpha s; y = A v, y = c - A v and y = c + A v take no
+// multiply (FP64 operations are slow on this GPU)
+template <typename T>
+struct Form {
+  int f;
+  T al, be;
+  const T* __restrict__ cv;
+  __device__ __forceinline__ Form(const RedArgs& a) : al((T)a.alpha), be((T)a.beta), cv((const T*)a.cvec) {
+    f = (al == T(1) && (!cv || be == T(0))) ? 0
+        : (cv && be == T(1) && al == T(-1)) ? 1 : (cv && be == T(1) && al == T(1)) ? 2 : 3;
+  }
+  __device__ __forceinline__ T operator()(T s, size_t o) const {
+    if (f == 0) return s;
+    if (f == 1) return cv[o] - s;
+    if (f == 2) return cv[o] + s;
+    T val = al * s;
+    if (cv) val = fma(be, cv[o], val);
+    return val;
+  }
+};
+
+// Pass 1 of the two-launch form for element K: z_K = S_K v_K into the scratch.
+template <int N1, typename TS, typename T, bool DIFF>
+__device__ __forceinline__ void elem_body(const RedArgs& a, long K) {
+  const int nx = a.nx, ny = a.ny;
+  const long nel = (long)nx * ny;
+  if (K >= nel) return;
+  const int i = (int)(K % nx), j = (int)(K / nx);
+  T zw[N1], ze[N1], zs[N1], zn[N1];
+  elem_product<N1, TS, T, DIFF>(a, nel, K, i, j, zw, ze, zs, zn);
+  T* __restrict__ z = (T*)a.z;
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    z[(size_t)(0 * N1 + q) * nel + K] = zw[q];
+    z[(size_t)(1 * N1 + q) * nel + K] = ze[q];
+    z[(size_t)(2 * N1 + q) * nel + K] = zs[q];
+    z[(size_t)(3 * N1 + q) * nel + K] = zn[q];
+  }
+}
+
+constexpr int kElemThreads = 128, kFaceThreads = 256;
+
+// Pass 2 for the kFaceThreads elements from K0 (t = thread index; every
+// thread of the CTA calls it): each owned face from its two contributions.
+// The face sums are staged in shared memory (sw, ss: kFaceThreads * N1 each)
+// so that y (and the addend) are then written / read in dof order: the W (and
+// S) edges of consecutive elements of a row are consecutive, so each warp
+// store is one contiguous run instead of 32 runs of n1 values.
+template <int N1, typename T>
+__device__ __forceinline__ void face_body(const RedArgs& a, long K0, int t, T* sw, T* ss) {
+  const int nx = a.nx, ny = a.ny;
+  const long nel = (long)nx * ny;
+  const long K = K0 + t;
+  const T* __restrict__ z = (const T*)a.z;
+  T* __restrict__ y = (T*)a.y;
+  const long nv = (long)(nx + 1) * ny;
+  if (K < nel) {
+    const int i = (int)(K % nx), j = (int)(K / nx);
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+      sw[t * N1 + q] = i > 0 ? z[(size_t)(0 * N1 + q) * nel + K] + z[(size_t)(1 * N1 + q) * nel + K - 1] : T(0);
+      ss[t * N1 + q] = j > 0 ? z[(size_t)(2 * N1 + q) * nel + K] + z[(size_t)(3 * N1 + q) * nel + K - nx] : T(0);
+    }
+    // the E / N domain-boundary edges have no owner element: zero them here
+    if (i == nx - 1) {
+#pragma unroll
+      for (int q = 0; q < N1; ++q) y[(i + 1 + (long)(nx + 1) * j) * N1 + q] = T(0);
+    }
+    if (j == ny - 1) {
+#pragma unroll
+      for (int q = 0; q < N1; ++q) y[(nv + i + (long)nx * (j + 1)) * N1 + q] = T(0);
+    }
+  }
+  __syncthreads();
+  const Form<T> form(a);
+  const int cnt = (int)((nel - K0) < kFaceThreads ? (nel - K0) : kFaceThreads);
+  for (int idx = t; idx < cnt * N1; idx += kFaceThreads) {
+    const int tt = idx / N1, q = idx - tt * N1;
+    const long Kt = K0 + tt;
+    const int i = (int)(Kt % nx), j = (int)(Kt / nx);
+    const size_t ow = (size_t)(i + (long)(nx + 1) * j) * N1 + q;
+    const size_t os = (size_t)(nv + i + (long)nx * j) * N1 + q;
+    y[ow] = i > 0 ? form(sw[idx], ow) : T(0);
+    y[os] = j > 0 ? form(ss[idx], os) : T(0);
+  }
+}
+
+}  // namespace red
+}  // namespace hdg

@@ -1,5 +1,6 @@
-"""One persistent launch over several uneven meshes (hdg_apply_multi) against
-each mesh's own apply and, for one instance, the FP64 oracle."""
+"""One launch (per pass) over several uneven meshes (hdg_apply_multi) against
+each mesh's own apply and, for one instance, the FP64 oracle: dense owner
+records (reduced = 0) and reduced blocks (reduced = 1)."""
 import numpy as np
 import pytest
 import torch
@@ -77,3 +78,33 @@ def test_setup_batch_and_multi_apply():
     with pytest.raises(hdg.HDGError) as e:
         hdg.setup_batch(bad)
     assert e.value.status == hdg.HDG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_multi_instance_reduced_blocks(prec):
+    """Contexts with reduced blocks: the batch runs the element and face passes
+    of the reduced apply once each for all instances; every instance's result
+    is bitwise equal to its own apply (the same per-element arithmetic) and
+    one instance matches the oracle."""
+    from paper_1705_09907_gb300 import hdg
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    probs = [(nx, ny, k, torch.as_tensor(np.exp(inputs.gaussian_field(nx, seed=q, corr_len=0.3, ny=ny)),
+                                         device="cuda")) for q, (nx, ny, k) in enumerate(CASES)]
+    sols = hdg.setup_batch(probs, reduced=1)
+    xs = [torch.as_tensor(inputs.random_trace(s.n_edges, s.k, seed=80 + q), dtype=dt, device="cuda")
+          for q, s in enumerate(sols)]
+    ys = hdg.apply_multi(sols, xs, prec=prec)
+    for s, x, y in zip(sols, xs, ys):
+        assert torch.equal(y, s.apply(x, prec=prec))
+    nx, ny, k = CASES[2]
+    m = omesh.Mesh(nx, ny)
+    prob = ohdg.HDGProblem(m, k, probs[2][3].cpu().numpy())
+    xh = xs[2].double().cpu().numpy()
+    ref = prob.apply_assembled(xh)
+    A, idx = prob.assemble_interior()
+    bound = np.zeros_like(ref)
+    bound[idx] = abs(A) @ np.abs(xh[idx])
+    tol = 1e-12 if prec == "fp64" else 3e-6
+    assert np.all(np.abs(ys[2].double().cpu().numpy() - ref) <= tol * bound + 1e-30)
+    for s in sols:
+        s.close()
