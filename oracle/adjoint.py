@@ -10,10 +10,14 @@ discrete solve (the trace vector lambda is the state u of J; Euclidean norm):
     dJ/df       = (db/df)^T psi
 
 with dA/dtheta_K = A_K^T (dS_K/dtheta_K) A_K and S_K, b_K from Eqs. shur0 and
-shur1 as in oracle.hdg. Only the (kappa^-1 q, v) block of the local system L_K
-depends on theta_K, and d(kappa^-1)/dtheta = -kappa^-1, so
-    dL/dtheta = [[-A, 0], [0, 0]],  d(L^-1) = -L^-1 (dL) L^-1,
-    dS_K = -[G tau H] L^-1 dL L^-1 [C; E],  db_K = -[G tau H] L^-1 dL L^-1 [0; F].
+shur1 as in oracle.hdg:
+    S_K = GH L^-1 CE + tau Ml,  b_K = GH L^-1 [0; F],  GH = [G  tau H],
+    CE = [C; E],  d(L^-1) = -L^-1 (dL) L^-1.
+With tau fixed only the (kappa^-1 q, v) block A of L_K depends on theta_K, and
+d(kappa^-1)/dtheta = -kappa^-1: dL = [[-A, 0], [0, 0]]. With tau_K = kappa_K
+the tau-proportional pieces vary too (d tau/dtheta = tau): D and E of L_K and
+CE, the tau H half of GH and tau Ml, so dL also has D in its (u, u) block,
+dCE = [0; E], dGH = [0, tau H] and d(tau Ml) = tau Ml.
 """
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -51,13 +55,21 @@ def gradients(prob, f_q, lam_obs):
         GH = np.hstack([mt["G"], mt["tau"] * mt["H"]])
         dL = np.zeros_like(L)
         dL[:2 * n, :2 * n] = -mt["A"]
+        dCE = np.zeros_like(CE)
+        dGH = np.zeros_like(GH)
+        dMl = np.zeros_like(mt["Ml"])
+        if prob.tau == "kappa":
+            dL[2 * n:, 2 * n:] = mt["D"]
+            dCE[2 * n:] = mt["E"]
+            dGH[:, 2 * n:] = mt["tau"] * mt["H"]
+            dMl = mt["tau"] * mt["Ml"]
         rhsF = np.zeros(3 * n)
         rhsF[2 * n:] = F[e]
         Linv_CE = np.linalg.solve(L, CE)
         Linv_F = np.linalg.solve(L, rhsF)
         GH_Linv = np.linalg.solve(L.T, GH.T).T
-        dS = -GH_Linv @ dL @ Linv_CE
-        db = -GH_Linv @ dL @ Linv_F
+        dS = dGH @ Linv_CE - GH_Linv @ dL @ Linv_CE + GH_Linv @ dCE + dMl
+        db = dGH @ Linv_F - GH_Linv @ dL @ Linv_F
         d = prob.dofs(e)
         dtheta[e] = psi[d] @ (db - dS @ lam[d])
         # db_K/dF = GH L^-1 [0; I]  ->  dJ/dF_K = [0 I] L^-T GH^T psi_K
@@ -66,9 +78,9 @@ def gradients(prob, f_q, lam_obs):
     return J, lam, dtheta, df.reshape(nel, prob.p + 2, prob.p + 2)
 
 
-def objective(mesh, p, log_kappa, f_q, lam_obs):
+def objective(mesh, p, log_kappa, f_q, lam_obs, tau=1.0):
     """J(theta, f) by a fresh direct solve (for finite differences)."""
-    prob = hdg.HDGProblem(mesh, p, np.exp(log_kappa))
+    prob = hdg.HDGProblem(mesh, p, np.exp(log_kappa), tau)
     lam = prob.solve_direct(prob.condense_rhs(f_q))
     r = lam - lam_obs
     r[np.setdiff1d(np.arange(prob.ndof), prob.interior_dofs())] = 0.0

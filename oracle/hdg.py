@@ -221,12 +221,18 @@ def f_quadrature_points(mesh, p):
 
 
 class HDGProblem:
-    """All element blocks of one mesh, degree p, per-element kappa, tau = 1."""
+    """All element blocks of one mesh, degree p, per-element kappa.
+
+    tau: the stabilisation on every face of every element, a positive number
+    (1 in Sec. 5 for the model problem), or "kappa" for tau_K = kappa_K on the
+    faces of element K (tau piecewise constant per element, Sec. 3)."""
 
     def __init__(self, mesh, p, kappa, tau=1.0, kappa_q_fn=None, nquad=None):
         self.mesh = mesh
         self.p = p
         self.kappa = np.asarray(kappa, dtype=np.float64).reshape(mesh.nel)
+        if not (tau == "kappa" or (np.isscalar(tau) and float(tau) > 0.0)):
+            raise ValueError("tau must be a positive number or 'kappa'")
         self.tau = tau
         self.ref = RefElement(p, mesh.hx, mesh.hy, nquad=nquad)
         self.n1 = p + 1
@@ -244,7 +250,10 @@ class HDGProblem:
             gy = oy + self.mesh.hy * (self.ref.xq + 1) / 2
             X, Y = np.meshgrid(gx, gy)
             kq = self.kappa_q_fn(X.ravel(), Y.ravel())
-        return element_matrices(self.ref, self.kappa[e], self.tau, kappa_q=kq)
+        return element_matrices(self.ref, self.kappa[e], self.tau_of(e), kappa_q=kq)
+
+    def tau_of(self, e):
+        return float(self.kappa[e]) if self.tau == "kappa" else float(self.tau)
 
     def dofs(self, e):
         """Global trace dof indices of element e's local Lambda_K (the map A_K)."""

@@ -180,27 +180,41 @@ def test_coarse_direct_solve():
     assert np.abs(Ac @ x - r).max() < 1e-13 * np.abs(r).max()
 
 
-def test_adjoint_vs_finite_differences():
+@pytest.mark.parametrize("tau", [1.0, "kappa"])
+def test_adjoint_vs_finite_differences(tau):
     rng = np.random.default_rng(7)
     m = omesh.Mesh(4, 4)
     p = 2
     th = rng.normal(size=m.nel)
     fq = rng.normal(size=(m.nel, p + 2, p + 2))
     lam_obs = rng.normal(size=m.n_edges * (p + 1))
-    J, lam, dth, df = adjoint.gradients(hdg.HDGProblem(m, p, np.exp(th)), fq, lam_obs)
+    prob = hdg.HDGProblem(m, p, np.exp(th), tau)
+    J, lam, dth, df = adjoint.gradients(prob, fq, lam_obs)
     h = 1e-6
     for e in (0, 6, 15):
         tp, tm = th.copy(), th.copy()
         tp[e] += h
         tm[e] -= h
-        fd = (adjoint.objective(m, p, tp, fq, lam_obs) - adjoint.objective(m, p, tm, fq, lam_obs)) / (2 * h)
+        fd = (adjoint.objective(m, p, tp, fq, lam_obs, tau) - adjoint.objective(m, p, tm, fq, lam_obs, tau)) / (2 * h)
         assert abs(fd - dth[e]) <= 1e-5 * max(abs(fd), 1e-3)
     for (e, a, b) in ((3, 1, 2), (9, 0, 3)):
         fp, fm = fq.copy(), fq.copy()
         fp[e, a, b] += h
         fm[e, a, b] -= h
-        fd = (adjoint.objective(m, p, th, fp, lam_obs) - adjoint.objective(m, p, th, fm, lam_obs)) / (2 * h)
+        fd = (adjoint.objective(m, p, th, fp, lam_obs, tau) - adjoint.objective(m, p, th, fm, lam_obs, tau)) / (2 * h)
         assert abs(fd - df[e, a, b]) <= 1e-5 * max(abs(fd), 1e-3)
+    if tau == "kappa":
+        # S_K = kappa_K S_ref and b_K does not depend on kappa_K, so
+        # dJ/dtheta_K = -psi_K^T S_K lambda_K (psi = A^-1 (lambda - lambda_obs))
+        A, idx = prob.assemble_interior()
+        r = np.zeros(prob.ndof)
+        r[idx] = (lam - lam_obs)[idx]
+        psi = np.zeros(prob.ndof)
+        psi[idx] = np.linalg.solve(A.toarray(), r[idx])
+        for e in range(m.nel):
+            d = prob.dofs(e)
+            closed = -psi[d] @ hdg.schur_block(prob.mats(e)) @ lam[d]
+            assert abs(closed - dth[e]) <= 1e-10 * np.abs(dth).max()
 
 
 def test_lognormal_field_statistics():

@@ -81,6 +81,34 @@ def test_schur_reflection_symmetry(p):
                 assert np.abs(S[np.ix_(swap, swap)] - S).max() > 1e-3 * scale
 
 
+@pytest.mark.parametrize("p", range(0, 6))
+def test_tau_kappa_scaling(p):
+    """With tau_K = kappa_K every local equation is kappa_K times the kappa = 1,
+    tau = 1 one once q is written as kappa q~ (the (kappa^-1 q, v) block becomes
+    (q~, v), the flux and stabilisation terms gain a factor kappa), so
+    S_K = kappa_K S_ref exactly and b_K = G^T F does not depend on kappa_K. The
+    per-element problem's tau_of must follow kappa."""
+    rng = np.random.default_rng(50 + p)
+    for hx, hy in ((0.1, 0.1), (0.3, 0.07)):
+        ref = hdg.RefElement(p, hx, hy)
+        S1 = hdg.schur_block(hdg.element_matrices(ref, 1.0, 1.0))
+        F = rng.normal(size=ref.n)
+        b1 = hdg.rhs_block(hdg.element_matrices(ref, 1.0, 1.0), F)
+        for kappa in (1e-3, 0.37, 42.0):
+            mt = hdg.element_matrices(ref, kappa, kappa)
+            assert np.abs(hdg.schur_block(mt) - kappa * S1).max() < 1e-12 * kappa * np.abs(S1).max()
+            assert np.abs(hdg.rhs_block(mt, F) - b1).max() < 1e-12 * np.abs(b1).max()
+            # tau fixed at 1 is not a scaling
+            S_t1 = hdg.schur_block(hdg.element_matrices(ref, kappa, 1.0))
+            assert np.abs(S_t1 - kappa * S1).max() > 1e-3 * kappa * np.abs(S1).max()
+    m = omesh.Mesh(3, 2)
+    kap = np.array([0.5, 2.0, 7.0, 1.0, 3.0, 0.25])
+    prob = hdg.HDGProblem(m, p, kap, "kappa")
+    assert [prob.tau_of(e) for e in range(m.nel)] == list(kap)
+    with pytest.raises(ValueError):
+        hdg.HDGProblem(m, p, kap, "other")
+
+
 @pytest.mark.parametrize("p", range(0, 5))
 def test_schur_energy_identity(p):
     """Independent second formula: lambda^T S mu = (kappa^-1 q_l, q_m)_K
@@ -127,16 +155,17 @@ def test_integration_by_parts_block():
         assert np.abs(mt["B2"] - mt["B"]).max() < 1e-13
 
 
+@pytest.mark.parametrize("tau", [1.0, "kappa"])
 @pytest.mark.parametrize("p", [0, 1, 2, 3])
-def test_condensed_equals_uncondensed(p):
+def test_condensed_equals_uncondensed(p, tau):
     rng = np.random.default_rng(30 + p)
     m = omesh.Mesh(3, 4, 0.0, 0.0, 1.5, 1.0)
     kappa = np.exp(rng.normal(size=m.nel))
     fq = rng.normal(size=(m.nel, p + 2, p + 2))
-    prob = hdg.HDGProblem(m, p, kappa)
+    prob = hdg.HDGProblem(m, p, kappa, tau)
     lam = prob.solve_direct(prob.condense_rhs(fq))
     u, q = prob.recover(lam, fq)
-    lam2, u2, q2 = hdg.uncondensed_solve(m, p, kappa, fq)
+    lam2, u2, q2 = hdg.uncondensed_solve(m, p, kappa, fq, tau)
     assert np.abs(lam - lam2).max() < 1e-12 * np.abs(lam2).max()
     assert np.abs(u - u2).max() < 1e-12 * np.abs(u2).max()
     assert np.abs(q - q2).max() < 1e-12 * np.abs(q2).max()
