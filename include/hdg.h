@@ -98,6 +98,12 @@ typedef struct {
                                  small launch for the faces on tile edges;
                                  0: the dense owner records (kernel chosen by
                                  `autotune`)                                 */
+  int tau_kappa;              /* 1: tau_K = kappa_K on the faces of element K
+                                 (tau piecewise constant per element, Sec. 3;
+                                 `tau` is unused): every local equation then
+                                 scales with kappa_K, S_K = kappa_K S_ref and
+                                 the condensed right-hand side does not depend
+                                 on kappa; 0: tau = `tau` everywhere (0)     */
 } hdg_options;
 
 typedef struct {

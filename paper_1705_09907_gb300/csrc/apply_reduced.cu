@@ -296,7 +296,52 @@ __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict
   }
 }
 
+// dth_K = -psi_K^T (S_K lambda_K): the reduced product of lambda, dotted with
+// the element's four faces of psi (boundary faces read as zero)
+template <int N1>
+__global__ void __launch_bounds__(kElemThreads) reduced_theta_kernel(const RedArgs a, const double* __restrict__ psi,
+                                                                     double* __restrict__ dth) {
+  const int nx = a.nx, ny = a.ny;
+  const long nel = (long)nx * ny;
+  const long K = blockIdx.x * (long)kElemThreads + threadIdx.x;
+  if (K >= nel) return;
+  const int i = (int)(K % nx), j = (int)(K / nx);
+  double zw[N1], ze[N1], zs[N1], zn[N1];
+  elem_product<N1, double, double, false>(a, nel, K, i, j, zw, ze, zs, zn);
+  const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
+  double d = 0.0;
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    if (i > 0) d = fma(psi[eW * N1 + q], zw[q], d);
+    if (i < nx - 1) d = fma(psi[(eW + 1) * N1 + q], ze[q], d);
+    if (j > 0) d = fma(psi[eS * N1 + q], zs[q], d);
+    if (j < ny - 1) d = fma(psi[(eS + nx) * N1 + q], zn[q], d);
+  }
+  dth[K] = -d;
+}
+
 }  // namespace
+
+cudaError_t launch_reduced_theta(Context* c, const double* lam, const double* psi, double* dth, cudaStream_t s) {
+  PLevel& L = c->plev[c->k];
+  if (!L.R64) return cudaErrorInvalidValue;
+  RedArgs a{};
+  a.R = L.R64; a.v = lam;
+  a.nx = c->mesh.nx; a.ny = c->mesh.ny;
+  const unsigned g = (unsigned)((c->nel + kElemThreads - 1) / kElemThreads);
+  switch (L.n1) {
+    case 1: reduced_theta_kernel<1><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 2: reduced_theta_kernel<2><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 3: reduced_theta_kernel<3><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 4: reduced_theta_kernel<4><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 5: reduced_theta_kernel<5><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 6: reduced_theta_kernel<6><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 7: reduced_theta_kernel<7><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    case 8: reduced_theta_kernel<8><<<g, kElemThreads, 0, s>>>(a, psi, dth); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 int reduced_tile_rows() { return kTileRows; }
 

@@ -49,7 +49,7 @@ extern "C" {
 void hdg_default_options(hdg_options* o) {
   if (!o) return;
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
-  o->autotune = 1; o->reduced = 1;
+  o->autotune = 1; o->reduced = 1; o->tau_kappa = 0;
 }
 
 const char* hdg_error_string(int s) {
@@ -120,7 +120,7 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   TRY(ctx_alloc(c, (void**)&c->Ainv, (size_t)c->nel * n * n * sizeof(double)));
   TRY(ctx_alloc(c, (void**)&c->Gfac, (size_t)c->nel * n * m * sizeof(double)));
   TRY(ctx_alloc(c, (void**)&c->elem_scratch, (size_t)c->nel * m * sizeof(double)));
-  if (c->opt.reduced) TRY(ctx_alloc(c, &c->red_z, (size_t)c->nel * m * sizeof(double)));
+  if (c->opt.reduced || c->opt.tau_kappa) TRY(ctx_alloc(c, &c->red_z, (size_t)c->nel * m * sizeof(double)));
   // p-levels
   c->plev.resize(k + 1);
   const int spr = (c->mesh.nx + kSeg - 1) / kSeg;
@@ -132,10 +132,12 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     L.rec_entries = (size_t)L.nseg * L.R * kSeg;
     TRY(cudaMallocAsync((void**)&L.Sdense, (size_t)c->nel * L.m * L.m * sizeof(double), s));
     TRY(ctx_alloc(c, (void**)&L.S64, L.rec_entries * sizeof(double)));
-    if (c->opt.reduced) {
+    // reduced blocks: for the reduced apply, and with tau_K = kappa_K also for
+    // the adjoint gradient (-psi_K^T S_K lambda_K per element)
+    if (c->opt.reduced || c->opt.tau_kappa) {
       const size_t q = (size_t)reduced_entries(L.n1) * c->nel;
       TRY(ctx_alloc(c, (void**)&L.R64, q * sizeof(double)));
-      if (mixed) TRY(ctx_alloc(c, (void**)&L.R32, q * sizeof(float)));
+      if (mixed && c->opt.reduced) TRY(ctx_alloc(c, (void**)&L.R32, q * sizeof(float)));
     }
     if (mixed) {
       TRY(ctx_alloc(c, (void**)&L.S32, L.rec_entries * sizeof(float)));
@@ -175,7 +177,7 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   for (int p = k; p >= 1; --p) TRY(launch_galerkin_coarsen(c, p, s));
   for (int p = k; p >= 0; --p) {
     TRY(launch_build_records(c, p, s));
-    if (c->opt.reduced) TRY(launch_reduced_blocks(c, p, s));
+    if (c->opt.reduced || c->opt.tau_kappa) TRY(launch_reduced_blocks(c, p, s));
     if (p >= 1) TRY(launch_asm_blocks(c, p, s));
   }
   // CG / reduction scratch
@@ -207,7 +209,8 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
   hdg_default_options(&o);
   if (opt) o = *opt;
   if (o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.coarse_n < 2 || !(o.tau > 0.0) ||
-      o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2)
+      o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2 ||
+      o.tau_kappa < 0 || o.tau_kappa > 1)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);

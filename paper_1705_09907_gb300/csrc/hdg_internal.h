@@ -178,6 +178,9 @@ int reduced_tile_rows();                  // rows of one tile of the reduced app
 cudaError_t launch_reduced_blocks(Context* c, int p, cudaStream_t s);
 cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, const void* cvec, void* y,
                                  double alpha, double beta, cudaStream_t s);
+// dth_K = -psi_K^T S_K lambda_K per element at level k (the adjoint gradient
+// with tau_K = kappa_K)
+cudaError_t launch_reduced_theta(Context* c, const double* lam, const double* psi, double* dth, cudaStream_t s);
 
 // Trace-operator apply on the record layout of level p:
 //   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)

@@ -5,7 +5,10 @@
 //   condensed RHS  b_K = G^T F                            (= W^T A_u^-1 F)
 //   recovery       U = A_u^-1 (F + W lambda_K)
 //                  Q_c = kappa (M^-1 B_c^T U - M^-1 C_c lambda_K)
-//   adjoint        dJ/dtheta_K = -(kappa^-1 q(lambda, f), q(psi, 0))_K
+//   adjoint        dJ/dtheta_K = -(kappa^-1 q(lambda, f), q(psi, 0))_K  (tau fixed)
+//                  dJ/dtheta_K = -psi_K^T S_K lambda_K                 (tau_K = kappa_K:
+//                                S_K = kappa_K S_ref and b_K does not depend on kappa_K;
+//                                from the reduced blocks, apply_reduced.cu)
 //                  dJ/df_q     = w_q |J| u(psi, 0)(x_q)
 #include "hdg_internal.h"
 
@@ -15,6 +18,7 @@ namespace hdg {
 struct LocalArgs {
   int nel, n, m, nf;
   double tau;
+  int tau_kappa;                 // 1: tau_K = kappa_K
   const double *Ainv, *Gfac, *kappa;
   const double *Vf, *wJf, *M;
   // transposed reference matrices (one contiguous row per column of the original)
@@ -95,7 +99,7 @@ static LocalArgs local_args(Context* c) {
   LocalArgs a{};
   a.nel = c->nel; a.n = c->ref.n; a.m = c->ref.m; a.nf = c->ref.nf;
   a.Ainv = c->Ainv; a.Gfac = c->Gfac; a.kappa = c->kappa;
-  a.tau = c->opt.tau;
+  a.tau = c->opt.tau; a.tau_kappa = c->opt.tau_kappa;
   a.Vf = c->d_ref + c->off_Vf; a.wJf = c->d_ref + c->off_wJf; a.M = c->d_ref + c->off_M;
   a.ZT = c->d_ref + c->off_ZT; a.EbT = c->d_ref + c->off_EbT;
   a.MiBtT = c->d_ref + c->off_MiBtT; a.MiCT = c->d_ref + c->off_MiCT; a.VfT = c->d_ref + c->off_VfT;
@@ -168,7 +172,7 @@ template <bool H>
 __device__ __forceinline__ void warp_local_solution(const LocalArgs& a, int e, double lc, int lane, double& f0,
                                                     double& f1, double (&q)[4]) {
   const int n = a.n, m = a.m;
-  const double kap = a.kappa[e], tau = a.tau;
+  const double kap = a.kappa[e], tau = a.tau_kappa ? kap : a.tau;
   double z0 = 0.0, z1 = 0.0, b0 = 0.0, b1 = 0.0;          // Z lambda, Eb lambda
   for (int c = 0; c < m; ++c) {
     const double l = __shfl_sync(0xffffffffu, lc, c);
@@ -289,9 +293,14 @@ __global__ void adjoint_warp_kernel(LocalArgs a, int nx, int ny, const double* _
 cudaError_t launch_adjoint(Context* c, const double* f_q, const double* lam, const double* psi, double* dJ_dlogk,
                            double* dJ_df, cudaStream_t s) {
   LocalArgs a = local_args(c);
-  if (a.n > 32) adjoint_warp_kernel<true><<<warp_grid(c->nel, c->num_sms), 256, 0, s>>>(a, c->mesh.nx, c->mesh.ny, lam, psi, f_q, dJ_dlogk, dJ_df);
-  else adjoint_warp_kernel<false><<<warp_grid(c->nel, c->num_sms), 256, 0, s>>>(a, c->mesh.nx, c->mesh.ny, lam, psi, f_q, dJ_dlogk, dJ_df);
-  return cudaGetLastError();
+  double* dth = c->opt.tau_kappa ? nullptr : dJ_dlogk;
+  if (dth || dJ_df) {
+    if (a.n > 32) adjoint_warp_kernel<true><<<warp_grid(c->nel, c->num_sms), 256, 0, s>>>(a, c->mesh.nx, c->mesh.ny, lam, psi, f_q, dth, dJ_df);
+    else adjoint_warp_kernel<false><<<warp_grid(c->nel, c->num_sms), 256, 0, s>>>(a, c->mesh.nx, c->mesh.ny, lam, psi, f_q, dth, dJ_df);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  if (c->opt.tau_kappa && dJ_dlogk) return launch_reduced_theta(c, lam, psi, dJ_dlogk, s);
+  return cudaSuccess;
 }
 
 }  // namespace hdg

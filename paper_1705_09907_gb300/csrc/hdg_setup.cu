@@ -32,7 +32,7 @@ struct LocalTables {
   const double *P, *Mb, *Z, *Eb, *Y, *Ml;
 };
 
-__global__ void local_setup_kernel(int nel, int n, int m, double tau, const double* __restrict__ kappa,
+__global__ void local_setup_kernel(int nel, int n, int m, double tau, int tau_kappa, const double* __restrict__ kappa,
                                    LocalTables tb, double* __restrict__ Sout, double* __restrict__ Ainv_out,
                                    double* __restrict__ Gout, int* err) {
   extern __shared__ double sm[];
@@ -43,8 +43,9 @@ __global__ void local_setup_kernel(int nel, int n, int m, double tau, const doub
   double* X = W + n * m;                     // A_u^-1, one column per lane
   for (int e = blockIdx.x * wpb + wid; e < nel; e += gridDim.x * wpb) {
     const double kap = kappa[e];
-    for (int idx = lane; idx < n * n; idx += 32) A[idx] = kap * tb.P[idx] + tau * tb.Mb[idx];
-    for (int idx = lane; idx < n * m; idx += 32) W[idx] = kap * tb.Z[idx] + tau * tb.Eb[idx];
+    const double te = tau_kappa ? kap : tau;          // tau_K
+    for (int idx = lane; idx < n * n; idx += 32) A[idx] = kap * tb.P[idx] + te * tb.Mb[idx];
+    for (int idx = lane; idx < n * m; idx += 32) W[idx] = kap * tb.Z[idx] + te * tb.Eb[idx];
     __syncwarp();
     // right-looking Cholesky, lower triangle in place
     bool bad = false;
@@ -76,7 +77,7 @@ __global__ void local_setup_kernel(int nel, int n, int m, double tau, const doub
     double* S = Sout + (size_t)e * m * m;
     for (int idx = lane; idx < m * m; idx += 32) {
       const int r = idx / m, c = idx % m;
-      double s = kap * tb.Y[idx] + ((r == c) ? tau * tb.Ml[r] : 0.0);
+      double s = kap * tb.Y[idx] + ((r == c) ? te * tb.Ml[r] : 0.0);
       for (int i = 0; i < n; ++i) s -= W[i * m + r] * W[i * m + c];
       S[idx] = s;
     }
@@ -129,7 +130,7 @@ cudaError_t launch_local_setup(Context* c, cudaStream_t s) {
   int blocks = (c->nel + wpb - 1) / wpb;
   const int cap = c->num_sms * 16;
   if (blocks > cap) blocks = cap;
-  local_setup_kernel<<<blocks, 32 * wpb, smem, s>>>(c->nel, n, m, c->opt.tau, c->kappa, tb,
+  local_setup_kernel<<<blocks, 32 * wpb, smem, s>>>(c->nel, n, m, c->opt.tau, c->opt.tau_kappa, c->kappa, tb,
                                                     c->plev[c->k].Sdense, c->Ainv, c->Gfac, c->err_flag);
   return cudaGetLastError();
 }
