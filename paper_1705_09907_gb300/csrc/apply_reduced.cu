@@ -296,6 +296,44 @@ __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict
   }
 }
 
+constexpr int kColsWarps = 4;             // elements per CTA of the column kernels
+
+template <int N1, typename TS, typename T, bool DIFF>
+__global__ void __launch_bounds__(32 * kColsWarps) reduced_cols_elem_kernel(const RedArgs a, int nb) {
+  cols_elem_body<N1, TS, T, DIFF>(a, blockIdx.x * (long)kColsWarps + (threadIdx.x >> 5), nb,
+                                  blockIdx.y * 32 + (threadIdx.x & 31));
+}
+
+template <int N1, typename T>
+__global__ void __launch_bounds__(32 * kColsWarps) reduced_cols_face_kernel(const RedArgs a, int nb) {
+  cols_face_body<N1, T>(a, blockIdx.x * (long)kColsWarps + (threadIdx.x >> 5), nb,
+                        blockIdx.y * 32 + (threadIdx.x & 31));
+}
+
+template <int N1, typename TS, typename T, bool DIFF>
+cudaError_t red_cols_launch(const RedArgs& a, long nel, int nb, cudaStream_t s) {
+  const dim3 g((unsigned)((nel + kColsWarps - 1) / kColsWarps), (unsigned)((nb + 31) / 32));
+  reduced_cols_elem_kernel<N1, TS, T, DIFF><<<g, 32 * kColsWarps, 0, s>>>(a, nb);
+  HDG_CUDA_TRY(cudaGetLastError());
+  reduced_cols_face_kernel<N1, T><<<g, 32 * kColsWarps, 0, s>>>(a, nb);
+  return cudaGetLastError();
+}
+
+template <typename TS, typename T, bool DIFF>
+cudaError_t red_cols_dispatch(int n1, const RedArgs& a, long nel, int nb, cudaStream_t s) {
+  switch (n1) {
+    case 1: return red_cols_launch<1, TS, T, DIFF>(a, nel, nb, s);
+    case 2: return red_cols_launch<2, TS, T, DIFF>(a, nel, nb, s);
+    case 3: return red_cols_launch<3, TS, T, DIFF>(a, nel, nb, s);
+    case 4: return red_cols_launch<4, TS, T, DIFF>(a, nel, nb, s);
+    case 5: return red_cols_launch<5, TS, T, DIFF>(a, nel, nb, s);
+    case 6: return red_cols_launch<6, TS, T, DIFF>(a, nel, nb, s);
+    case 7: return red_cols_launch<7, TS, T, DIFF>(a, nel, nb, s);
+    case 8: return red_cols_launch<8, TS, T, DIFF>(a, nel, nb, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // dth_K = -psi_K^T (S_K lambda_K): the reduced product of lambda, dotted with
 // the element's four faces of psi (boundary faces read as zero)
 template <int N1>
@@ -321,6 +359,23 @@ __global__ void __launch_bounds__(kElemThreads) reduced_theta_kernel(const RedAr
 }
 
 }  // namespace
+
+cudaError_t launch_reduced_cols(Context* c, int p, int prec, const void* v, const void* cvec, void* y, double alpha,
+                                double beta, int nb, void* z, cudaStream_t s) {
+  PLevel& L = c->plev[p];
+  RedArgs a{};
+  a.v = v; a.cvec = cvec; a.y = y; a.z = z;
+  a.alpha = alpha; a.beta = beta;
+  a.nx = c->mesh.nx; a.ny = c->mesh.ny;
+  if (prec_double(prec)) {
+    if (!L.R64) return cudaErrorInvalidValue;
+    a.R = L.R64;
+    return red_cols_dispatch<double, double, false>(L.n1, a, c->nel, nb, s);
+  }
+  if (!L.R32) return cudaErrorInvalidValue;
+  a.R = L.R32;
+  return red_cols_dispatch<float, float, true>(L.n1, a, c->nel, nb, s);
+}
 
 cudaError_t launch_reduced_theta(Context* c, const double* lam, const double* psi, double* dth, cudaStream_t s) {
   PLevel& L = c->plev[c->k];

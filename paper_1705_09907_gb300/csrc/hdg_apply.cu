@@ -8,6 +8,16 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
   PLevel& L = c->plev[p];
   if (which == 0 && nrhs == 1 && c->opt.reduced)
     return launch_reduced_apply(c, p, prec, v, cvec, y, alpha, beta, s);
+  // columns with double vectors: the reduced column kernels (FP64-pipe bound,
+  // 2x fewer operations); float columns keep the dense column kernel, which
+  // reads the blocks once for all columns and beats the reduced form's scratch
+  // round trip when the pass is bandwidth bound (0.27 vs 0.47 ms at 256^2,
+  // k = 5, 64 right-hand sides)
+  if (which == 0 && nrhs > 1 && c->opt.reduced && c->cur_zb && prec_double(prec)) {
+    const size_t need = (size_t)c->nel * L.m * nrhs * sizeof(double);
+    if (need <= c->cur_zb_bytes)
+      return launch_reduced_cols(c, p, prec, v, cvec, y, alpha, beta, nrhs, c->cur_zb, s);
+  }
   const void* rec = nullptr;
   if (prec == HDG_PREC_FP64) rec = which ? (const void*)L.M64 : (const void*)L.S64;
   else if (prec == HDG_PREC_FP32) rec = which ? (const void*)L.M32 : (const void*)L.S32;

@@ -286,6 +286,13 @@ int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void*
   if (!c || !x || !y || nrhs < 1 || x == y) return HDG_ERR_INVALID_ARG;
   if (prec < 0 || prec > 3) return HDG_ERR_INVALID_ARG;
   if (!prec_ok(c, prec)) return HDG_ERR_UNSUPPORTED;
+  // many right-hand sides on reduced blocks: the scratch of the batched work
+  // (allocated on the first call with this nrhs)
+  if (nrhs > 1 && c->opt.reduced == 1) {
+    const cudaError_t e = use_batched_work(c, nrhs, prec);
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HDG_ERR_OOM; }
+    TRY(e);
+  }
   TRY(launch_apply(c, c->k, 0, prec, x, nullptr, y, 1.0, 0.0, nrhs, (cudaStream_t)stream));
   return HDG_OK;
 }

@@ -102,6 +102,7 @@ struct VWork {
   double* cg_part = nullptr;                // [3][reduction blocks][nb]
   double* h_sc = nullptr;                   // pinned host mirror [2][nb]
   std::vector<void*> own;                   // device buffers owned by this work
+  void* red_z = nullptr;                    // batched reduced-apply scratch [4(k+1)][nel][nb]
 };
 
 struct Context {
@@ -144,6 +145,10 @@ struct Context {
   // V-cycle work: single vector (double, float family) and batched (on demand)
   VWork w1[2];                              // [0] double, [1] float
   VWork* wb[2] = {nullptr, nullptr};
+  // the reduced-apply scratch of the batched work whose cycle, solve or apply
+  // is being issued (launch_apply with nrhs > 1 uses it; null: dense columns)
+  void* cur_zb = nullptr;
+  size_t cur_zb_bytes = 0;
   int vcycle_kernels = 0;                   // kernel nodes of the captured V-cycle
   // uniform coefficient: the shared block for the tensor-core batched apply
   bool uniform_kappa = false;
@@ -178,6 +183,10 @@ int reduced_tile_rows();                  // rows of one tile of the reduced app
 cudaError_t launch_reduced_blocks(Context* c, int p, cudaStream_t s);
 cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, const void* cvec, void* y,
                                  double alpha, double beta, cudaStream_t s);
+// the same for nb right-hand sides ([ndof][nb]) with the scratch z of
+// nel * 4(p+1) * nb vector entries (a batched work's)
+cudaError_t launch_reduced_cols(Context* c, int p, int prec, const void* v, const void* cvec, void* y, double alpha,
+                                double beta, int nb, void* z, cudaStream_t s);
 // dth_K = -psi_K^T S_K lambda_K per element at level k (the adjoint gradient
 // with tau_K = kappa_K)
 cudaError_t launch_reduced_theta(Context* c, const double* lam, const double* psi, double* dth, cudaStream_t s);
@@ -201,6 +210,9 @@ int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rto
                       hdg_solve_info* info, cudaStream_t s);
 // releases the V-cycle works' graphs and the batched works' buffers
 void release_works(Context* c);
+// makes the batched work of nb right-hand sides (vector type of prec) current
+// for column applies: allocates it on first use, sets cur_zb
+cudaError_t use_batched_work(Context* c, int nb, int prec);
 
 // Vector helpers (hdg_apply.cu)
 cudaError_t vec_dot(Context* c, const double* a, const double* b, int n, double* out_dev, cudaStream_t s);

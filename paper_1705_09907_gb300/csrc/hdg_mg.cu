@@ -923,6 +923,10 @@ static cudaError_t batched_work(Context* c, int nb, bool dbl, VWork** out) {
     w->coarse_w = (double*)work_alloc(w, (size_t)c->coarse_dim * nb * sizeof(double));
     ok = w->coarse_w != nullptr;
   }
+  if (ok && c->opt.reduced == 1) {   // double-sized: the batched CG's outer apply is FP64 in every mode
+    w->red_z = work_alloc(w, (size_t)c->nel * c->ref.m * nb * sizeof(double));
+    ok = w->red_z != nullptr;
+  }
   if (!ok) {
     release_work(*w);
     delete w;
@@ -933,11 +937,24 @@ static cudaError_t batched_work(Context* c, int nb, bool dbl, VWork** out) {
   return cudaSuccess;
 }
 
+static void set_cols_scratch(Context* c, const VWork* w) {
+  c->cur_zb = w->red_z;
+  c->cur_zb_bytes = w->red_z ? (size_t)c->nel * c->ref.m * w->nb * sizeof(double) : 0;
+}
+
+cudaError_t use_batched_work(Context* c, int nb, int prec) {
+  VWork* w = nullptr;
+  HDG_CUDA_TRY(batched_work(c, nb, prec_double(prec), &w));
+  set_cols_scratch(c, w);
+  return cudaSuccess;
+}
+
 cudaError_t vcycle(Context* c, int prec, const void* r, void* z, int nb, cudaStream_t s) {
   const bool dbl = prec_double(prec);
   if (nb == 1) return vcycle_typed(c, c->w1[dbl ? 0 : 1], prec, r, z, false, s);
   VWork* w = nullptr;
   HDG_CUDA_TRY(batched_work(c, nb, dbl, &w));
+  set_cols_scratch(c, w);
   return vcycle_typed(c, *w, prec, r, z, false, s);
 }
 
@@ -1310,6 +1327,7 @@ int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rto
   VWork* w = nullptr;
   if (batched_work(c, nb, prec_double(inner), &w) != cudaSuccess) return HDG_ERR_OOM;
   if (work_cg(c, w) != cudaSuccess) return HDG_ERR_OOM;
+  set_cols_scratch(c, w);
   const size_t n = (size_t)c->ndof * nb;
   const int g = grid_for(n);
   const int gs = (nb + 255) / 256;

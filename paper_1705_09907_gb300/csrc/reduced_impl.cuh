@@ -73,9 +73,10 @@ struct RedArgs {
 
 // z_K = S_K v_K for element K = (i, j) by the reduced product; the four face
 // outputs in zw, ze, zs, zn (boundary faces of v read as zero)
+// (v: column `col` of nb right-hand sides stored right-hand side fastest)
 template <int N1, typename TS, typename T, bool DIFF>
 __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K, int i, int j, T (&zw)[N1],
-                                             T (&ze)[N1], T (&zs)[N1], T (&zn)[N1]) {
+                                             T (&ze)[N1], T (&zs)[N1], T (&zn)[N1], int nb = 1, int col = 0) {
   using RD = Red<N1>;
   constexpr int se = RD::se, so = RD::so;
   const int nx = a.nx, ny = a.ny;
@@ -85,10 +86,10 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
   T xw[N1], xe[N1], xs[N1], xn[N1];
 #pragma unroll
   for (int q = 0; q < N1; ++q) {
-    xw[q] = hW ? v[eW * N1 + q] : T(0);
-    xe[q] = hE ? v[(eW + 1) * N1 + q] : T(0);
-    xs[q] = hS ? v[eS * N1 + q] : T(0);
-    xn[q] = hN ? v[(eS + nx) * N1 + q] : T(0);
+    xw[q] = hW ? v[(eW * N1 + q) * nb + col] : T(0);
+    xe[q] = hE ? v[((eW + 1) * N1 + q) * nb + col] : T(0);
+    xs[q] = hS ? v[(eS * N1 + q) * nb + col] : T(0);
+    xn[q] = hN ? v[((eS + nx) * N1 + q) * nb + col] : T(0);
   }
   if (DIFF) {   // S_K has zero row sums: apply it to v_K - mean(v_K)
     T sum = T(0);
@@ -255,6 +256,53 @@ __device__ __forceinline__ void face_body(const RedArgs& a, long K0, int t, T* s
     const size_t os = (size_t)(nv + i + (long)nx * j) * N1 + q;
     y[ow] = i > 0 ? form(sw[idx], ow) : T(0);
     y[os] = j > 0 ? form(ss[idx], os) : T(0);
+  }
+}
+
+// Many right-hand sides (v, y: [ndof][nb], right-hand side fastest): element K
+// and column col per thread, a warp over 32 consecutive columns of one element
+// (the block entries it reads are the same for the whole warp: one broadcast
+// load each, reused by 32 columns). Scratch z: [4 n1][nel][nb].
+template <int N1, typename TS, typename T, bool DIFF>
+__device__ __forceinline__ void cols_elem_body(const RedArgs& a, long K, int nb, int col) {
+  const int nx = a.nx, ny = a.ny;
+  const long nel = (long)nx * ny;
+  if (K >= nel || col >= nb) return;
+  const int i = (int)(K % nx), j = (int)(K / nx);
+  T zw[N1], ze[N1], zs[N1], zn[N1];
+  elem_product<N1, TS, T, DIFF>(a, nel, K, i, j, zw, ze, zs, zn, nb, col);
+  T* __restrict__ z = (T*)a.z;
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    z[((size_t)(0 * N1 + q) * nel + K) * nb + col] = zw[q];
+    z[((size_t)(1 * N1 + q) * nel + K) * nb + col] = ze[q];
+    z[((size_t)(2 * N1 + q) * nel + K) * nb + col] = zs[q];
+    z[((size_t)(3 * N1 + q) * nel + K) * nb + col] = zn[q];
+  }
+}
+
+template <int N1, typename T>
+__device__ __forceinline__ void cols_face_body(const RedArgs& a, long K, int nb, int col) {
+  const int nx = a.nx, ny = a.ny;
+  const long nel = (long)nx * ny;
+  if (K >= nel || col >= nb) return;
+  const int i = (int)(K % nx), j = (int)(K / nx);
+  const T* __restrict__ z = (const T*)a.z;
+  T* __restrict__ y = (T*)a.y;
+  const Form<T> form(a);
+  const long nv = (long)(nx + 1) * ny;
+  const long eW = i + (long)(nx + 1) * j, eS = nv + i + (long)nx * j;
+#pragma unroll
+  for (int q = 0; q < N1; ++q) {
+    const size_t ow = (size_t)(eW * N1 + q) * nb + col, os = (size_t)(eS * N1 + q) * nb + col;
+    y[ow] = i > 0 ? form(z[((size_t)(0 * N1 + q) * nel + K) * nb + col] +
+                         z[((size_t)(1 * N1 + q) * nel + K - 1) * nb + col], ow)
+                  : T(0);
+    y[os] = j > 0 ? form(z[((size_t)(2 * N1 + q) * nel + K) * nb + col] +
+                         z[((size_t)(3 * N1 + q) * nel + K - nx) * nb + col], os)
+                  : T(0);
+    if (i == nx - 1) y[((eW + 1) * N1 + q) * nb + col] = T(0);
+    if (j == ny - 1) y[((eS + nx) * N1 + q) * nb + col] = T(0);
   }
 }
 

@@ -22,12 +22,14 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
+@pytest.mark.parametrize("reduced", [1, 0])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("f32x2", 1e-12), ("fp32", 3e-6), ("bf16", 1.2e-2)])
 @pytest.mark.parametrize("k,nb", [(0, 2), (1, 33), (3, 64), (5, 7), (7, 3)])
-def test_column_apply_vs_assembled(prec, tol, k, nb):
+def test_column_apply_vs_assembled(prec, tol, k, nb, reduced):
     """FP64 / F32X2: rounding of an 8(k+1)-term sum (~48 bits for F32X2); FP32 and
     BF16 blocks: entry rounding 2^-24 / 2^-9 with FP32 accumulation. Bound
-    relative to |A||x| per entry; boundary rows of x are nonzero and ignored."""
+    relative to |A||x| per entry; boundary rows of x are nonzero and ignored.
+    reduced = 1: the reduced-block column kernels; 0: the dense column kernel."""
     from paper_1705_09907_gb300 import hdg
     nx, ny = 37, 6
     m = omesh.Mesh(nx, ny)
@@ -38,7 +40,7 @@ def test_column_apply_vs_assembled(prec, tol, k, nb):
     dt = torch.float64 if prec in ("fp64", "f32x2") else torch.float32
     Xd = cuda(X, dt)
     Xh = host(Xd)
-    s = hdg.HDGSolver(nx, ny, k, cuda(kap))
+    s = hdg.HDGSolver(nx, ny, k, cuda(kap), reduced=reduced)
     Y = host(s.apply(Xd, prec=prec))
     ref = np.zeros_like(Xh)
     ref[idx] = A @ Xh[idx]

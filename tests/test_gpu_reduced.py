@@ -80,3 +80,23 @@ def test_vcycle_forms_agree_and_match_oracle(prec, k, nx, ny):
     z = host(zs[0])
     tol = 1e-11 if prec == "fp64" else 1e-4
     assert np.linalg.norm(z - z_ref) <= tol * np.linalg.norm(z_ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+@pytest.mark.parametrize("k,nb", [(0, 3), (2, 33), (4, 64), (7, 5)])
+def test_column_kernels_equal_single_vector_applies(prec, k, nb):
+    """The reduced column kernels (nb right-hand sides, right-hand side
+    fastest; used for double vectors) do per column exactly the arithmetic of
+    the one-vector reduced apply: every column is bitwise equal to its own
+    single apply."""
+    from paper_1705_09907_gb300 import hdg
+    nx, ny = 45, 11
+    m = omesh.Mesh(nx, ny)
+    kap = np.exp(inputs.gaussian_field(nx, seed=k, corr_len=0.3, ny=ny))
+    dt = torch.float64
+    s = hdg.HDGSolver(nx, ny, k, cuda(kap))
+    X = cuda(inputs.random_trace(m.n_edges, k, seed=400 + k, nrhs=nb), dt)
+    Y = s.apply(X, prec=prec)
+    for j in range(nb):
+        assert torch.equal(Y[:, j], s.apply(X[:, j].contiguous(), prec=prec)), j
+    s.close()
