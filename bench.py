@@ -603,31 +603,34 @@ def run_reference(args):
 
 
 def run_profile_apply(args):
-    """A small fixed launch sequence for kernel captures (ncu --set full): one
-    FP64-only context (lognormal kappa, seed 0; a few GB on the device at
-    512^2, k = 4), then 3 applies of the condensed blocks on the reduced
-    blocks (NVTX range apply_reduced) and 3 on the dense owner records with the
-    autotuned kernel that also applies the Schwarz blocks (apply_dense)."""
+    """A small fixed launch sequence for kernel captures (ncu --set full): a
+    context (lognormal kappa, seed 0; FP64 only for --prec fp64, about 6 GB on
+    the device at 512^2, k = 4), then 3 applies of the condensed blocks in
+    --prec on the reduced blocks (NVTX range apply_reduced) and 3 on the dense
+    owner records with the autotuned kernel that also applies the Schwarz
+    blocks (apply_dense)."""
     import torch
 
     from paper_1705_09907_gb300 import hdg, inputs
 
-    N, k = args.n, args.k
+    N, k, prec = args.n, args.k, args.prec
     kap = torch.as_tensor(inputs.lognormal_kappa(N, SEED), device="cuda")
     x = torch.as_tensor(inputs.random_trace(2 * N * (N + 1), k, seed=1), device="cuda")
+    if prec in ("fp32", "bf16"):
+        x = x.float()
     y = torch.empty_like(x)
     for name, red in (("apply_reduced", 1), ("apply_dense", 0)):
-        s = hdg.HDGSolver(N, N, k, kap, mixed=0, reduced=red)
+        s = hdg.HDGSolver(N, N, k, kap, mixed=0 if prec == "fp64" else 1, reduced=red)
         for _ in range(args.warmup):
-            s.apply(x, out=y)
+            s.apply(x, prec, out=y)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push(name)
         for _ in range(3):
-            s.apply(x, out=y)
+            s.apply(x, prec, out=y)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         s.close()
-    print(json.dumps({"profile_apply": True, "n": N, "k": k}))
+    print(json.dumps({"profile_apply": True, "n": N, "k": k, "prec": prec}))
 
 
 def main():
@@ -642,7 +645,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="one solve step and 3 applies per precision, then exit")
     ap.add_argument("--profile-apply", action="store_true",
-                    help="FP64-only context, 3 reduced and 3 dense condensed-block applies (kernel captures)")
+                    help="3 reduced and 3 dense condensed-block applies in --prec (kernel captures)")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16", "f32x2"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
