@@ -75,8 +75,9 @@ cudaError_t vec_fill(void* p, int prec, size_t n, cudaStream_t s) {
 namespace hdg {
 
 // Set-up autotuner: for every level, precision and block kind, time the
-// candidate launch shapes (warps per CTA x ring stages per warp) on a test
-// vector and keep the fastest. Shapes only change speed, never results.
+// candidate launch shapes (warps per CTA x ring stages per warp, and the
+// segment kernel with 8 / 4 / 2 warps) on a test vector and keep the fastest.
+// The shapes differ only in the order in which the products are summed.
 // bytes of one ring stage with its x windows and partial sums (matches
 // stage_total_bytes in the launcher)
 static unsigned stage_bytes_of(int n1, int prec) {

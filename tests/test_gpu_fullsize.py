@@ -20,11 +20,11 @@ from paper_1705_09907_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def _oracle_edge_rows(m, k, kappa, fq, edges):
+def _oracle_edge_rows(m, k, kappa, fq, edges, tau=1.0):
     """For each sampled interior edge, per adjacent element: (S_K rows of the
     edge, the element's global dofs, b_K rows of the edge)."""
     el, fc = m.edge_to_elem()
-    prob = ohdg.HDGProblem(m, k, kappa)
+    prob = ohdg.HDGProblem(m, k, kappa, tau)
     out = []
     for e in edges:
         rows = []
@@ -145,3 +145,42 @@ def test_fullsize_uneven_instances_sampled():
             assert np.all(np.abs(yh[e * n1:(e + 1) * n1] - y1h[e * n1:(e + 1) * n1]) <= 2e-12 * scale)
     for s in sols:
         s.close()
+
+
+def test_fullsize_tau_kappa_sampled():
+    """512 x 512, k = 4, lognormal kappa (seed 0), f = 1 with tau_K = kappa_K:
+    the reduced apply, the condensed right-hand side and the solve's residual at
+    300 sampled interior edges against the oracle's element blocks (tau = kappa),
+    as in the tau = 1 check above."""
+    from paper_1705_09907_gb300 import hdg
+    N, k = 512, 4
+    m = omesh.Mesh(N, N)
+    kappa = inputs.lognormal_kappa(N, 0)
+    fq = inputs.constant_f(N, k)
+    edges = np.random.default_rng(77).choice(m.interior_edges(), size=300, replace=False)
+    rows, prob = _oracle_edge_rows(m, k, kappa, fq, edges, tau="kappa")
+    boundary = np.setdiff1d(np.arange(prob.ndof), prob.interior_dofs())
+    n1 = k + 1
+    s = hdg.HDGSolver(N, N, k, torch.as_tensor(kappa, device="cuda"), tau_kappa=1)
+    x = inputs.random_trace(m.n_edges, k, seed=8)
+    y = s.apply(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    xm = x.copy()
+    xm[boundary] = 0.0
+    for e, rr in zip(edges, rows):
+        ref = sum(S @ xm[d] for S, d, _ in rr)
+        scale = sum(np.abs(S) @ np.abs(xm[d]) for S, d, _ in rr)
+        assert np.all(np.abs(y[e * n1:(e + 1) * n1] - ref) <= 1e-12 * scale)
+    b = s.condense_rhs(torch.as_tensor(fq, device="cuda"))
+    b_h = b.cpu().numpy()
+    bmax, b2 = np.abs(b_h).max(), np.linalg.norm(b_h)
+    for e, rr in zip(edges, rows):
+        assert np.abs(b_h[e * n1:(e + 1) * n1] - sum(bk for _, _, bk in rr)).max() <= 1e-12 * bmax
+    rtol = 1e-10
+    lam, info = s.solve(b, rtol=rtol, maxit=400)
+    assert info["relres"] <= rtol
+    lam_h = lam.cpu().numpy()
+    for e, rr in zip(edges, rows):
+        res = sum(bk for _, _, bk in rr) - sum(S @ lam_h[d] for S, d, _ in rr)
+        absl = sum(np.abs(S) @ np.abs(lam_h[d]) for S, d, _ in rr)
+        assert np.all(np.abs(res) <= rtol * b2 + 1e-13 * absl)
+    s.close()

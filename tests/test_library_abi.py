@@ -70,3 +70,20 @@ def test_setup_batch_rejects_bad_arguments_before_any_device_work(lib):
     # the first instance is invalid (nx < 2): rejected before anything is set up
     assert hdg.hdg_setup_batch(2, ms, ks, kp, None, None, out) == hdg.HDG_ERR_INVALID_ARG
     assert out[0] is None and out[1] is None
+
+
+def test_options_validated_before_any_device_work(lib):
+    """Out-of-range options are rejected by hdg_setup before it touches a
+    device (the kappa pointer is never read); the defaults are the documented
+    ones."""
+    from paper_1705_09907_gb300 import hdg
+    d = hdg.default_options()
+    assert (d.nu1, d.nu2, d.coarse_n, d.tau, d.cheb_degree, d.mixed, d.use_graphs, d.autotune, d.reduced,
+            d.tau_kappa) == (2, 2, 2, 1.0, 2, 1, 1, 1, 1, 0)
+    ctx = ctypes.c_void_p()
+    m = hdg.hdg_mesh(4, 4, 0.0, 0.0, 1.0, 1.0)
+    for bad in ({"reduced": 3}, {"reduced": -1}, {"tau_kappa": 2}, {"tau": 0.0}, {"nu1": 0},
+                {"cheb_degree": 9}, {"coarse_n": 1}):
+        o = hdg.default_options(**bad)
+        st = hdg.hdg_setup(ctypes.byref(m), 1, ctypes.c_void_p(16), ctypes.byref(o), None, ctypes.byref(ctx))
+        assert st == hdg.HDG_ERR_INVALID_ARG, bad
