@@ -34,7 +34,8 @@
 //      tile (shuffles across the row, registers and shared memory up the
 //      column); the faces on tile edges go through a small second launch.
 // The blocks are read once, directly from HBM with coalesced streaming loads
-// ([Q][nel]: the 32 lanes of a warp read 32 consecutive elements' entry q).
+// (warp chunks [nel/32][Q][32]: the 32 lanes of a warp read 32 consecutive
+// elements' entry q, and a warp's Q entries are one contiguous chunk).
 #include "reduced_impl.cuh"
 
 namespace hdg {
@@ -291,8 +292,9 @@ __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict
     for (int x = 0; x < ci.cnt; ++x)
       for (int y = 0; y < cj.cnt; ++y) acc += ci.sg[x] * cj.sg[y] * S[ci.dof[x] * m + cj.dof[y]];
     const double val = acc / (double)(ci.cnt * cj.cnt);
-    R64[t] = val;
-    if (R32) R32[t] = (float)val;
+    const size_t o = red_base(K, Q) + (size_t)q * 32;
+    R64[o] = val;
+    if (R32) R32[o] = (float)val;
   }
 }
 

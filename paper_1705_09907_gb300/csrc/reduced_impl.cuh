@@ -12,12 +12,19 @@ struct Red {
   static constexpr int se = N1 / 2 + (N1 & 1), so = N1 / 2;                 // even / odd node parts
   static constexpr int d0 = 2 * se, d1 = so + se, d2 = se + so, d3 = 2 * so;   // block dimensions
   static constexpr int q0 = 0, q1 = d0 * (d0 + 1) / 2, q2 = q1 + d1 * (d1 + 1) / 2, q3 = q2 + d2 * (d2 + 1) / 2;
+  static constexpr int Q = q3 + d3 * (d3 + 1) / 2;                            // entries per element
 };
 
+// Block layout: warp-sized chunks, entry q of element K at
+// [((K / 32) * Q + q) * 32 + K % 32] — the 32 consecutive elements of a warp
+// read entry q as one 128 / 256-byte run, and all of a warp's entries form one
+// contiguous chunk (Q runs in a row, so DRAM pages are read sequentially).
+__device__ __forceinline__ size_t red_base(long K, int Q) { return ((size_t)(K >> 5) * Q) * 32 + (K & 31); }
+
 // u = B t for one symmetric block of dimension D stored as a packed upper
-// triangle (row-major) at R[(qoff + idx) * nel + K]
+// triangle (row-major) from entry qoff on (base = red_base(K, Q))
 template <int D, typename T, typename TS>
-__device__ __forceinline__ void sym_block(const TS* __restrict__ R, int qoff, long nel, long K, const T (&t)[D > 0 ? D : 1],
+__device__ __forceinline__ void sym_block(const TS* __restrict__ R, int qoff, size_t base, const T (&t)[D > 0 ? D : 1],
                                           T (&u)[D > 0 ? D : 1]) {
 #pragma unroll
   for (int i = 0; i < D; ++i) u[i] = T(0);
@@ -26,7 +33,7 @@ __device__ __forceinline__ void sym_block(const TS* __restrict__ R, int qoff, lo
   for (int i = 0; i < D; ++i) {
 #pragma unroll
     for (int j = i; j < D; ++j, ++q) {
-      const T b = (T)__ldcs(R + (size_t)q * nel + K);
+      const T b = (T)__ldcs(R + base + (size_t)q * 32);
       if (j == i) {
         u[i] = fma(b, t[i], u[i]);
       } else {
@@ -62,7 +69,7 @@ __device__ __forceinline__ void join_nodes(const T* ev, const T* od, T (&v)[N1])
 }
 
 struct RedArgs {
-  const void* R;       // reduced blocks [Q][nel] (type TS)
+  const void* R;       // reduced blocks, warp chunks [nel/32][Q][32] (type TS)
   const void* v;       // input vector (type T)
   const void* cvec;    // addend or nullptr
   void* y;             // output
@@ -134,10 +141,11 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
   const TS* __restrict__ R = (const TS*)a.R;
   T u0[RD::d0 > 0 ? RD::d0 : 1], u1[RD::d1 > 0 ? RD::d1 : 1], u2[RD::d2 > 0 ? RD::d2 : 1],
       u3[RD::d3 > 0 ? RD::d3 : 1];
-  sym_block<RD::d0, T>(R, RD::q0, nel, K, t0, u0);
-  sym_block<RD::d1, T>(R, RD::q1, nel, K, t1, u1);
-  sym_block<RD::d2, T>(R, RD::q2, nel, K, t2, u2);
-  sym_block<RD::d3, T>(R, RD::q3, nel, K, t3, u3);
+  const size_t base = red_base(K, RD::Q);
+  sym_block<RD::d0, T>(R, RD::q0, base, t0, u0);
+  sym_block<RD::d1, T>(R, RD::q1, base, t1, u1);
+  sym_block<RD::d2, T>(R, RD::q2, base, t2, u2);
+  sym_block<RD::d3, T>(R, RD::q3, base, t3, u3);
   // back to face dofs: z = F^T u
   T Po[N1], Mo[N1], Ppo[N1], Mpo[N1];
   {
