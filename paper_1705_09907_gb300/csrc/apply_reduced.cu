@@ -292,9 +292,8 @@ __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict
     for (int x = 0; x < ci.cnt; ++x)
       for (int y = 0; y < cj.cnt; ++y) acc += ci.sg[x] * cj.sg[y] * S[ci.dof[x] * m + cj.dof[y]];
     const double val = acc / (double)(ci.cnt * cj.cnt);
-    const size_t o = red_base(K, Q) + (size_t)q * 32;
-    R64[o] = val;
-    if (R32) R32[o] = (float)val;
+    R64[red_base(K, Q) + (size_t)q * 32] = val;
+    if (R32) R32[red_index32(K, Q, q)] = (float)val;
   }
 }
 

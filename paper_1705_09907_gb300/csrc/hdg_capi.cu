@@ -135,9 +135,10 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     // reduced blocks: for the reduced apply, and with tau_K = kappa_K also for
     // the adjoint gradient (-psi_K^T S_K lambda_K per element)
     if (c->opt.reduced || c->opt.tau_kappa) {
-      const size_t q = (size_t)reduced_entries(L.n1) * (((size_t)c->nel + 31) / 32 * 32);   // warp chunks
-      TRY(ctx_alloc(c, (void**)&L.R64, q * sizeof(double)));
-      if (mixed && c->opt.reduced) TRY(ctx_alloc(c, (void**)&L.R32, q * sizeof(float)));
+      const size_t ep = ((size_t)c->nel + 31) / 32 * 32;                     // warp chunks
+      const size_t Q = (size_t)reduced_entries(L.n1);
+      TRY(ctx_alloc(c, (void**)&L.R64, Q * ep * sizeof(double)));
+      if (mixed && c->opt.reduced) TRY(ctx_alloc(c, (void**)&L.R32, (Q + 3) / 4 * 4 * ep * sizeof(float)));
     }
     if (mixed) {
       TRY(ctx_alloc(c, (void**)&L.S32, L.rec_entries * sizeof(float)));

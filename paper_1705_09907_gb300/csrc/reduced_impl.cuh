@@ -21,6 +21,37 @@ struct Red {
 // contiguous chunk (Q runs in a row, so DRAM pages are read sequentially).
 __device__ __forceinline__ size_t red_base(long K, int Q) { return ((size_t)(K >> 5) * Q) * 32 + (K & 31); }
 
+// FP32 blocks: the same chunks in groups of four entries, entry q of element K
+// at [((K / 32) * ceil(Q / 4) + q / 4) * 128 + (K % 32) * 4 + q % 4], so a
+// thread reads its entries as float4 (one 512-byte run per warp and group) and
+// has ceil(Q/4) wide loads in flight before any arithmetic
+__host__ __device__ constexpr int red_groups(int Q) { return (Q + 3) / 4; }
+__device__ __forceinline__ size_t red_index32(long K, int Q, int q) {
+  return ((size_t)(K >> 5) * red_groups(Q) + (q >> 2)) * 128 + (K & 31) * 4 + (q & 3);
+}
+
+// u = B t for one block whose entries are already in registers (bq: the
+// element's entries from the block's first on)
+template <int D, typename T>
+__device__ __forceinline__ void sym_block_reg(const float* bq, const T (&t)[D > 0 ? D : 1], T (&u)[D > 0 ? D : 1]) {
+#pragma unroll
+  for (int i = 0; i < D; ++i) u[i] = T(0);
+  int q = 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+#pragma unroll
+    for (int j = i; j < D; ++j, ++q) {
+      const T b = (T)bq[q];
+      if (j == i) {
+        u[i] = fma(b, t[i], u[i]);
+      } else {
+        u[i] = fma(b, t[j], u[i]);
+        u[j] = fma(b, t[i], u[j]);
+      }
+    }
+  }
+}
+
 // u = B t for one symmetric block of dimension D stored as a packed upper
 // triangle (row-major) from entry qoff on (base = red_base(K, Q))
 template <int D, typename T, typename TS>
@@ -69,7 +100,7 @@ __device__ __forceinline__ void join_nodes(const T* ev, const T* od, T (&v)[N1])
 }
 
 struct RedArgs {
-  const void* R;       // reduced blocks, warp chunks [nel/32][Q][32] (type TS)
+  const void* R;       // reduced blocks in warp chunks (type TS; see red_base / red_index32)
   const void* v;       // input vector (type T)
   const void* cvec;    // addend or nullptr
   void* y;             // output
@@ -86,6 +117,19 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
                                              T (&ze)[N1], T (&zs)[N1], T (&zn)[N1], int nb = 1, int col = 0) {
   using RD = Red<N1>;
   constexpr int se = RD::se, so = RD::so;
+  // FP32 blocks: every entry of the element loaded first, as float4
+  constexpr bool kVec = sizeof(TS) == 4;
+  constexpr int G = kVec ? red_groups(RD::Q) : 1;
+  float bq[4 * G];
+  if (kVec) {
+    const float4* __restrict__ R4 = (const float4*)a.R;
+    const size_t g0 = ((size_t)(K >> 5) * G) * 32 + (K & 31);
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const float4 w = __ldcs(R4 + g0 + (size_t)g * 32);
+      bq[4 * g] = w.x; bq[4 * g + 1] = w.y; bq[4 * g + 2] = w.z; bq[4 * g + 3] = w.w;
+    }
+  }
   const int nx = a.nx, ny = a.ny;
   const T* __restrict__ v = (const T*)a.v;
   const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
@@ -141,11 +185,18 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
   const TS* __restrict__ R = (const TS*)a.R;
   T u0[RD::d0 > 0 ? RD::d0 : 1], u1[RD::d1 > 0 ? RD::d1 : 1], u2[RD::d2 > 0 ? RD::d2 : 1],
       u3[RD::d3 > 0 ? RD::d3 : 1];
-  const size_t base = red_base(K, RD::Q);
-  sym_block<RD::d0, T>(R, RD::q0, base, t0, u0);
-  sym_block<RD::d1, T>(R, RD::q1, base, t1, u1);
-  sym_block<RD::d2, T>(R, RD::q2, base, t2, u2);
-  sym_block<RD::d3, T>(R, RD::q3, base, t3, u3);
+  if (kVec) {
+    sym_block_reg<RD::d0, T>(bq + RD::q0, t0, u0);
+    sym_block_reg<RD::d1, T>(bq + RD::q1, t1, u1);
+    sym_block_reg<RD::d2, T>(bq + RD::q2, t2, u2);
+    sym_block_reg<RD::d3, T>(bq + RD::q3, t3, u3);
+  } else {
+    const size_t base = red_base(K, RD::Q);
+    sym_block<RD::d0, T>(R, RD::q0, base, t0, u0);
+    sym_block<RD::d1, T>(R, RD::q1, base, t1, u1);
+    sym_block<RD::d2, T>(R, RD::q2, base, t2, u2);
+    sym_block<RD::d3, T>(R, RD::q3, base, t3, u3);
+  }
   // back to face dofs: z = F^T u
   T Po[N1], Mo[N1], Ppo[N1], Mpo[N1];
   {
