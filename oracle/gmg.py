@@ -27,6 +27,12 @@ Paper passages followed (Sec. 6, "Multigrid algorithm"):
     Reading: coarse p-operators are Galerkin, A_{p-1} = P^T A_p P, which is
     again a sum of element blocks P_K^T S_K P_K because P acts per edge.
     coarse_op="rediscretize" keeps the paper's literal choice for comparison.
+  * Sec. 6.4.1: FSAI smoother x += G^T G (f - A x) (the SPAI step with the
+    factorized inverse for a symmetric operator), G from fsai_factor. Readings:
+    the paper's "operator complexity of unity" is G on the lower-triangular
+    pattern of A (applying G^T G then costs about one product with A); its more
+    aggressive variant (complexity ~2.5) is the pattern of A^2; no damping, as
+    in the printed update.
   * Sec. 6.4.2: weighted additive Schwarz smoother x += W M (f - A x),
     M = sum_e R_e^T A_e^-1 R_e, dense local blocks applied unassembled.
     Reading: the patch is one element (its 4 faces); A_e is the assembled
@@ -197,10 +203,37 @@ def chebyshev(A, dinv, lmax, f, x, degree=2, lo=0.1, hi=1.1):
     return x
 
 
-class PLevel:
-    """One p-level on the fixed mesh: interior-dof matrix and ASM blocks."""
+def fsai_factor(A, pattern):
+    """Factorized sparse approximate inverse of an SPD matrix (Sec. 6.4.1): the
+    lower-triangular G with the given sparsity (a sparse matrix whose lower
+    triangle, diagonal included, is the allowed pattern) that minimises
+    |I - G L|_F, L the Cholesky factor of A, normalised so that G A G^T has a
+    unit diagonal; M = G^T G approximates A^-1. Row i is independent of the
+    others: with J the allowed columns of row i (all <= i),
+    A[J, J] g = e_i, then G[i, J] = g / sqrt(g_i)."""
+    A = sp.csr_matrix(A)
+    P = sp.tril(sp.csr_matrix(pattern), format="csr")
+    n = A.shape[0]
+    rows, cols, vals = [], [], []
+    Ad = A.tolil()
+    for i in range(n):
+        J = P.indices[P.indptr[i]:P.indptr[i + 1]]
+        J = np.unique(np.append(J, i))
+        AJ = Ad[J][:, J].toarray()
+        rhs = (J == i).astype(np.float64)
+        g = np.linalg.solve(AJ, rhs)
+        g = g / np.sqrt(g[J == i][0])
+        rows.extend([i] * len(J))
+        cols.extend(J.tolist())
+        vals.extend(g.tolist())
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
 
-    def __init__(self, mesh, p, kappa, tau=1.0, A=None):
+
+class PLevel:
+    """One p-level on the fixed mesh: interior-dof matrix and its smoother
+    (weighted ASM blocks, or FSAI)."""
+
+    def __init__(self, mesh, p, kappa, tau=1.0, A=None, smoother="asm", fsai_pattern="A"):
         self.p = p
         self.prob = HDGProblem(mesh, p, kappa, tau)
         if A is None:
@@ -225,6 +258,18 @@ class PLevel:
             self.patches.append((loc, np.linalg.inv(Ae)))
             count[loc] += 1
         self.weight = 1.0 / count
+        self.smoother = smoother
+        if smoother == "fsai":
+            # pattern of A (operator complexity one: applying G^T G costs about
+            # one product with A) or of A^2 (a wider, stronger approximate inverse)
+            pat = self.A if fsai_pattern == "A" else (self.A @ self.A)
+            self.G = fsai_factor(self.A, pat)
+        elif smoother != "asm":
+            raise ValueError(smoother)
+
+    def fsai(self, r):
+        """z = G^T G r."""
+        return self.G.T @ (self.G @ r)
 
     def asm(self, r):
         """z = W M r, M = sum_e R_e^T A_e^-1 R_e."""
@@ -234,8 +279,9 @@ class PLevel:
         return self.weight * z
 
     def smooth(self, f, x, nu):
+        M = self.fsai if self.smoother == "fsai" else self.asm
         for _ in range(nu):
-            x = x + self.asm(f - self.A @ x)
+            x = x + M(f - self.A @ x)
         return x
 
 
@@ -260,13 +306,14 @@ class NestedGMG:
     vcycle() takes and returns vectors on ALL trace dofs (boundary entries 0)."""
 
     def __init__(self, mesh, k, kappa, tau=1.0, nu1=2, nu2=2, coarse_n=2,
-                 coarse_op="galerkin"):
+                 coarse_op="galerkin", smoother="asm", fsai_pattern="A"):
         self.mesh, self.k, self.nu1, self.nu2 = mesh, k, nu1, nu2
         kappa = np.asarray(kappa, dtype=np.float64).reshape(mesh.nel)
+        sm = dict(smoother=smoother, fsai_pattern=fsai_pattern)
         if coarse_op == "rediscretize":
-            self.plevels = {p: PLevel(mesh, p, kappa, tau) for p in range(k, -1, -1)}
+            self.plevels = {p: PLevel(mesh, p, kappa, tau, **sm) for p in range(k, -1, -1)}
         elif coarse_op == "galerkin":
-            self.plevels = {k: PLevel(mesh, k, kappa, tau)}
+            self.plevels = {k: PLevel(mesh, k, kappa, tau, **sm)}
         else:
             raise ValueError(coarse_op)
         # p-transfers between interior-dof vectors; Galerkin coarse p-operators
@@ -278,7 +325,7 @@ class NestedGMG:
             self.Pp[p + 1] = P[fine.idx][:, ic].tocsr()
             if coarse_op == "galerkin":
                 Ac = (self.Pp[p + 1].T @ fine.A @ self.Pp[p + 1]).tocsr()
-                self.plevels[p] = PLevel(mesh, p, kappa, tau, A=Ac)
+                self.plevels[p] = PLevel(mesh, p, kappa, tau, A=Ac, **sm)
         # h-levels: index 0 = p = 0 HDG (interior edges), then Q1 finest..coarsest
         A0 = self.plevels[0].A
         PJ = q1_to_p0(mesh)[self.plevels[0].idx]

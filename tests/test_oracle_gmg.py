@@ -145,6 +145,72 @@ def test_convergence_factor_paper(k, bound):
     assert gmg.convergence_factor(hist) < bound
 
 
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    B = rng.normal(size=(n, n))
+    return B @ B.T + n * np.eye(n)
+
+
+def test_fsai_full_pattern_is_exact_inverse():
+    """With every lower-triangular entry allowed, the factorized approximate
+    inverse is exact: G = L^-1 for A = L L^T, so G^T G = A^-1."""
+    A = _spd(12, 1)
+    G = gmg.fsai_factor(A, np.tril(np.ones((12, 12)))).toarray()
+    assert np.abs(G.T @ G - np.linalg.inv(A)).max() < 1e-12 * np.abs(np.linalg.inv(A)).max()
+    assert np.abs(np.triu(G, 1)).max() == 0.0
+
+
+def test_fsai_diagonal_pattern_is_jacobi():
+    A = _spd(9, 2)
+    G = gmg.fsai_factor(A, np.eye(9)).toarray()
+    assert np.allclose(G, np.diag(1.0 / np.sqrt(np.diag(A))), rtol=1e-14, atol=0)
+
+
+def test_fsai_rows_optimal_and_normalised():
+    """For a banded pattern: G A G^T has a unit diagonal, and each row's
+    Frobenius-optimality condition holds, (G A)[i, j] = 0 for the allowed
+    j != i (the residual of row i is orthogonal to its pattern)."""
+    n = 15
+    A = _spd(n, 3)
+    pat = np.tril(np.triu(np.ones((n, n)), -3))
+    G = gmg.fsai_factor(A, pat).toarray()
+    assert np.abs(np.diag(G @ A @ G.T) - 1.0).max() < 1e-12
+    GA = G @ A
+    for i in range(n):
+        for j in range(max(0, i - 3), i):
+            assert abs(GA[i, j]) < 1e-12 * np.abs(GA[i]).max()
+    assert np.all(G[pat == 0] == 0.0)
+
+
+def test_fsai_vcycle_symmetric_positive():
+    m = omesh.Mesh(8, 8)
+    G = gmg.NestedGMG(m, 2, np.exp(np.random.default_rng(4).normal(size=m.nel)), smoother="fsai")
+    rng = np.random.default_rng(5)
+    top = G.plevels[2]
+    r = np.zeros(top.ndof)
+    s = np.zeros(top.ndof)
+    r[top.idx] = rng.normal(size=len(top.idx))
+    s[top.idx] = rng.normal(size=len(top.idx))
+    Vr, Vs = G.vcycle(r), G.vcycle(s)
+    assert abs(s @ Vr - r @ Vs) < 1e-11 * abs(s @ Vr)
+    assert r @ Vr > 0
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_fsai_convergence_factor_paper(k):
+    """Sec. 7 with the paper's smoother: V(2,2) with FSAI of operator complexity
+    one (pattern of A) as a stationary solver on 32 x 32, K = 1: every factor
+    is below the paper's 0.22 (it reports 0.13-0.15 for even p); measured here
+    0.157 / 0.112 / 0.109 for p = 2 / 3 / 4 with Galerkin coarse p-operators."""
+    m = omesh.Mesh(32, 32)
+    G = gmg.NestedGMG(m, k, np.ones(m.nel), smoother="fsai")
+    top = G.plevels[k]
+    b = np.zeros(top.ndof)
+    b[top.idx] = np.random.default_rng(0).normal(size=len(top.idx))
+    _, hist = G.stationary(b, 9)
+    assert gmg.convergence_factor(hist) < 0.22
+
+
 def test_rediscretized_coarse_ops_diverge_at_k1():
     """Documents the reading on coarse p-operators: the literal rediscretised
     p = 0 level (tau = 1) makes the k = 1 V-cycle diverge on a 16 x 16 mesh."""
