@@ -176,9 +176,14 @@ int hdg_condense_rhs(void* ctx, const double* f_q, double* b, int nrhs, void* st
  * interior edge, y = 0 on boundary edges. Each face is written once, by one
  * thread, with no atomics. x, y: device [ndof][nrhs] in the type `prec`
  * selects (double for FP64 and F32X2, float for FP32 and BF16); x and y must
- * not overlap. With nrhs > 1 each CTA stages one segment's blocks in shared
- * memory once and applies them to all columns (lanes over right-hand sides). Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED
- * (FP32/BF16/F32X2 when the context was built with mixed = 0).
+ * not overlap. Kernels: with `reduced` (default) the symmetry-reduced blocks
+ * (one vector: element pass + face pass; nrhs > 1 with double vectors: the
+ * column form of the same, bitwise equal per column, whose scratch belongs to
+ * the batched work of that nrhs, allocated by the first call with it); else,
+ * and for float columns, the dense owner records (nrhs > 1: each CTA stages one
+ * segment's blocks in shared memory once and applies them to all columns).
+ * Errors: INVALID_ARG (nrhs < 1, null pointers), UNSUPPORTED (FP32/BF16/F32X2
+ * when the context was built with mixed = 0), OOM (batched work).
  */
 int hdg_apply_trace(void* ctx, const void* x, void* y, int nrhs, int prec, void* stream);
 
@@ -196,10 +201,13 @@ int hdg_setup_batch(int n, const hdg_mesh* meshes, const int* k, const double* c
 
 /*
  * The trace apply of Alg. 3 for n independent meshes (1 <= n <= 16 contexts,
- * uneven sizes, degrees 0..5) in ONE kernel launch: the record segments of all
- * meshes form a single work list (one CTA per entry, each on its mesh's degree),
- * so small meshes do not leave SMs idle behind large ones and the batch costs one
- * launch. y[q] = A_q x[q] for each q, same layouts and boundary rules
+ * uneven sizes, degrees 0..5) as one batch: the work of all meshes forms a
+ * single list (each CTA serves one mesh, on its degree), so small meshes do not
+ * leave SMs idle behind large ones. When every context has `reduced` = 1 the
+ * batch is the element pass and the face pass of the reduced apply, one launch
+ * each for all meshes (each result bitwise equal to the mesh's own apply);
+ * otherwise one launch over all record segments of the dense owner records.
+ * y[q] = A_q x[q] for each q, same layouts and boundary rules
  * as hdg_apply_trace (nrhs = 1). prec: HDG_PREC_FP64 (double vectors) or
  * HDG_PREC_FP32 (float vectors). All contexts must belong to the current device.
  * Errors: INVALID_ARG (count, pointers, degree, device), UNSUPPORTED (FP32 when a
