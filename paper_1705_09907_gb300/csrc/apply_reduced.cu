@@ -35,7 +35,9 @@
 //      column); the faces on tile edges go through a small second launch.
 // The blocks are read once, directly from HBM with coalesced streaming loads
 // (warp chunks [nel/32][Q][32]: the 32 lanes of a warp read 32 consecutive
-// elements' entry q, and a warp's Q entries are one contiguous chunk).
+// elements' entry q, and a warp's Q entries are one contiguous chunk; the FP32
+// copy keeps four entries of an element together, [nel/32][Q/4][32][4], and is
+// read as float4 before any arithmetic).
 #include "reduced_impl.cuh"
 
 namespace hdg {
