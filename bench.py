@@ -133,6 +133,22 @@ def cpu_baseline_worker(n_sub, N, k, seed, reps):
     print(json.dumps({"times": times, "nel": nel, "extras": extras}))
 
 
+def host_cpu():
+    """The host's core count and CPU model (the oracle baseline runs there)."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_count": os.cpu_count(), "model": model or platform.machine()}
+
+
 def run_cpu_baseline(N, k, n_sub=48, reps=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, "-c",
@@ -149,7 +165,7 @@ def run_cpu_baseline(N, k, n_sub=48, reps=1):
         "sample": "%dx%d sub-mesh of the %dx%d k=%d lognormal workload (same h and kappa), oracle condense + "
                   "scipy SuperLU direct solve + recovery, %.2f s, scaled linearly by element count"
                   % (n_sub, n_sub, N, N, k, t),
-        "sample_seconds": t,
+        "sample_seconds": t, "host": host_cpu(),
     }
     ex = out.get("extras", {})
     if "csr_matvec_s" in ex:
@@ -644,7 +660,7 @@ def run_reference(args):
         "config": {"workload": "hdg_trace_gmg_pcg", "mesh": "%dx%d" % (N, N), "k": k},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "value": value, "unit": "solve/s",
                          "sample": "%dx%d sub-mesh per step (same h, kappa), oracle condense + SuperLU + recovery, "
-                                   "scaled linearly by element count" % (n_sub, n_sub)},
+                                   "scaled linearly by element count" % (n_sub, n_sub), "host": host_cpu()},
         "e2e": {"value": value, "unit": "solve/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
