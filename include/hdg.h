@@ -31,6 +31,15 @@
  *  - Every call returns an hdg_status. On an error nothing is written to the
  *    outputs that later calls depend on; the context stays usable unless the
  *    status is HDG_ERR_CUDA (a sticky CUDA error).
+ *  - A context holds work vectors, scratch and captured V-cycle graphs that its
+ *    calls reuse: calls on one context must not run concurrently (issue them
+ *    from one thread, or on one stream in order). Different contexts are
+ *    independent.
+ *  - The FP32 / BF16 / F32X2 precisions below describe the blocks a call
+ *    reads. With `hdg_options.reduced` (default) the condensed blocks are read
+ *    in their symmetry-reduced form: FP64 and F32X2 calls use the FP64 reduced
+ *    blocks, FP32 and BF16 calls the FP32 reduced blocks; the Schwarz blocks of
+ *    the V-cycle are always read in the precision named.
  */
 #ifndef HDG_H
 #define HDG_H
