@@ -81,6 +81,57 @@ def test_schur_reflection_symmetry(p):
                 assert np.abs(S[np.ix_(swap, swap)] - S).max() > 1e-3 * scale
 
 
+def _character_coordinates(n):
+    """Rows of the transform F on face dofs [W|E|S|N] (n nodes per face): face
+    sums / differences of the W/E and S/N pairs, then node-pair sums (even
+    part, with the middle node) / differences (odd part), grouped by the
+    character (sigma_x, sigma_y) = (+,+), (+,-), (-,+), (-,-)."""
+    h = n // 2
+    I = np.eye(n)
+    ev = [I[i] + I[n - 1 - i] for i in range(h)] + ([I[h]] if n % 2 else [])
+    od = [I[i] - I[n - 1 - i] for i in range(h)]
+    Z = np.zeros(n)
+    P = lambda v: np.concatenate([v, v, Z, Z])
+    M = lambda v: np.concatenate([v, -v, Z, Z])
+    Pp = lambda v: np.concatenate([Z, Z, v, v])
+    Mp = lambda v: np.concatenate([Z, Z, v, -v])
+    return [np.array([P(v) for v in ev] + [Pp(v) for v in ev]),
+            np.array([P(v) for v in od] + [Mp(v) for v in ev]),
+            np.array([M(v) for v in ev] + [Pp(v) for v in od]),
+            np.array([M(v) for v in od] + [Mp(v) for v in od])]
+
+
+@pytest.mark.parametrize("p", range(0, 8))
+def test_schur_character_blocks(p):
+    """Consequence of the reflection symmetry used by the reduced storage: in
+    the character coordinates t = F x the element block is block diagonal,
+    F S_K F^T = diag(B0, B1, B2, B3) of sizes 2s, a+s, s+a, 2a (s = ceil(n/2),
+    a = floor(n/2), n = p+1), and S_K = F^T D^-1 B D^-1 F with D = F F^T
+    diagonal; the packed triangles hold sum d(d+1)/2 numbers (61 at p = 4)."""
+    n = p + 1
+    rng = np.random.default_rng(60 + p)
+    blocks = [b for b in _character_coordinates(n) if len(b)]
+    F = np.vstack(blocks)
+    D = F @ F.T
+    assert np.abs(D - np.diag(np.diag(D))).max() == 0.0
+    sizes = [len(b) for b in _character_coordinates(n)]
+    s_, a_ = (n + 1) // 2, n // 2
+    assert sizes == [2 * s_, a_ + s_, s_ + a_, 2 * a_]
+    packed = sum(d * (d + 1) // 2 for d in sizes)
+    assert packed == {0: 5, 1: 12, 2: 25, 3: 40, 4: 61, 5: 84, 6: 113, 7: 144}[p]
+    for hx, hy in ((0.1, 0.1), (0.3, 0.07)):
+        S = hdg.schur_block(hdg.element_matrices(hdg.RefElement(p, hx, hy), float(np.exp(rng.normal())), 1.0))
+        B = F @ S @ F.T
+        off = np.cumsum([0] + [len(b) for b in blocks])
+        mask = np.zeros_like(B, dtype=bool)
+        for q in range(len(blocks)):
+            mask[off[q]:off[q + 1], off[q]:off[q + 1]] = True
+        scale = np.abs(B).max()
+        assert np.abs(B[~mask]).max(initial=0.0) < 1e-13 * scale
+        Dinv = np.diag(1.0 / np.diag(D))
+        assert np.abs(F.T @ (Dinv @ np.where(mask, B, 0.0) @ Dinv) @ F - S).max() < 1e-13 * np.abs(S).max()
+
+
 @pytest.mark.parametrize("p", range(0, 6))
 def test_tau_kappa_scaling(p):
     """With tau_K = kappa_K every local equation is kappa_K times the kappa = 1,
