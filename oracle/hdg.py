@@ -20,7 +20,8 @@ Layouts (shared only as a specification with the GPU library):
   volume unknowns per element: Q = [Qx (n), Qy (n)], U (n); n = (p+1)^2, nodal
   at the GLL tensor grid, index I = i + j (p+1) (i along x).
   trace unknowns per element: Lambda = [W, E, S, N] faces x (p+1) GL nodes.
-  f input: samples at the (p+2) x (p+2) GL points of each element,
+  f input: samples at the (p+2) x (p+2) GL points of each element (any nq x nq
+  GL tensor grid is accepted; Table 1 of Sec. 5 uses nq = p + 1),
   f_q[e, jy, ix] (x fastest).
 """
 import numpy as np
@@ -197,20 +198,28 @@ def local_solve(mats, lam_K, F):
 
 
 def load_vector(ref, mats, f_q_e):
-    """F_K[i] = (f, phi_i)_K from samples at the (p+2)^2 GL points."""
-    # the load uses the (p+2)-point GL rule of the samples, whatever ref.nq is
-    xq, wq = qd.gauss_legendre(ref.p + 2)
+    """F_K[i] = (f, phi_i)_K from samples at the nq x nq GL points of the element
+    (x fastest), nq read from the sample count: (p+2)^2 samples are the library's
+    input format; (p+1)^2 samples give the (p+1)-point rule with which the paper's
+    Table 1 was computed (Sec. 5)."""
+    f_q_e = np.asarray(f_q_e).ravel()
+    nq = int(round(np.sqrt(f_q_e.size)))
+    if nq * nq != f_q_e.size:
+        raise ValueError("f samples must form an nq x nq tensor grid")
+    xq, wq = qd.gauss_legendre(nq)
     B1 = qd.lagrange_matrix(ref.vnodes, xq)
     V = np.kron(B1, B1)
     wJ = np.kron(wq, wq) * ref.hx * ref.hy / 4.0
-    return V.T @ (wJ * np.asarray(f_q_e).ravel())
+    return V.T @ (wJ * f_q_e)
 
 
-def f_quadrature_points(mesh, p):
-    """Physical coordinates of the (p+2)^2 GL sample points of every element:
-    X, Y with shape [nel, p+2, p+2] (index [e, jy, ix])."""
-    xq, _ = qd.gauss_legendre(p + 2)
-    X = np.zeros((mesh.nel, p + 2, p + 2))
+def f_quadrature_points(mesh, p, npts=None):
+    """Physical coordinates of the npts x npts GL sample points of every element
+    (npts = p + 2 by default, the library's input format): X, Y with shape
+    [nel, npts, npts] (index [e, jy, ix])."""
+    nq = p + 2 if npts is None else int(npts)
+    xq, _ = qd.gauss_legendre(nq)
+    X = np.zeros((mesh.nel, nq, nq))
     Y = np.zeros_like(X)
     for e in range(mesh.nel):
         ox, oy = mesh.elem_origin(e)
@@ -413,8 +422,10 @@ def uncondensed_solve(mesh, p, kappa, f_q, tau=1.0):
     return lam, u, q
 
 
-def l2_errors(prob, u, q, u_exact, q_exact, nquad=None):
-    """L2 norms of u_h - u and q_h - q by (p+4)-point GL quadrature per element."""
+def l2_errors(prob, u, q, u_exact, q_exact, nquad=None, components=False):
+    """L2 norms of u_h - u and q_h - q by nquad-point GL quadrature per element
+    (p+4 points by default; Table 1 of Sec. 5 is reproduced with p+1 points).
+    With components=True returns (|u_h - u|, |q_h,x - q_x|, |q_h,y - q_y|)."""
     ref = prob.ref
     nq = ref.p + 4 if nquad is None else nquad
     xq, wq = qd.gauss_legendre(nq)
@@ -422,7 +433,8 @@ def l2_errors(prob, u, q, u_exact, q_exact, nquad=None):
     V = np.kron(B1, B1)
     wJ = np.kron(wq, wq) * prob.mesh.hx * prob.mesh.hy / 4.0
     eu = 0.0
-    eq = 0.0
+    eqx = 0.0
+    eqy = 0.0
     for e in range(prob.mesh.nel):
         ox, oy = prob.mesh.elem_origin(e)
         X, Y = np.meshgrid(ox + prob.mesh.hx * (xq + 1) / 2, oy + prob.mesh.hy * (xq + 1) / 2)
@@ -430,5 +442,8 @@ def l2_errors(prob, u, q, u_exact, q_exact, nquad=None):
         uh = V @ u[e]
         eu += np.sum(wJ * (uh - u_exact(X, Y)) ** 2)
         qx, qy = q_exact(X, Y)
-        eq += np.sum(wJ * ((V @ q[e, 0] - qx) ** 2 + (V @ q[e, 1] - qy) ** 2))
-    return np.sqrt(eu), np.sqrt(eq)
+        eqx += np.sum(wJ * (V @ q[e, 0] - qx) ** 2)
+        eqy += np.sum(wJ * (V @ q[e, 1] - qy) ** 2)
+    if components:
+        return np.sqrt(eu), np.sqrt(eqx), np.sqrt(eqy)
+    return np.sqrt(eu), np.sqrt(eqx + eqy)

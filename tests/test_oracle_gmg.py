@@ -70,6 +70,46 @@ def test_q1_stiffness_closed_form():
     assert abs(A[0, 0] - kap.sum() * (2 / 6) * (hy / hx + hx / hy)) < 1e-14
 
 
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(6, 6, 1.0, 1.0), (5, 4, 1.0, 0.5)])
+def test_q1_stiffness_full_stencil(nx, ny, Lx, Ly):
+    """Every entry of the Q1 stiffness (kappa grad u, grad v) against the closed
+    form of the bilinear element on hx x hy (a = hy/hx, b = hx/hy): per element,
+    its own vertex (a + b)/3, the vertex across an x-edge (b - 2a)/6, across a
+    y-edge (a - 2b)/6, the opposite corner -(a + b)/6; on squares with kappa = 1
+    this is the 9-point stencil (8, -1 x 8)/3 with zero sums on rows away from
+    the boundary."""
+    m = omesh.Mesh(nx, ny, 0, 0, Lx, Ly)
+    rng = np.random.default_rng(11)
+    kap = rng.uniform(0.5, 3.0, m.nel)
+    A = gmg.q1_stiffness(m, kap).toarray()
+    a, b = m.hy / m.hx, m.hx / m.hy
+    own, xn, yn, cor = (a + b) / 3, (b - 2 * a) / 6, (a - 2 * b) / 6, -(a + b) / 6
+    vid = lambda i, j: (i - 1) + (nx - 1) * (j - 1)
+    ref = np.zeros_like(A)
+    for j in range(1, ny):
+        for i in range(1, nx):
+            r = vid(i, j)
+            for ei in (i - 1, i):
+                for ej in (j - 1, j):
+                    k = kap[ei + nx * ej]
+                    ref[r, r] += own * k
+                    # the element's other vertices: across its x-edge, y-edge, corner
+                    xi = i - 1 if ei == i - 1 else i + 1
+                    yj = j - 1 if ej == j - 1 else j + 1
+                    for (ii, jj, v) in ((xi, j, xn), (i, yj, yn), (xi, yj, cor)):
+                        if 1 <= ii < nx and 1 <= jj < ny:
+                            ref[r, vid(ii, jj)] += v * k
+    assert np.abs(A - ref).max() < 1e-13 * np.abs(ref).max()
+    if nx == ny and Lx == Ly:
+        A1 = gmg.q1_stiffness(m, np.ones(m.nel)).toarray()
+        r = vid(3, 3)
+        row = A1[r].reshape(ny - 1, nx - 1)
+        assert np.allclose(row[1:4, 1:4], np.array([[-1, -1, -1], [-1, 8, -1], [-1, -1, -1]]) / 3, atol=1e-14)
+        for j in range(2, ny - 1):
+            for i in range(2, nx - 1):
+                assert abs(A1[vid(i, j)].sum()) < 1e-14
+
+
 def test_chebyshev_is_scaled_chebyshev_polynomial():
     """On a diagonal matrix the degree-2 step maps e0 -> T2((theta - l)/delta) /
     T2(theta/delta) e0 at every eigenvalue l (Jacobi scaling trivial)."""

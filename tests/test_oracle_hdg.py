@@ -270,38 +270,87 @@ def _load_tab1():
     return rows
 
 
-@pytest.mark.parametrize("p", [3, 4])
-def test_table1_rates_and_magnitudes(p):
-    """Sec. 5 Table 1: K = tanh(x+y)+1 (varying inside elements, evaluated at
-    quadrature points), tau = 1. The rates of u_h match the table within 0.25
-    where the error is above 1e-12; the u_h and q_h errors are within a factor
-    of 3 and 6 of the printed values (the printed constants are smaller than this
-    discretisation gives; the paper does not state enough to close the gap)."""
+def _table1_exact(K_is_one):
     sy = pytest.importorskip("sympy")
     x, y = sy.symbols("x y")
-    K = sy.tanh(x + y) + 1
+    K = sy.Integer(1) if K_is_one else sy.tanh(x + y) + 1
     u = x * (x - 1) * y * (y - 1) * sy.exp(-x ** 2 - y ** 2)
     f = -(sy.diff(K * sy.diff(u, x), x) + sy.diff(K * sy.diff(u, y), y))
-    fl, ul, Kl = (sy.lambdify((x, y), e, "numpy") for e in (f, u, K))
-    qxl = sy.lambdify((x, y), -K * sy.diff(u, x), "numpy")
-    qyl = sy.lambdify((x, y), -K * sy.diff(u, y), "numpy")
+    lam = lambda e: sy.lambdify((x, y), e, "numpy")
+    fl, ul, Kl = lam(f), lam(u), lam(K + 0 * x)
+    qxl, qyl = lam(-K * sy.diff(u, x)), lam(-K * sy.diff(u, y))
+    return fl, ul, (lambda a, b: Kl(a, b) * np.ones_like(a)), (lambda a, b: (qxl(a, b), qyl(a, b)))
+
+
+@pytest.mark.parametrize("p", [3, 4, 5, 6])
+def test_table1_reproduced(p):
+    """Sec. 5 Table 1, the |u_h - u| and |q_h - q| columns, reproduced to the
+    printed three digits. Reading (DESIGN, reading 16): the table is the model
+    Poisson problem of Sec. 5 (K = 1, tau = 1; the text's tanh coefficient does
+    not give these constants), u = x(x-1)y(y-1)exp(-x^2-y^2), with the load and
+    the error norms integrated by the (p+1)-point Gauss-Legendre rule per
+    direction, and the flux error of one component (|q_x - q_hx| = |q_y - q_hy|
+    by the x <-> y symmetry of u). Entries below 1e-12 sit on the table's
+    rounding floor (the N = 32 rows grow again) and are skipped."""
+    fl, ul, _, qe = _table1_exact(True)
     table = {(pp, N): (a, b) for pp, N, a, b in _load_tab1() if pp == p}
-    Ns = (2, 4, 8, 16)
+    for N in (2, 4, 8, 16):
+        m = omesh.Mesh(N, N)
+        X, Y = hdg.f_quadrature_points(m, p, npts=p + 1)
+        prob = hdg.HDGProblem(m, p, np.ones(m.nel))
+        fq = fl(X, Y)
+        lam = prob.solve_direct(prob.condense_rhs(fq))
+        uu, qq = prob.recover(lam, fq)
+        eu, eqx, eqy = hdg.l2_errors(prob, uu, qq, ul, qe, nquad=p + 1, components=True)
+        assert abs(eqx - eqy) <= 1e-4 * eqx
+        tu, tq = table[(p, N)]
+        if tu > 1e-12:
+            assert abs(eu / tu - 1.0) < 0.01, (p, N, eu, tu)
+        if tq > 1e-12:
+            assert abs(eqx / tq - 1.0) < 0.01, (p, N, eqx, tq)
+
+
+def test_table1_sensitive_to_its_reading():
+    """The Table 1 match is not loose: the default (p+4)-point error rule, the
+    norm of the whole flux, or the (p+2)-point load each move an entry by more
+    than the 1% band (p = 3, N = 8: 1.057, 1.551, 1.002 -> checked > 1.04 etc.)."""
+    p, N = 3, 8
+    fl, ul, _, qe = _table1_exact(True)
+    tu, tq = {(pp, n): (a, b) for pp, n, a, b in _load_tab1()}[(p, N)]
+    m = omesh.Mesh(N, N)
+    prob = hdg.HDGProblem(m, p, np.ones(m.nel))
+    X, Y = hdg.f_quadrature_points(m, p, npts=p + 1)
+    fq = fl(X, Y)
+    uu, qq = prob.recover(prob.solve_direct(prob.condense_rhs(fq)), fq)
+    eu, eq = hdg.l2_errors(prob, uu, qq, ul, qe)
+    assert eu / tu > 1.04 and eq / tq > 1.5
+    eu, eq = hdg.l2_errors(prob, uu, qq, ul, qe, nquad=p + 1)
+    assert abs(eu / tu - 1) < 0.01 and eq / tq > 1.4
+    # a load vector off by a factor 2 moves u_h by a factor 2
+    uu2, qq2 = prob.recover(prob.solve_direct(prob.condense_rhs(2 * fq)), 2 * fq)
+    eu2, _, _ = hdg.l2_errors(prob, uu2, qq2, ul, qe, nquad=p + 1, components=True)
+    assert eu2 / tu > 10
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_table1_text_coefficient_rates(p):
+    """The coefficient named in the text of Sec. 5, K = tanh(x+y)+1 (evaluated at
+    the quadrature points), gives the same p+1 rates for u_h and q_h as Table 1
+    (within 0.25, N = 4 -> 8 -> 16), with larger constants."""
+    fl, ul, Kl, qe = _table1_exact(False)
+    table = {(pp, N): (a, b) for pp, N, a, b in _load_tab1() if pp == p}
+    Ns = (4, 8, 16)
     ours = {}
     for N in Ns:
         m = omesh.Mesh(N, N)
         X, Y = hdg.f_quadrature_points(m, p)
         xc, yc = m.elem_centres()
-        prob = hdg.HDGProblem(m, p, Kl(xc, yc), kappa_q_fn=lambda a, b: Kl(a, b), nquad=p + 4)
+        prob = hdg.HDGProblem(m, p, Kl(xc, yc), kappa_q_fn=Kl, nquad=p + 4)
         fq = fl(X, Y)
-        lam = prob.solve_direct(prob.condense_rhs(fq))
-        uu, qq = prob.recover(lam, fq)
-        ours[N] = hdg.l2_errors(prob, uu, qq, ul, lambda a, b: (qxl(a, b), qyl(a, b)))
-    for N in Ns:
-        tu, tq = table[(p, N)]
-        assert tu / 3 < ours[N][0] < tu * 3
-        assert tq / 6 < ours[N][1] < tq * 6
-    for N0, N1 in zip(Ns[1:-1], Ns[2:]):
-        rate_t = np.log2(table[(p, N0)][0] / table[(p, N1)][0])
-        rate_o = np.log2(ours[N0][0] / ours[N1][0])
-        assert abs(rate_t - rate_o) < 0.25
+        uu, qq = prob.recover(prob.solve_direct(prob.condense_rhs(fq)), fq)
+        ours[N] = hdg.l2_errors(prob, uu, qq, ul, qe)
+    for N0, N1 in zip(Ns[:-1], Ns[1:]):
+        for c in (0, 1):
+            rate_t = np.log2(table[(p, N0)][c] / table[(p, N1)][c])
+            rate_o = np.log2(ours[N0][c] / ours[N1][c])
+            assert abs(rate_t - rate_o) < 0.25
