@@ -113,6 +113,21 @@ typedef struct {
                                  scales with kappa_K, S_K = kappa_K S_ref and
                                  the condensed right-hand side does not depend
                                  on kappa; 0: tau = `tau` everywhere (0)     */
+  size_t max_device_bytes;    /* cap on the device memory the context keeps
+                                 (set-up data and work vectors; 0 = no cap):
+                                 an allocation that would pass it fails with
+                                 HDG_ERR_OOM as if the device were full (0)   */
+  int wait_probe;             /* test of the bounded-wait path (0 = off): the
+                                 first `wait_probe` launches after set-up of
+                                 the one-CTA-per-segment apply kernel (see
+                                 `autotune`) make their first CTA wait, with
+                                 the usual ~1 s bound, on a barrier nothing
+                                 completes; it gives up, raises the context's
+                                 error flag, drains its own block copy and
+                                 exits, so the call that reads the flag
+                                 (hdg_solve, hdg_adjoint_grad) returns
+                                 HDG_ERR_TIMEOUT; later calls run normally.
+                                 0 <= wait_probe <= 64                        */
 } hdg_options;
 
 typedef struct {
@@ -269,7 +284,9 @@ int hdg_gmg_vcycle(void* ctx, const void* r, void* z, int nrhs, int prec, void* 
  * ~48-bit products) and CG uses the flexible Polak-Ribiere beta, since a
  * low-precision V-cycle is not exactly symmetric. info (host, may be NULL) receives the
  * iteration count and residual history. Errors: NOT_CONVERGED (lambda holds
- * the last iterate), BREAKDOWN, TIMEOUT, CUDA.
+ * the last iterate), BREAKDOWN, TIMEOUT (a bounded device wait gave up during
+ * the solve; reported in preference to NOT_CONVERGED or BREAKDOWN, which it
+ * may have caused), CUDA.
  */
 int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol, int maxit,
               int inner, hdg_solve_info* info, void* stream);
@@ -281,6 +298,19 @@ int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol,
  */
 int hdg_recover_local(void* ctx, const double* lambda, const double* f_q, double* u, double* q,
                       void* stream);
+
+/*
+ * Element-local postprocessing (Sec. 3 step (v); the local filter of the LDG-H
+ * analysis the paper cites, Sec. 5 and Table 1): on each element K, u* in
+ * Q_{k+1}(K) solves the Neumann problem (kappa grad u*, grad w)_K =
+ * -(q_h, grad w)_K for all w in Q_{k+1}(K) with the element mean of u_h, and
+ * q* = -kappa grad u*. u*, q* converge at rates k+2 and k+1 (Table 1).
+ * u [nel][(k+1)^2], q [nel][2][(k+1)^2]: device inputs in the layout of
+ * hdg_recover_local. ustar [nel][(k+2)^2], qstar [nel][2][(k+2)^2]: device
+ * outputs, values at the (k+2)^2 tensor Gauss-Lobatto nodes of each element
+ * (index i + (k+2)*j, i along x); either may be NULL. Errors: INVALID_ARG.
+ */
+int hdg_postprocess(void* ctx, const double* u, const double* q, double* ustar, double* qstar, void* stream);
 
 /*
  * Adjoint gradient of J = 1/2 |lambda - lambda_obs|_2^2 (interior dofs) where
@@ -305,13 +335,16 @@ int hdg_adjoint_grad(void* ctx, const double* f_q, const double* lambda, const d
  * Same arguments, layout and result as hdg_condense_rhs. Its per-element
  * scratch is a fixed array of 2^19 doubles (4 MiB) inside the library, held
  * by every GPU that loads the library until the process exits; contexts
- * with nel * 4(k+1) > 2^19 are rejected with HDG_ERR_INVALID_ARG. The first
- * call on a device looks up that array's device address (a host-side step);
- * make that first call before any stream capture. All calls share the array:
- * calls that overlap on the GPU (different streams, no ordering between them)
- * race on it and must not be issued. The array needs no clearing: every call
- * overwrites the entries it reads. Allocates nothing (no cudaMalloc, no
- * cudaFree, no allocating library routine).
+ * with nel * 4(k+1) > 2^19 are rejected with HDG_ERR_INVALID_ARG. hdg_setup
+ * looks up that array's device address on the context's device (this loads
+ * the part of the library that holds it), so calls made afterwards on that
+ * device find it ready and do no host-side set-up; the address does not
+ * survive a cudaDeviceReset (which also ends every context). The call must be
+ * made with the context's device current (else HDG_ERR_INVALID_ARG). All
+ * calls share the array: calls that overlap on the GPU (different streams, no
+ * ordering between them) race on it and must not be issued. The array needs
+ * no clearing: every call overwrites the entries it reads. Allocates nothing
+ * (no cudaMalloc, no cudaFree, no allocating library routine).
  */
 int hdg_condense_rhs_noalloc(void* ctx, const double* f_q, double* b, int nrhs, void* stream);
 

@@ -24,8 +24,12 @@ class HDGSolve(torch.autograd.Function):
         f_d = f_q.detach().to(torch.float64).contiguous()
         b = solver.condense_rhs(f_d)
         lam, info = solver.solve(b, rtol=rtol, maxit=maxit)
+        # the solver lives as long as the autograd node (its context is released
+        # when the node is freed), so a graph kept with retain_graph=True can be
+        # differentiated more than once
         ctx.solver = solver
         ctx.rtol, ctx.maxit = rtol, maxit
+        ctx.dtypes = (log_kappa.dtype, f_q.dtype)
         ctx.save_for_backward(f_d, lam)
         return lam
 
@@ -35,8 +39,8 @@ class HDGSolve(torch.autograd.Function):
         solver = ctx.solver
         lam_obs = (lam - g.to(torch.float64)).contiguous()
         _, dth, df, _ = solver.adjoint_grad(f_d, lam, lam_obs, rtol=ctx.rtol, maxit=ctx.maxit)
-        solver.close()
-        ctx.solver = None
+        dth = dth.to(ctx.dtypes[0])
+        df = df.to(ctx.dtypes[1])
         return dth, df, None, None, None, None, None, None
 
 

@@ -228,6 +228,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   }
 }
 
+// The segment kernels' wait for their block copy (thread 0; `bar` is followed
+// by 8 spare bytes of shared memory). While the context's probe count
+// (err[1], hdg_options.wait_probe) is positive, block 0 of a launch first waits
+// on a second barrier that nothing ever completes: the bounded wait gives up
+// and the caller takes the timeout path (flag, drain its own copy, exit).
+__device__ __forceinline__ bool seg_first_wait(const ApplyArgs& a, uint64_t* bar) {
+  if (blockIdx.x == 0) {
+    volatile int* probe = a.err + 1;
+    const int left = *probe;
+    if (left > 0) {
+      *probe = left - 1;
+      uint64_t* never = bar + 1;
+      mbar_init(never, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      if (!mbar_wait_bounded(never, 0)) return false;
+    }
+  }
+  return mbar_wait_bounded(bar, 0);
+}
+
 __device__ __forceinline__ void pair_barrier(int id) {
   asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
 }
@@ -532,7 +552,7 @@ __device__ __forceinline__ void seg_body(const ApplyArgs& a, int seg, const TS* 
   }
   // one thread polls the copy's mbarrier (bounded) while the others sleep in the
   // block barrier, leaving the issue slots to the SM's other CTAs
-  if (__syncthreads_or(threadIdx.x == 0 ? !mbar_wait_bounded(bar, 0) : 0)) {
+  if (__syncthreads_or(threadIdx.x == 0 ? !seg_first_wait(a, bar) : 0)) {
     // the copy did not land within the bound: flag it, give it one more bounded
     // wait (it writes this CTA's shared memory), and leave together
     if (threadIdx.x == 0) {

@@ -282,4 +282,96 @@ void build_ref_tables(int p, double hx, double hy, RefTables& t) {
     }
 }
 
+// Tables of the element-local postprocessing (Sec. 3 step (v)) for degree p
+// on an hx x hy rectangle. u* lies in Q_{p+1} (Lagrange at the (p+2)^2 GLL
+// tensor nodes) and solves (kappa grad u*, grad w) = -(q_h, grad w) for all w
+// in Q_{p+1}, with the element mean of u_h. The Neumann matrix S (ns x ns,
+// ns = (p+2)^2) is singular only on constants and the right-hand side g sums
+// to zero, so fixing the first nodal value gives the SPD system S[1:,1:] and a
+// solution u~; the constant shift c 1 that restores the mean follows from the
+// node integrals m_i = (phi*_i, 1):
+//   u* = kappa^-1 (I - 1 m^T / |K|) A g + 1 (u_h, 1) / |K|,  g = -sum_c D_c^T W V q_c
+// with A = [[0, 0], [0, S[1:,1:]^-1]]. Outputs (row-major):
+//   Hq [2][ns][n]  (kappa = 1 map from q_x, q_y nodal values to u*)
+//   mu [n]         ((phi_j, 1) / |K|: the mean of u_h is mu . u)
+//   Dn [2][ns][ns] (d/dx, d/dy of the Q_{p+1} interpolant at its own nodes)
+void build_post_tables(int p, double hx, double hy, std::vector<double>& Hq, std::vector<double>& mu,
+                       std::vector<double>& Dn) {
+  const int n1 = p + 1, n = n1 * n1, s1 = p + 2, ns = s1 * s1;
+  std::vector<double> vn, vw, sn, sw;
+  if (p == 0) vn = {0.0};
+  else gauss_lobatto(p + 1, vn, vw);
+  gauss_lobatto(p + 2, sn, sw);
+  const int nq = p + 3;                         // exact for the degree 2p+2 products
+  std::vector<double> xq, wq, v, d;
+  gauss_legendre(nq, xq, wq);
+  std::vector<double> Bh(nq * n1), Bs(nq * s1), Ds(nq * s1);
+  for (int q = 0; q < nq; ++q) {
+    lagrange_eval(vn, xq[q], v, d);
+    for (int i = 0; i < n1; ++i) Bh[q * n1 + i] = v[i];
+    lagrange_eval(sn, xq[q], v, d);
+    for (int i = 0; i < s1; ++i) { Bs[q * s1 + i] = v[i]; Ds[q * s1 + i] = d[i]; }
+  }
+  const double jac = hx * hy / 4.0, dxi = 2.0 / hx, deta = 2.0 / hy, area = hx * hy;
+  // S, the gradient load G_c[i][j] = (d_c phi*_i, phi_j), node integrals
+  std::vector<double> S(ns * ns, 0.0), G(2 * ns * n, 0.0), ms(ns, 0.0);
+  mu.assign(n, 0.0);
+  for (int qy = 0; qy < nq; ++qy)
+    for (int qx = 0; qx < nq; ++qx) {
+      const double wgt = wq[qx] * wq[qy] * jac;
+      std::vector<double> gx(ns), gy(ns), ph(ns), pv(n);
+      for (int I = 0; I < ns; ++I) {
+        const int ix = I % s1, iy = I / s1;
+        ph[I] = Bs[qx * s1 + ix] * Bs[qy * s1 + iy];
+        gx[I] = Ds[qx * s1 + ix] * dxi * Bs[qy * s1 + iy];
+        gy[I] = Bs[qx * s1 + ix] * Ds[qy * s1 + iy] * deta;
+      }
+      for (int J = 0; J < n; ++J) pv[J] = Bh[qx * n1 + J % n1] * Bh[qy * n1 + J / n1];
+      for (int I = 0; I < ns; ++I) {
+        ms[I] += wgt * ph[I];
+        for (int K = 0; K < ns; ++K) S[I * ns + K] += wgt * (gx[I] * gx[K] + gy[I] * gy[K]);
+        for (int J = 0; J < n; ++J) {
+          G[I * n + J] += wgt * gx[I] * pv[J];
+          G[ns * n + I * n + J] += wgt * gy[I] * pv[J];
+        }
+      }
+      for (int J = 0; J < n; ++J) mu[J] += wgt * pv[J] / area;
+    }
+  // inverse of S with the first node fixed
+  const int r = ns - 1;
+  std::vector<double> S11((size_t)r * r), S11i;
+  for (int i = 0; i < r; ++i)
+    for (int k = 0; k < r; ++k) S11[(size_t)i * r + k] = S[(size_t)(i + 1) * ns + (k + 1)];
+  spd_inverse(r, S11, S11i);
+  Hq.assign((size_t)2 * ns * n, 0.0);
+  for (int c = 0; c < 2; ++c) {
+    // t = A g per unit q_j: t[0] = 0, t[1:] = -S11^-1 G_c[1:, j]
+    std::vector<double> t((size_t)ns * n, 0.0);
+    for (int i = 1; i < ns; ++i)
+      for (int j = 0; j < n; ++j) {
+        double acc = 0.0;
+        for (int k = 1; k < ns; ++k) acc += S11i[(size_t)(i - 1) * r + (k - 1)] * G[(size_t)c * ns * n + k * n + j];
+        t[(size_t)i * n + j] = -acc;
+      }
+    for (int j = 0; j < n; ++j) {
+      double mt = 0.0;
+      for (int i = 0; i < ns; ++i) mt += ms[i] * t[(size_t)i * n + j];
+      for (int i = 0; i < ns; ++i) Hq[(size_t)c * ns * n + i * n + j] = t[(size_t)i * n + j] - mt / area;
+    }
+  }
+  // nodal derivative matrices of Q_{p+1} at its own nodes
+  Dn.assign((size_t)2 * ns * ns, 0.0);
+  std::vector<double> D1(s1 * s1), E1(s1 * s1);
+  for (int a = 0; a < s1; ++a) {
+    lagrange_eval(sn, sn[a], v, d);
+    for (int b = 0; b < s1; ++b) { D1[a * s1 + b] = d[b]; E1[a * s1 + b] = (a == b) ? 1.0 : 0.0; }
+  }
+  for (int I = 0; I < ns; ++I)
+    for (int K = 0; K < ns; ++K) {
+      const int ix = I % s1, iy = I / s1, kx = K % s1, ky = K / s1;
+      Dn[(size_t)I * ns + K] = D1[ix * s1 + kx] * dxi * E1[iy * s1 + ky];
+      Dn[(size_t)ns * ns + I * ns + K] = E1[ix * s1 + kx] * D1[iy * s1 + ky] * deta;
+    }
+}
+
 }  // namespace hdg

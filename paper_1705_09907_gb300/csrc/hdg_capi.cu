@@ -50,6 +50,7 @@ void hdg_default_options(hdg_options* o) {
   if (!o) return;
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
   o->autotune = 1; o->reduced = 1; o->tau_kappa = 0;
+  o->max_device_bytes = 0; o->wait_probe = 0;
 }
 
 const char* hdg_error_string(int s) {
@@ -101,10 +102,30 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     c->off_MiCT = put(mic);
     c->off_VfT = put(tr(r.Vf.data(), r.nf, r.n));
   }
+  {
+    // postprocessing tables, transposed so that lane o reads entry o of a row
+    std::vector<double> Hq, mu, Dn;
+    build_post_tables(k, c->hx, c->hy, Hq, mu, Dn);
+    const int n = c->ref.n, ns = (k + 2) * (k + 2);
+    c->post_ns = ns;
+    std::vector<double> post((size_t)2 * n * ns + n + (size_t)2 * ns * ns);
+    for (int cmp = 0; cmp < 2; ++cmp)
+      for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < n; ++j) post[(size_t)cmp * n * ns + (size_t)j * ns + i] = Hq[(size_t)cmp * ns * n + i * n + j];
+    for (int j = 0; j < n; ++j) post[(size_t)2 * n * ns + j] = mu[j];
+    double* dn = post.data() + (size_t)2 * n * ns + n;
+    for (int cmp = 0; cmp < 2; ++cmp)
+      for (int i = 0; i < ns; ++i)
+        for (int kk = 0; kk < ns; ++kk) dn[(size_t)cmp * ns * ns + (size_t)kk * ns + i] = Dn[(size_t)cmp * ns * ns + i * ns + kk];
+    TRY(ctx_alloc(c, (void**)&c->d_post, post.size() * sizeof(double)));
+    TRY(cudaMemcpyAsync(c->d_post, post.data(), post.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    TRY(cudaStreamSynchronize(s));   // the host vector goes out of scope
+  }
   TRY(ctx_alloc(c, (void**)&c->d_ref, pack.size() * sizeof(double)));
   TRY(cudaMemcpyAsync(c->d_ref, pack.data(), pack.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  TRY(ctx_alloc(c, (void**)&c->err_flag, sizeof(int)));
-  TRY(cudaMemsetAsync(c->err_flag, 0, sizeof(int), s));
+  // [0]: error flag; [1]: launches left that test the bounded-wait path
+  TRY(ctx_alloc(c, (void**)&c->err_flag, 2 * sizeof(int)));
+  TRY(cudaMemsetAsync(c->err_flag, 0, 2 * sizeof(int), s));
   TRY(ctx_alloc(c, (void**)&c->kappa, (size_t)c->nel * sizeof(double)));
   TRY(cudaMemcpyAsync(c->kappa, kappa, (size_t)c->nel * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TRY(launch_check_kappa(c, s));
@@ -191,6 +212,12 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     TRY(ctx_alloc(c, (void**)p, nd * sizeof(double)));
   if (c->opt.autotune) TRY(autotune_applies(c, s));
   TRY(build_hierarchy(c, s));
+  TRY(noalloc_prepare_device(c->dev));
+  if (c->opt.wait_probe > 0) {
+    // armed only now, so the set-up's own applies (autotuning) are not probed
+    const int probe = c->opt.wait_probe;
+    TRY(cudaMemcpyAsync(c->err_flag + 1, &probe, sizeof(int), cudaMemcpyHostToDevice, s));
+  }
   for (int p = 0; p <= k; ++p) {
     TRY(cudaFreeAsync(c->plev[p].Sdense, s));
     c->plev[p].Sdense = nullptr;
@@ -211,7 +238,7 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
   if (opt) o = *opt;
   if (o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.coarse_n < 2 || !(o.tau > 0.0) ||
       o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2 ||
-      o.tau_kappa < 0 || o.tau_kappa > 1)
+      o.tau_kappa < 0 || o.tau_kappa > 1 || o.wait_probe < 0 || o.wait_probe > 64)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);
@@ -352,7 +379,9 @@ int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol,
   int st = nrhs == 1 ? pcg_solve(c, b, lambda, rtol, maxit, inner, info, s)
                      : pcg_solve_batched(c, b, lambda, nrhs, rtol, maxit, inner, info, s);
   const int fl = read_err_flag(c, s);
-  if (st == HDG_OK && fl != HDG_OK) st = fl;
+  // a wait that gave up leaves part of an apply unwritten, which can also stop
+  // CG from converging: report the cause
+  if (fl != HDG_OK && (st == HDG_OK || st == HDG_ERR_NOT_CONVERGED || st == HDG_ERR_BREAKDOWN)) st = fl;
   if (info) info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
 }
@@ -362,6 +391,14 @@ int hdg_recover_local(void* ctx, const double* lambda, const double* f_q, double
   if (!c || !lambda || !f_q) return HDG_ERR_INVALID_ARG;
   if (!u && !q) return HDG_OK;
   TRY(launch_recover(c, lambda, f_q, u, q, (cudaStream_t)stream));
+  return HDG_OK;
+}
+
+int hdg_postprocess(void* ctx, const double* u, const double* q, double* ustar, double* qstar, void* stream) {
+  Context* c = (Context*)ctx;
+  if (!c || !u || !q) return HDG_ERR_INVALID_ARG;
+  if (!ustar && !qstar) return HDG_OK;
+  TRY(launch_postprocess(c, u, q, ustar, qstar, (cudaStream_t)stream));
   return HDG_OK;
 }
 

@@ -35,6 +35,10 @@ struct RefTables {
 };
 
 void build_ref_tables(int p, double hx, double hy, RefTables& t);
+// Postprocessing tables (hdg_basis.cpp): Hq [2][ns][n], mu [n], Dn [2][ns][ns],
+// ns = (p+2)^2
+void build_post_tables(int p, double hx, double hy, std::vector<double>& Hq, std::vector<double>& mu,
+                       std::vector<double>& Dn);
 // Per-edge embedding degree p -> p+1: Pp[(p+2) x (p+1)], Pp[a'][a] = mu_a(x_a')
 void p_prolongation_1d(int p, std::vector<double>& Pp);
 // 1-D Gauss-Legendre and Gauss-Lobatto rules (ascending nodes)
@@ -102,6 +106,8 @@ struct VWork {
   double* cg_part = nullptr;                // [3][reduction blocks][nb]
   double* h_sc = nullptr;                   // pinned host mirror [2][nb]
   std::vector<void*> own;                   // device buffers owned by this work
+  size_t own_bytes = 0;                     // their total size
+  size_t cap = ~size_t(0);                  // most it may allocate (memory cap)
   void* red_z = nullptr;                    // batched reduced-apply scratch [4(k+1)][nel][nb]
 };
 
@@ -122,6 +128,8 @@ struct Context {
          off_MiBt = 0, off_MiC = 0, off_Vf = 0, off_wJf = 0, off_M = 0;
   size_t off_ZT = 0, off_EbT = 0, off_MiBtT = 0, off_MiCT = 0, off_VfT = 0;   // transposes
   double* elem_scratch = nullptr;           // [nel][m] per-element partial results
+  double* d_post = nullptr;                 // postprocessing tables: Hq^T [2][n][ns], mu [n], Dn^T [2][ns][ns]
+  int post_ns = 0;                          // (k+2)^2
   void* red_z = nullptr;                    // [m][nel] element products of the reduced apply
   // finest-level local operators: A_u^-1 (symmetric, stored full) and G = A_u^-1 W
   double* Ainv = nullptr;                   // [nel][n][n]
@@ -218,12 +226,19 @@ cudaError_t use_batched_work(Context* c, int nb, int prec);
 cudaError_t vec_dot(Context* c, const double* a, const double* b, int n, double* out_dev, cudaStream_t s);
 cudaError_t vec_fill(void* p, int prec, size_t n, cudaStream_t s);
 
+// looks up the allocation-free scratch of hdg_condense_rhs_noalloc on device
+// dev (current) at set-up (hdg_noalloc.cu)
+cudaError_t noalloc_prepare_device(int dev);
+
 // Local element operations (hdg_local.cu)
 cudaError_t launch_condense(Context* c, const double* f_q, double* b, int nrhs, cudaStream_t s);
 cudaError_t launch_recover(Context* c, const double* lam, const double* f_q, double* u, double* q,
                            cudaStream_t s);
 cudaError_t launch_adjoint(Context* c, const double* f_q, const double* lam, const double* psi,
                            double* dJ_dlogk, double* dJ_df, cudaStream_t s);
+// u* and q* of the element-local postprocessing (hdg_post.cu)
+cudaError_t launch_postprocess(Context* c, const double* u, const double* q, double* ustar, double* qstar,
+                               cudaStream_t s);
 
 }  // namespace hdg
 

@@ -876,8 +876,10 @@ static void single_works(Context* c) {
 
 static void* work_alloc(VWork* w, size_t bytes) {
   void* p = nullptr;
+  if (w->own_bytes + bytes > w->cap) return nullptr;   // the context's memory cap
   if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
   w->own.push_back(p);
+  w->own_bytes += bytes;
   return p;
 }
 
@@ -903,6 +905,12 @@ static cudaError_t batched_work(Context* c, int nb, bool dbl, VWork** out) {
   VWork* w = new VWork();
   w->nb = nb;
   w->dbl = dbl;
+  if (c->opt.max_device_bytes) {
+    // what the cap leaves after the set-up data and the other batched work
+    size_t used = c->bytes;
+    if (c->wb[1 - f]) used += c->wb[1 - f]->own_bytes;
+    w->cap = c->opt.max_device_bytes > used ? c->opt.max_device_bytes - used : 0;
+  }
   const size_t es = dbl ? sizeof(double) : sizeof(float);
   bool ok = true;
   for (int p = 0; p <= c->k && ok; ++p) {

@@ -31,14 +31,14 @@ static __device__ __align__(256) double g_condense_scratch[kNoAllocScratch];
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};                    // device address per device
 
-// Device address of the scratch array for the current device. The first call
-// on a device looks it up (the array's name is only a host-side stand-in in
-// host code); later calls reuse the cached address.
-cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Device address of the scratch array on device `dev`, which must be the
+// current device. The first lookup on a device asks the runtime for it (the
+// array's name is only a host-side stand-in in host code; the lookup also loads
+// the part of the library image that holds the array); later calls reuse the
+// cached address.
+cudaError_t scratch_for_device(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaError_t e;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
@@ -52,12 +52,26 @@ cudaError_t scratch_for_current_device(double** out) {
 
 }  // namespace
 
+namespace hdg {
+// Called by hdg_setup with the context's device current: looks the scratch
+// address up while the caller is still setting up, so the entry point's own
+// calls on that device find it cached.
+cudaError_t noalloc_prepare_device(int dev) {
+  double* p = nullptr;
+  return scratch_for_device(dev, &p);
+}
+}  // namespace hdg
+
 extern "C" int hdg_condense_rhs_noalloc(void* ctx, const double* f_q, double* b, int nrhs, void* stream) {
   Context* c = (Context*)ctx;
   if (!c || !f_q || !b || nrhs < 1) return HDG_ERR_INVALID_ARG;
   if ((size_t)c->nel * (size_t)c->ref.m > kNoAllocScratch) return HDG_ERR_INVALID_ARG;
+  // the scratch is per device: use it only on the context's own device
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HDG_ERR_CUDA;
+  if (dev != c->dev) return HDG_ERR_INVALID_ARG;
   double* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
+  cudaError_t e = scratch_for_device(dev, &scratch);
   if (e != cudaSuccess) return HDG_ERR_CUDA;
   e = launch_condense_into(c, f_q, b, nrhs, scratch, (cudaStream_t)stream);
   return e == cudaSuccess ? HDG_OK : HDG_ERR_CUDA;

@@ -10,6 +10,8 @@ namespace hdg {
 
 cudaError_t ctx_alloc(Context* c, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  // the caller's memory cap (hdg_options.max_device_bytes) fails like a full device
+  if (c->opt.max_device_bytes && c->bytes + bytes > c->opt.max_device_bytes) return cudaErrorMemoryAllocation;
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) return e;
   c->allocs.push_back(*p);

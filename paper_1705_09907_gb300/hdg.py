@@ -36,7 +36,7 @@ class hdg_options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_n", ctypes.c_int), ("tau", ctypes.c_double),
                 ("cheb_degree", ctypes.c_int), ("mixed", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("reduced", ctypes.c_int),
-                ("tau_kappa", ctypes.c_int)]
+                ("tau_kappa", ctypes.c_int), ("max_device_bytes", ctypes.c_size_t), ("wait_probe", ctypes.c_int)]
 
 
 class hdg_info(ctypes.Structure):
@@ -73,6 +73,7 @@ def _load():
         "hdg_gmg_vcycle": (i, [vp, vp, vp, i, i, vp]),
         "hdg_solve": (i, [vp, vp, vp, i, d, i, i, ctypes.POINTER(hdg_solve_info), vp]),
         "hdg_recover_local": (i, [vp, vp, vp, vp, vp, vp]),
+        "hdg_postprocess": (i, [vp, vp, vp, vp, vp, vp]),
         "hdg_adjoint_grad": (i, [vp, vp, vp, vp, d, i, vp, vp, vp, vp, vp]),
         "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_shared_batched": (i, [vp, vp, vp, i, vp]),
@@ -101,6 +102,7 @@ hdg_apply_trace = _lib.hdg_apply_trace
 hdg_gmg_vcycle = _lib.hdg_gmg_vcycle
 hdg_solve = _lib.hdg_solve
 hdg_recover_local = _lib.hdg_recover_local
+hdg_postprocess = _lib.hdg_postprocess
 hdg_adjoint_grad = _lib.hdg_adjoint_grad
 hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
 hdg_apply_shared_batched = _lib.hdg_apply_shared_batched
@@ -282,6 +284,16 @@ class HDGSolver:
         _check(_lib.hdg_recover_local(self.ctx, _ptr(lam, torch.float64), _ptr(f_q), _ptr(u), _ptr(q), _stream()),
                "hdg_recover_local")
         return u, q
+
+    def postprocess(self, u, q, flux=True):
+        """u*, and q* = -kappa grad u* if flux, from the recovered (u, q): values at
+        the (k+2)^2 Gauss-Lobatto nodes of each element."""
+        ns = (self.k + 2) ** 2
+        us = torch.empty((self.nel, ns), dtype=torch.float64, device="cuda")
+        qs = torch.empty((self.nel, 2, ns), dtype=torch.float64, device="cuda") if flux else None
+        _check(_lib.hdg_postprocess(self.ctx, _ptr(u, torch.float64), _ptr(q, torch.float64), _ptr(us),
+                                    _ptr(qs), _stream()), "hdg_postprocess")
+        return (us, qs) if flux else us
 
     def adjoint_grad(self, f_q, lam, lam_obs, rtol=1e-12, maxit=200):
         f_q = f_q.to(device="cuda", dtype=torch.float64).contiguous()

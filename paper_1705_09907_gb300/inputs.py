@@ -107,3 +107,25 @@ def random_trace(n_edges, k, seed, nrhs=None):
 
 def observation_noise(size, seed, std=1e-3):
     return np.random.default_rng(seed).normal(0.0, std, size=size)
+
+
+def _bump_1d(t):
+    """a(t) = t (t - 1) exp(-t^2) and its first two derivatives."""
+    e = np.exp(-t * t)
+    return ((t * t - t) * e, (-2 * t ** 3 + 2 * t * t + 2 * t - 1) * e,
+            (4 * t ** 4 - 4 * t ** 3 - 10 * t * t + 6 * t + 2) * e)
+
+
+def bump_solution(X, Y):
+    """The manufactured solution of the paper's Sec. 5 experiment,
+    u = x (x - 1) y (y - 1) exp(-x^2 - y^2) = a(x) a(y), its flux q = -grad u
+    (K = 1) and f = -laplace u, at the points X, Y (any shape)."""
+    ax, dax, ddax = _bump_1d(np.asarray(X, dtype=np.float64))
+    ay, day, dday = _bump_1d(np.asarray(Y, dtype=np.float64))
+    return ax * ay, (-dax * ay, -ax * day), -(ddax * ay + ax * dday)
+
+
+def bump_f(n, k):
+    """f of bump_solution at the (k+2) x (k+2) GL sample points of an n x n mesh."""
+    X, Y = element_sample_points(n, k)
+    return bump_solution(X, Y)[2]

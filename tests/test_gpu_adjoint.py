@@ -33,6 +33,27 @@ def test_autograd_matches_oracle_adjoint():
     assert np.abs(fq.grad.cpu().numpy() - df_ref).max() <= 1e-8 * np.abs(df_ref).max()
 
 
+def test_autograd_retain_graph_and_dtypes():
+    """A graph kept with retain_graph=True differentiates twice (the solver lives
+    with the autograd node) with the same gradients, and the gradients come back
+    in the inputs' dtypes (float32 sources give a float32 dL/df)."""
+    from paper_1705_09907_gb300.autograd import hdg_solve
+    nx = ny = 8
+    k = 1
+    th = torch.tensor(inputs.gaussian_field(nx, seed=0, corr_len=0.2), device="cuda", requires_grad=True)
+    fq = torch.tensor(np.random.default_rng(4).normal(size=(nx * ny, k + 2, k + 2)), device="cuda",
+                      dtype=torch.float32, requires_grad=True)
+    lam = hdg_solve(th, fq, nx, ny, k, rtol=1e-13)
+    J = 0.5 * (lam ** 2).sum()
+    J.backward(retain_graph=True)
+    g1 = (th.grad.clone(), fq.grad.clone())
+    assert fq.grad.dtype == torch.float32 and th.grad.dtype == torch.float64
+    th.grad = None
+    fq.grad = None
+    J.backward()
+    assert torch.allclose(th.grad, g1[0], rtol=1e-9, atol=0) and torch.allclose(fq.grad, g1[1], rtol=1e-6, atol=0)
+
+
 def test_adjoint_full_size_vs_finite_differences():
     """512 x 512, k = 2: log kappa = seeded Gaussian field (seed 0), lambda_obs =
     the solve at a second field (seed 1) plus N(0, 1e-3) noise (seed 2), f = 1;

@@ -105,3 +105,17 @@ def test_postprocess_rate_p_plus_2():
         ru = np.log2(errs[1][0] / errs[2][0])
         rq = np.log2(errs[1][1] / errs[2][1])
         assert abs(ru - (p + 2)) < 0.25 and abs(rq - (p + 1)) < 0.25
+
+
+def test_bump_solution_closed_form_matches_symbolic():
+    """The numpy closed form of the Sec. 5 manufactured solution (used by the GPU
+    tests, where sympy is absent) against sympy's derivatives."""
+    from paper_1705_09907_gb300 import inputs
+    fl, ul, qe = _exact()
+    rng = np.random.default_rng(0)
+    X, Y = rng.uniform(0, 1, 50), rng.uniform(0, 1, 50)
+    u, (qx, qy), f = inputs.bump_solution(X, Y)
+    qxs, qys = qe(X, Y)
+    assert np.allclose(u, ul(X, Y), rtol=1e-13, atol=1e-16)
+    assert np.allclose(qx, qxs, rtol=1e-13, atol=1e-15) and np.allclose(qy, qys, rtol=1e-13, atol=1e-15)
+    assert np.allclose(f, fl(X, Y), rtol=1e-12, atol=1e-14)
