@@ -15,6 +15,10 @@
 // X is BF16, Y FP32 (kind::f16 with BF16 operands, FP32 accumulation). One
 // tcgen05.mma (M = 128, N = 16, K = 16) per 16 columns of K, issued by one
 // thread; completion through tcgen05.commit on an mbarrier (bounded wait).
+// The x window of an item is loaded by five tensor-map (TMA) copies, one per
+// edge row, into 128-byte-swizzled shared memory that the MMAs read directly.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "hdg_internal.h"
@@ -77,60 +81,52 @@ __device__ __forceinline__ bool mbar_wait_1s(uint64_t* bar, unsigned parity) {
   }
 }
 
-// A tiles are MN-major without swizzle: core matrices of 8 k-rows x 16 bytes (8
-// consecutive m), K-direction core matrices 128 bytes apart, groups of 8 m
-// `sbo` bytes apart. B tiles are K-major with the same core-matrix strides.
-// x window of one segment and one group of 64 right-hand sides, built once and
-// read by the MMAs directly. 5 edge rows (V1: vertical edges of row j-1, V0:
-// row j, Hm: horizontal edges of row j-1, H0: row j, H1: row j+1) x 18 slots
-// (slot = i - (i0 - 1)); one slot holds one edge as 8 m-groups (8 right-hand
-// sides each) x 8 k-rows (the edge's nodes, zero beyond k+1) x 16 bytes, i.e.
-// eight MN-major core matrices 128 bytes apart. With SBO = 128 B an MMA's 16
-// m-groups cover two consecutive slots = two neighbouring elements' faces; the
-// two core matrices of a K16 step are the edges (W, E) of one element (next
-// slot, LBO = 1 KB) or (S, N) (next row, LBO = one row).
+// 128-byte-swizzled K/MN-major descriptor (tcgen05 layout type 2): start,
+// leading-byte offset = stride between 64-element atoms along M/N, stride-byte
+// offset = stride between groups of 8 rows along K, descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return smem_desc(addr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
+// x window of one segment and one group of 64 right-hand sides, read by the
+// MMAs directly. 5 edge rows (V1: vertical edges of row j-1, V0: row j, Hm:
+// horizontal edges of row j-1, H0: row j, H1: row j+1) x 10 slots (slot = i -
+// (i0 - 1)); one slot holds one edge as 8 node rows (zero past k+1) x 64
+// right-hand sides x 2 bytes = one 1 KB swizzle atom of an MN-major operand
+// (a row's 16-byte chunks XOR-permuted by the row index, as the TMA copies
+// write them). An MMA's M = 128 rows are two atoms (two neighbouring elements'
+// faces, next slot: LBO = 1 KB); its K = 16 columns are two 8-row groups, the
+// edges (W, E) of one element (next slot, SBO = 1 KB) or (S, N) (next row).
 constexpr int kBS = 8;                      // elements per segment of this kernel
 constexpr int kWRows = 5, kWSlots = kBS + 2;
 constexpr uint32_t kSlotB = 1024u, kRowB = kWSlots * kSlotB;
+constexpr uint32_t kWinTx = kWRows * kRowB; // bytes landed per window
 enum { RV1 = 0, RV0 = 1, RHM = 2, RH0 = 3, RH1 = 4 };
 
-// Gather one item's window (segment seg, right-hand sides chunk*64 ..): the
-// interior edges' node rows by cp.async (one commit group), zeros for edges
-// outside the mesh. Node rows nd >= k+1 are zero from the start and never written.
-__device__ __forceinline__ void gather_window(const BatchedArgs& a, unsigned char* W, int seg, int chunk, int tid,
-                                              int nthreads) {
-  const int n1 = a.n1;
-  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+// Tensor maps over X restricted to the interior edges, so that every boundary
+// or off-mesh edge of a window is outside the map and lands as zeros:
+//   tv: vertical edges i = 1..nx-1 of rows j = 0..ny-1, dims (rhs, node, i-1, j)
+//   th: horizontal edges j = 1..ny-1, i = 0..nx-1, dims (rhs, node, i, j-1)
+// The node box is 8 (past k+1 out of the map: zeros). One copy per edge row.
+__device__ __forceinline__ void tma_load_row(unsigned char* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                             int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(su32(dst)), "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void load_window(const BatchedArgs& a, const CUtensorMap* tv, const CUtensorMap* th,
+                                            unsigned char* W, int seg, int chunk, uint64_t* bar) {
   const int j = seg / a.spr, i0 = (seg % a.spr) * kBS;
-  const size_t rstride = (size_t)a.nrhs;                      // elements between node rows of X
-  // one thread per (row, slot, 16-byte group): the edge is found once, then its
-  // k+1 node rows follow with an address step
-  for (int idx = tid; idx < kWRows * kWSlots * 8; idx += nthreads) {
-    const int g = idx & 7, rs = idx >> 3;
-    const int r = rs / kWSlots, sl = rs - r * kWSlots;
-    const int i = i0 - 1 + sl;
-    int edge = -1;
-    bool inb = false;
-    switch (r) {
-      case RV1: inb = j >= 1 && i >= 1 && i <= nx - 1; edge = i + (nx + 1) * (j - 1); break;
-      case RV0: inb = i >= 1 && i <= nx - 1; edge = i + (nx + 1) * j; break;
-      case RHM: inb = j >= 2 && i >= 0 && i < nx; edge = nv + i + nx * (j - 1); break;
-      case RH0: inb = j >= 1 && i >= 0 && i < nx; edge = nv + i + nx * j; break;
-      default: inb = j + 1 <= ny - 1 && i >= 0 && i < nx; edge = nv + i + nx * (j + 1); break;
-    }
-    const uint32_t dst = su32(W + (uint32_t)(r * kWSlots + sl) * kSlotB + (uint32_t)g * 128u);
-    if (inb) {   // interior edges only (the boundary trace is zero)
-      const __nv_bfloat16* src = a.X + (size_t)edge * n1 * rstride + chunk * 64 + g * 8;
-      for (int nd = 0; nd < n1; ++nd)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + (uint32_t)nd * 16u),
-                     "l"(src + (size_t)nd * rstride)
-                     : "memory");
-    } else {
-      for (int nd = 0; nd < n1; ++nd)
-        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + (uint32_t)nd * 16u), "r"(0u) : "memory");
-    }
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
+  const int x = chunk * 64;            // 128-byte aligned innermost coordinate
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(kWinTx) : "memory");
+  // slot 0 is edge i0 - 1: vertical map coordinate i - 1 = i0 - 2
+  tma_load_row(W + RV1 * kRowB, tv, x, 0, i0 - 2, j - 1, bar);
+  tma_load_row(W + RV0 * kRowB, tv, x, 0, i0 - 2, j, bar);
+  tma_load_row(W + RHM * kRowB, th, x, 0, i0 - 1, j - 2, bar);
+  tma_load_row(W + RH0 * kRowB, th, x, 0, i0 - 1, j - 1, bar);
+  tma_load_row(W + RH1 * kRowB, th, x, 0, i0 - 1, j, bar);
 }
 
 // The kBS tiles (kBS/2 W face pairs, kBS/2 S face pairs) x 4 K16 steps of one
@@ -141,7 +137,7 @@ __device__ __forceinline__ void issue_mmas(const unsigned char* W, const unsigne
   constexpr int kTiles = kBS;
   // descriptors = fixed fields + (address >> 4); shared addresses stay below 256 KB,
   // so the 14-bit address field never carries into the next field
-  const uint64_t dslot = smem_desc(0u, kSlotB, 128u), drow = smem_desc(0u, kRowB, 128u);
+  const uint64_t dslot = smem_desc_sw128(0u, kSlotB, kSlotB), drow = smem_desc_sw128(0u, kSlotB, kRowB);
   const uint32_t wb4 = su32(W) >> 4;
   const uint64_t db0 = smem_desc(su32(Bbuf), 128u, 1024u), db1 = smem_desc(su32(Bbuf + tileB), 128u, 1024u);
 #pragma unroll
@@ -151,7 +147,7 @@ __device__ __forceinline__ void issue_mmas(const unsigned char* W, const unsigne
     const uint64_t bd0 = type ? db1 : db0;
     uint64_t ad[4];
     ad[0] = dslot + wb4 + (uint32_t)(RV0 * kWSlots + sl) * (kSlotB >> 4);   // own W, E
-    ad[1] = drow + wb4 + (uint32_t)(RH0 * kWSlots + sl) * (kSlotB >> 4);    // own S, N
+    ad[1] = drow + wb4 + (uint32_t)(RH0 * kWSlots + sl) * (kSlotB >> 4);    // own S, N (N: next row)
     if (type == 0) {                                                         // west neighbour
       ad[2] = dslot + wb4 + (uint32_t)(RV0 * kWSlots + sl - 1) * (kSlotB >> 4);
       ad[3] = drow + wb4 + (uint32_t)(RH0 * kWSlots + sl - 1) * (kSlotB >> 4);
@@ -229,37 +225,43 @@ __device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, in
 
 // Persistent CTAs with warp-specialized roles and a two-deep pipeline over items
 // (segment x 64 right-hand sides):
-//   gather warps 8..10 fill window n%2 by cp.async; each thread's copies arrive
-//     on full[n%2] when they land (cp.async.mbarrier.arrive);
-//   warp 11 (one thread) waits for full[n%2], issues the item's 32 MMAs into
+//   warp 8 (one thread) loads window n%2 with five TMA copies that complete on
+//     full[n%2] (expect-tx of the whole window; off-map parts land as zeros);
+//   warp 9 (one thread) waits for full[n%2], issues the item's 32 MMAs into
 //     accumulator n%2 and commits them to mma_done[n%2];
 //   drain warps 0..7 wait for mma_done[n%2] and write the item's faces (warp w
 //     reads TMEM lane quadrant w%4, tiles 4(w/4) .. 4(w/4)+3), then release the
 //     accumulator through tmem_free[n%2].
 // A window is refilled only after the MMAs that read it completed, an accumulator
 // only after it was drained. Every wait is bounded (1 s); a role whose wait runs
-// out stops, and the others then run out of their own waits.
-constexpr int kDrainWarps = 8, kGatherWarps = 3;
-constexpr int kSpecThreads = 32 * (kDrainWarps + kGatherWarps + 1);
-constexpr int kGatherThreads = 32 * kGatherWarps;
-constexpr int kIssueWarp = kDrainWarps + kGatherWarps;
+// out stops, and the others then run out of their own waits. Before the CTA
+// exits after such a stop, the last copy and the last commit issued on each
+// buffer get one more bounded wait, so nothing is left in flight.
+constexpr int kDrainWarps = 8;
+constexpr int kLoadWarp = kDrainWarps, kIssueWarp = kDrainWarps + 1;
+constexpr int kSpecThreads = 32 * (kDrainWarps + 2);
 
 __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-__global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm[];
+__global__ void __launch_bounds__(kSpecThreads)
+    batched_apply_kernel(BatchedArgs a, const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap th) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  // the swizzle atoms of the windows must start on 1 KB boundaries of the
+  // shared address space: round the dynamic base up (1 KB of slack is requested)
+  unsigned char* sm = sm_raw + ((1024u - (su32(sm_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr uint32_t tileB = kTileN * 64 * 2;                // K = 64 (4 steps x 16)
   constexpr uint32_t winB = kWRows * kRowB;
-  // windows [2][5][kWSlots][1 KB] at sm and sm + winB
+  // windows [2][5][kWSlots][1 KB] at sm and sm + winB (1 KB aligned)
   unsigned char* Bbuf = sm + 2 * winB;                       // [2][tileB]
   uint64_t* full = reinterpret_cast<uint64_t*>(Bbuf + 2 * tileB);       // [2]
   uint64_t* mma_done = full + 2;                                          // [2]
   uint64_t* tmem_free = mma_done + 2;                                     // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_free + 2);
-  // [0] drain, [1] gather, [2] issuer failed; [3], [4] commits issued per accumulator
+  // [0] drain, [1] load, [2] issuer failed; [3], [4] commits issued per
+  // accumulator; [5], [6] windows loaded per buffer
   volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 1);
   constexpr int kCols = 2 * kBS * kTileN;                    // two accumulators of 8 tiles x 16 columns
 
@@ -271,16 +273,18 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
   }
   if (tid == 0) {
     for (int q = 0; q < 2; ++q) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(full + q)), "r"(kGatherThreads) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + q)) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mma_done + q)) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(tmem_free + q)), "r"(kDrainWarps) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int q = 0; q < 5; ++q) flags[q] = 0;
+    for (int q = 0; q < 7; ++q) flags[q] = 0;
   }
-  // both windows zero (the node rows past k+1 stay zero), then the shared blocks
-  for (uint32_t o = (uint32_t)tid * 16u; o < 2u * winB; o += kSpecThreads * 16u)
-    *reinterpret_cast<uint4*>(sm + o) = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 32 * kLoadWarp) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tv) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&th) : "memory");
+  }
+  // the shared blocks, K-major without swizzle (core matrices of 8 n x 16 bytes)
   for (int idx = tid; idx < 2 * kTileN * 64; idx += kSpecThreads) {
     const int t = idx / (kTileN * 64), rem = idx % (kTileN * 64);
     const int n = rem / 64, k = rem % 64;
@@ -315,26 +319,22 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(tmem_free + buf)) : "memory");
     }
-  } else if (warp < kIssueWarp) {
-    // ---------------- gather ----------------
-    const int gtid = tid - 32 * kDrainWarps;
-    unsigned pd0 = 0u, pd1 = 0u;
-    long n = 0;
-    for (long item = first; item < items; item += step, ++n) {
-      const int buf = (int)(n & 1);
-      if (n >= 2) {      // window buf was read by item n-2's MMAs
-        if (gtid == 0 && !mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0)) flags[1] = 1;
-        named_sync(2, kGatherThreads);
-        if (flags[1]) break;
-        if (buf) pd1 ^= 1u; else pd0 ^= 1u;
+  } else if (warp == kLoadWarp) {
+    // ---------------- TMA loads ----------------
+    if (lane == 0) {
+      unsigned pd0 = 0u, pd1 = 0u;
+      long n = 0;
+      for (long item = first; item < items; item += step, ++n) {
+        const int buf = (int)(n & 1);
+        if (n >= 2) {      // window buf was read by item n-2's MMAs
+          if (!mbar_wait_1s(mma_done + buf, buf ? pd1 : pd0)) { flags[1] = 1; break; }
+          if (buf) pd1 ^= 1u; else pd0 ^= 1u;
+        }
+        load_window(a, &tv, &th, sm + (buf ? winB : 0u), (int)(item / chunks), (int)(item % chunks), full + buf);
+        flags[5 + buf] = flags[5 + buf] + 1;
       }
-      gather_window(a, sm + (buf ? winB : 0u), (int)(item / chunks), (int)(item % chunks), gtid, kGatherThreads);
-      // zero stores visible to the tensor cores; the copies arrive when they land
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(full + buf)) : "memory");
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-  } else if (lane == 0) {
+  } else if (warp == kIssueWarp && lane == 0) {
     // ---------------- MMA issue ----------------
     unsigned pf0 = 0u, pf1 = 0u, pt0 = 0u, pt1 = 0u;
     long n = 0;
@@ -346,7 +346,6 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
         if (!mbar_wait_1s(tmem_free + buf, buf ? pt1 : pt0)) { flags[2] = 1; break; }
         if (buf) pt1 ^= 1u; else pt0 ^= 1u;
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       issue_mmas(sm + (buf ? winB : 0u), Bbuf, tmem + (uint32_t)(buf * kBS * kTileN), mma_done + buf);
       flags[3 + buf] = flags[3 + buf] + 1;
@@ -355,13 +354,15 @@ __global__ void __launch_bounds__(kSpecThreads) batched_apply_kernel(BatchedArgs
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (flags[0] || flags[1] || flags[2]) {
-    // a wait ran out: flag it, and give the last commit issued on each
-    // accumulator (at most one is outstanding per accumulator) one more bounded
-    // wait before its tensor memory is freed
+    // a wait ran out: flag it, and give the last window copy and the last
+    // commit issued on each buffer (at most one of each is outstanding) one more
+    // bounded wait before the shared and tensor memory are released
     if (tid == 0) {
       atomicExch(a.err, 2);
-      for (int q = 0; q < 2; ++q)
+      for (int q = 0; q < 2; ++q) {
+        if (flags[5 + q] > 0) (void)mbar_wait_1s(full + q, (unsigned)((flags[5 + q] - 1) & 1));
         if (flags[3 + q] > 0) (void)mbar_wait_1s(mma_done + q, (unsigned)((flags[3 + q] - 1) & 1));
+      }
     }
     __syncthreads();
   }
@@ -406,7 +407,56 @@ cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s) {
 
 size_t batched_smem_bytes(int n1) {
   (void)n1;
-  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 80;   // + 6 mbarriers, TMEM slot, 5 flags
+  // windows, shared blocks, 6 mbarriers + TMEM slot + 7 flags, alignment slack
+  return (size_t)2 * kWRows * kRowB + (size_t)2 * kTileN * 64 * 2 + 80 + 1024;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library), looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// The two interior-edge maps over X [ndof][nrhs] (BF16): see load_window.
+static cudaError_t make_edge_maps(const Context* c, const void* X, int nrhs, CUtensorMap* tv, CUtensorMap* th) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int nx = c->mesh.nx, ny = c->mesh.ny, n1 = c->k + 1;
+  const cuuint64_t rowB = (cuuint64_t)nrhs * 2, edgeB = rowB * n1;
+  const size_t nv = (size_t)(nx + 1) * ny;
+  const cuuint32_t box[4] = {64, 8, (cuuint32_t)kWSlots, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  {
+    char* base = (char*)X + edgeB;                                   // edge i = 1 of row 0
+    const cuuint64_t dims[4] = {(cuuint64_t)nrhs, (cuuint64_t)n1, (cuuint64_t)(nx - 1), (cuuint64_t)ny};
+    const cuuint64_t str[3] = {rowB, edgeB, edgeB * (cuuint64_t)(nx + 1)};
+    if (enc(tv, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    char* base = (char*)X + edgeB * (cuuint64_t)(nv + (size_t)nx);  // horizontal edge row j = 1
+    const cuuint64_t dims[4] = {(cuuint64_t)nrhs, (cuuint64_t)n1, (cuuint64_t)nx, (cuuint64_t)(ny - 1)};
+    const cuuint64_t str[3] = {rowB, edgeB, edgeB * (cuuint64_t)nx};
+    if (enc(th, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s) {
@@ -414,14 +464,17 @@ cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, 
   a.X = (const __nv_bfloat16*)X; a.Y = Y; a.B = c->shared_B;
   a.nx = c->mesh.nx; a.ny = c->mesh.ny; a.n1 = c->k + 1; a.Kp = shared_kp(a.n1);
   a.nrhs = nrhs; a.spr = (c->mesh.nx + kBS - 1) / kBS; a.nseg = a.spr * c->mesh.ny; a.err = c->err_flag;
+  if (a.n1 > 8 || c->mesh.nx < 2 || c->mesh.ny < 2) return cudaErrorInvalidValue;
+  alignas(64) CUtensorMap tv, th;
+  HDG_CUDA_TRY(make_edge_maps(c, X, nrhs, &tv, &th));
   const size_t smem = batched_smem_bytes(a.n1);
   if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
   HDG_CUDA_TRY(cudaFuncSetAttribute(batched_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin));
   const long items = (long)a.nseg * (nrhs / 64);
-  // two resident CTAs per SM (256 TMEM columns and ~104 KB shared memory each)
+  // two resident CTAs per SM (256 TMEM columns and ~107 KB shared memory each)
   long blocks = (long)c->num_sms * 2;
   if (blocks > items) blocks = items;
-  batched_apply_kernel<<<(int)blocks, kSpecThreads, smem, s>>>(a);
+  batched_apply_kernel<<<(int)blocks, kSpecThreads, smem, s>>>(a, tv, th);
   return cudaGetLastError();
 }
 
