@@ -113,6 +113,13 @@ typedef struct {
                                  scales with kappa_K, S_K = kappa_K S_ref and
                                  the condensed right-hand side does not depend
                                  on kappa; 0: tau = `tau` everywhere (0)     */
+  int smoother;               /* p-level smoother of the V-cycle: 0 = weighted
+                                 additive Schwarz on element patches
+                                 (Sec. 6.4.2, default); 1 = factorized sparse
+                                 approximate inverse (Sec. 6.4.1), x += G^T G
+                                 (f - A x), G lower triangular on the pattern
+                                 of the level operator, unit diagonal of
+                                 G A G^T                                      */
   size_t max_device_bytes;    /* cap on the device memory the context keeps
                                  (set-up data and work vectors; 0 = no cap):
                                  an allocation that would pass it fails with

@@ -68,6 +68,11 @@ struct PLevel {
   // V-cycle work vectors, [ndof] each, per precision (d = double, f = float)
   double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
   float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;
+  // FSAI smoother (hdg_options.smoother = 1, p >= 1): factor G by row edge and
+  // slot (hdg_fsai.cu), FP64 and FP32; w: scratch of G t for one vector
+  double* G64 = nullptr; float* G32 = nullptr;
+  size_t fsai_entries = 0;
+  double* w64 = nullptr; float* w32 = nullptr;
   // p = 0 only: inverse diagonal of the assembled operator (Chebyshev/Jacobi)
   double* dinv64 = nullptr; float* dinv32 = nullptr;
   double lmax = 0.0;
@@ -95,6 +100,7 @@ struct VWork {
   int nb = 1;
   bool dbl = true;
   std::vector<void*> pr, px, pt;            // p-levels 0..k: residual, correction, scratch
+  std::vector<void*> pw;                    // p-levels 0..k: FSAI scratch (null without FSAI)
   void* p0d = nullptr;                      // p = 0 Chebyshev direction
   std::vector<void*> hr, hx, ht, hd, hd2;   // Q1 levels, finest first (hd2: second Chebyshev direction)
   double* coarse_w = nullptr;               // [nb][coarse_dim] FP64 scratch
@@ -221,6 +227,12 @@ void release_works(Context* c);
 // makes the batched work of nb right-hand sides (vector type of prec) current
 // for column applies: allocates it on first use, sets cur_zb
 cudaError_t use_batched_work(Context* c, int nb, int prec);
+
+// FSAI smoother (hdg_fsai.cu): factor of level p from plev[p].Sdense, and
+// out = add + G^T G in for nb columns (add may be null or alias out)
+cudaError_t launch_fsai_setup(Context* c, int p, cudaStream_t s);
+cudaError_t launch_fsai_smooth(Context* c, int p, int prec, const void* in, const void* add, void* out, void* wbuf,
+                               int nb, cudaStream_t s);
 
 // Vector helpers (hdg_apply.cu)
 cudaError_t vec_dot(Context* c, const double* a, const double* b, int n, double* out_dev, cudaStream_t s);

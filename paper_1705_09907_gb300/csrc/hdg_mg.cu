@@ -719,11 +719,16 @@ static cudaError_t pmg(Context* c, VWork& w, int prec, int p, const T* r, T* x, 
   const int nb = w.nb;
   T* t = (T*)w.pt[p];
   const int nu1 = c->opt.nu1, nu2 = c->opt.nu2;
+  // smoother M of this level: x_out = x_add + M v (Schwarz blocks, or G^T G)
+  auto smooth = [&](const T* v, const T* xadd, T* xout) -> cudaError_t {
+    if (c->opt.smoother == 1) return launch_fsai_smooth(c, p, prec, v, xadd, xout, w.pw[p], nb, s);
+    return launch_apply(c, p, 1, prec, v, xadd, xout, 1.0, xadd ? 1.0 : 0.0, nb, s);
+  };
   // pre-smoothing: x = M r, then x += M (r - A x)
-  HDG_CUDA_TRY(launch_apply(c, p, 1, prec, r, nullptr, x, 1.0, 0.0, nb, s));
+  HDG_CUDA_TRY(smooth(r, nullptr, x));
   for (int i = 1; i < nu1; ++i) {
     HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, nb, s));
-    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, nb, s));
+    HDG_CUDA_TRY(smooth(t, x, x));
   }
   // restricted residual; a BF16 cycle takes it with the FP32 blocks: its smooth
   // part drives the coarse correction, and BF16 rounding (2^-9) of the blocks
@@ -739,7 +744,7 @@ static cudaError_t pmg(Context* c, VWork& w, int prec, int p, const T* r, T* x, 
   HDG_CUDA_TRY(p_transfer<T>(false, Lc.n1, c->n_edges, nb, Pp, xc, x, s));
   for (int i = 0; i < nu2; ++i) {
     HDG_CUDA_TRY(launch_apply(c, p, 0, prec, x, r, t, -1.0, 1.0, nb, s));
-    HDG_CUDA_TRY(launch_apply(c, p, 1, prec, t, x, x, 1.0, 1.0, nb, s));
+    HDG_CUDA_TRY(smooth(t, x, x));
   }
   return cudaSuccess;
 }
@@ -854,12 +859,13 @@ static void single_works(Context* c) {
     const bool dbl = (f == 0);
     w.nb = 1;
     w.dbl = dbl;
-    w.pr.clear(); w.px.clear(); w.pt.clear();
+    w.pr.clear(); w.px.clear(); w.pt.clear(); w.pw.clear();
     for (int p = 0; p <= c->k; ++p) {
       PLevel& L = c->plev[p];
       w.pr.push_back(dbl ? (void*)L.r64 : (void*)L.r32);
       w.px.push_back(dbl ? (void*)L.x64 : (void*)L.x32);
       w.pt.push_back(dbl ? (void*)L.t64 : (void*)L.t32);
+      w.pw.push_back(dbl ? (void*)L.w64 : (void*)L.w32);
     }
     w.p0d = dbl ? (void*)c->plev[0].d64 : (void*)c->plev[0].d32;
     w.hr.clear(); w.hx.clear(); w.ht.clear(); w.hd.clear(); w.hd2.clear();
@@ -918,6 +924,9 @@ static cudaError_t batched_work(Context* c, int nb, bool dbl, VWork** out) {
     void *a = work_alloc(w, n), *b = work_alloc(w, n), *d = work_alloc(w, n);
     ok = a && b && d;
     w->pr.push_back(a); w->px.push_back(b); w->pt.push_back(d);
+    void* fw = nullptr;
+    if (ok && p >= 1 && c->opt.smoother == 1) { fw = work_alloc(w, n); ok = fw != nullptr; }
+    w->pw.push_back(fw);
   }
   if (ok) { w->p0d = work_alloc(w, (size_t)c->n_edges * nb * es); ok = w->p0d != nullptr; }
   for (size_t l = 0; l < c->hlev.size() && ok; ++l) {
@@ -1031,6 +1040,10 @@ cudaError_t build_hierarchy(Context* c, cudaStream_t s) {
     const size_t n = ne * L.n1;
     HDG_CUDA_TRY(alloc_vecs_d(c, n, {&L.r64, &L.x64, &L.t64}));
     if (mixed) HDG_CUDA_TRY(alloc_vecs_f(c, n, {&L.r32, &L.x32, &L.t32}));
+    if (p >= 1 && c->opt.smoother == 1) {
+      HDG_CUDA_TRY(alloc_vecs_d(c, n, {&L.w64}));
+      if (mixed) HDG_CUDA_TRY(alloc_vecs_f(c, n, {&L.w32}));
+    }
   }
   // p = 0 Jacobi diagonal and Chebyshev direction vector
   PLevel& L0 = c->plev[0];
