@@ -120,6 +120,10 @@ typedef struct {
                                  (f - A x), G lower triangular on the pattern
                                  of the level operator, unit diagonal of
                                  G A G^T                                      */
+  int fmg_start;              /* hdg_solve with one right-hand side starts CG
+                                 from one full multigrid cycle (Sec. 7) with
+                                 this many V-cycles per level instead of from
+                                 zero; 0 = zero start (0), at most 16         */
   size_t max_device_bytes;    /* cap on the device memory the context keeps
                                  (set-up data and work vectors; 0 = no cap):
                                  an allocation that would pass it fails with
@@ -247,15 +251,20 @@ int hdg_setup_batch(int n, const hdg_mesh* meshes, const int* k, const double* c
 int hdg_apply_multi(int n, void* const* ctxs, const void* const* x, void* const* y, int prec, void* stream);
 
 /*
- * Batched apply for a uniform coefficient (every S_K equal): Y = A X for nrhs
- * right-hand sides on the 5th-generation tensor cores. Each owned face computes
- * y_e = [S[F rows], S[F' rows]] [x_K; x_nb] (Alg. 3 with a shared block) as one
+ * Batched apply with one shared element block: Y = A X for nrhs right-hand
+ * sides on the 5th-generation tensor cores, for a uniform coefficient (every
+ * S_K equal) or for tau_K = kappa_K (every S_K = kappa_K S_ref, Sec. 3 with tau
+ * piecewise constant; each element's part scaled by its kappa when the
+ * accumulator is read). Each owned face computes
+ * y_e = s_K S[F rows] x_K + s_nb S[F' rows] x_nb (Alg. 3 with a shared block) as one
  * MMA row block: two faces x 64 right-hand sides (M = 128) by the 2*4(k+1)
- * gathered dofs (K) by k+1 outputs (N, padded to 16), FP32 accumulation in
- * tensor memory. X: device BF16 [ndof][nrhs] (right-hand side fastest), Y:
- * device FP32 [ndof][nrhs]; nrhs a multiple of 64; both 16-byte aligned; boundary
- * entries of X are ignored and Y is 0 there. Errors: INVALID_ARG (nrhs, alignment,
- * null), UNSUPPORTED (the context's kappa is not uniform).
+ * gathered dofs (K) by 16 outputs (N: the own element's k+1 rows, then the
+ * neighbour's), FP32 accumulation in tensor memory. X: device BF16
+ * [ndof][nrhs] (right-hand side fastest), Y: device FP32 [ndof][nrhs]; nrhs a
+ * multiple of 64; both 16-byte aligned; boundary entries of X are ignored and Y
+ * is 0 there. X is read through TMA tensor maps made for each call. Errors:
+ * INVALID_ARG (nrhs, alignment, null), UNSUPPORTED (neither a uniform kappa
+ * nor tau_kappa).
  */
 int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void* stream);
 
@@ -299,12 +308,44 @@ int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol,
               int inner, hdg_solve_info* info, void* stream);
 
 /*
+ * n independent problems of uneven size solved together (1 <= n <= 64
+ * contexts, e.g. from hdg_setup_batch, all on the current device, each at most
+ * once): hdg_solve of context q on (b[q], lambda[q]) with the common rtol,
+ * maxit and inner precision, each on a stream and host thread of its own, so
+ * the instances share the GPU at the same time (small meshes fill the SMs that
+ * large ones leave idle). Every instance runs the kernels of its own hdg_solve,
+ * so each lambda[q] is bitwise what hdg_solve gives for it alone. The call
+ * orders itself after the work already issued on `stream`, makes `stream` wait
+ * for every instance, and returns when all have finished. b[q], lambda[q]:
+ * device [ndof_q] doubles. infos (host [n], may be NULL) and statuses (host
+ * [n], may be NULL) receive each instance's report and status; the return
+ * value is HDG_OK if every instance converged, else the first failing
+ * instance's status. Errors: INVALID_ARG (count, pointers, a context twice or
+ * on another device), UNSUPPORTED (a mixed precision without mixed blocks),
+ * and those of hdg_solve.
+ */
+int hdg_solve_multi(int n, void* const* ctxs, const double* const* b, double* const* lambda, double rtol,
+                    int maxit, int inner, hdg_solve_info* infos, int* statuses, void* stream);
+
+/*
  * Surface-to-volume reconstruction (Sec. 3 step (iv), Eq. shur0, Sec. 8.3):
  * from the trace lambda [ndof] and sources f_q [nel][k+2][k+2] compute
  * u [nel][(k+1)^2] and q [nel][2][(k+1)^2] (device doubles; either may be NULL).
  */
 int hdg_recover_local(void* ctx, const double* lambda, const double* f_q, double* u, double* q,
                       void* stream);
+
+/*
+ * One full multigrid cycle (Sec. 7): b (device [ndof] doubles) restricted to
+ * every level (R = P^T), a direct solve on the coarsest mesh, then level by
+ * level upwards the coarser solution interpolated (P) as the start and
+ * `cycles` FP64 V-cycles of that level's own hierarchy (Alg. 1 on the p = 0
+ * and Q1 levels, Alg. 2 on the p-levels) applied to its residual; lambda
+ * (device [ndof]) receives the finest solution. Asynchronous on `stream`. Its
+ * per-level vectors are allocated on the first call. 1 <= cycles <= 16.
+ * Errors: INVALID_ARG, OOM.
+ */
+int hdg_fmg(void* ctx, const double* b, double* lambda, int cycles, void* stream);
 
 /*
  * Element-local postprocessing (Sec. 3 step (v); the local filter of the LDG-H

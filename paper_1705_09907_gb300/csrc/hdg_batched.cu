@@ -34,6 +34,7 @@ struct BatchedArgs {
   const __nv_bfloat16* X;     // [ndof][nrhs]
   float* Y;                   // [ndof][nrhs]
   const __nv_bfloat16* B;     // [2][16][Kp] shared blocks, face type W then S (row n, column k)
+  const double* kappa;        // per-element scale of the two halves of D (tau_K = kappa_K), or null (1)
   int nx, ny, n1, Kp, nrhs, spr, nseg;
   int* err;
 };
@@ -57,12 +58,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(kTileN >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
 
+// One bounded probe of an mbarrier phase. The suspend-time hint lets the
+// hardware park the polling thread until the phase completes (or ~0.1 ms pass)
+// instead of spinning: the three polling threads of a CTA would otherwise take
+// most of the SM's issue slots from the drain warps.
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(su32(bar)), "r"(parity)
+      : "r"(su32(bar)), "r"(parity), "r"(100000u)
       : "memory");
   return ok != 0;
 }
@@ -206,10 +211,20 @@ __device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, in
       if (i < nx) {
         const bool bndrow = type == 0 ? (i == 0) : (j == 0);
         const int eout = type == 0 ? i + (nx + 1) * j : nv + i + nx * j;
-        // fixed-trip loops over the tile's 16 columns keep v in registers
+        // columns 0..7 hold the own element's part, 8..15 the neighbour's (west
+        // for W faces, south for S faces); each is scaled by its element's kappa
+        // when the blocks are kappa_K S_ref
+        float so = 1.0f, sn = 1.0f;
+        if (a.kappa && !bndrow) {
+          so = (float)a.kappa[i + nx * j];
+          sn = (float)a.kappa[type == 0 ? (i - 1) + nx * j : i + nx * (j - 1)];
+        }
+        // fixed-trip loops over the tile's columns keep v in registers
 #pragma unroll
-        for (int q = 0; q < kTileN; ++q)
-          if (q < n1) ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0f : __uint_as_float(vt[q]);
+        for (int q = 0; q < kTileN / 2; ++q)
+          if (q < n1)
+            ybase[((size_t)eout * n1 + q) * a.nrhs] =
+                bndrow ? 0.0f : so * __uint_as_float(vt[q]) + sn * __uint_as_float(vt[kTileN / 2 + q]);
         if (type == 0 && i == nx - 1) {
           const int eb = nx + (nx + 1) * j;
           for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
@@ -371,24 +386,29 @@ __global__ void __launch_bounds__(kSpecThreads)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
-// B blocks from the shared FP64 block S (element 0 of the finest level):
-// type 0 (W faces): row n < k+1: [S[W row n, :], S[E row n, :]]; type 1 (S faces):
-// [S[S row n, :], S[N row n, :]]; zero rows n >= k+1 and columns k >= 2m.
-__global__ void pack_shared_b_kernel(const double* __restrict__ S, int n1, int Kp, __nv_bfloat16* __restrict__ B) {
+// B blocks from the shared FP64 block S (element 0 of the finest level, times
+// `scale`): type 0 (W faces): output row n < k+1 of the own part holds
+// [S[W row n, :] on the own element's (W, E), (S, N) edges]; row 8 + n of the
+// neighbour part holds [S[E row n, :] on the west neighbour's edges]; type 1 (S
+// faces) the same with S / N rows and the south neighbour. All other entries
+// are zero (rows past k+1, the own part on the neighbour's K steps and back).
+__global__ void pack_shared_b_kernel(const double* __restrict__ S, int n1, double scale,
+                                     __nv_bfloat16* __restrict__ B) {
   // B[type][n][k], k = step*16 + h*8 + node: step 0 own (W, E), 1 own (S, N),
-  // 2 neighbour (W, E), 3 neighbour (S, N); rows n = the face's node (zero past k+1)
+  // 2 neighbour (W, E), 3 neighbour (S, N)
   const int m = 4 * n1;
-  (void)Kp;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * kTileN * 64; idx += gridDim.x * blockDim.x) {
     const int t = idx / (kTileN * 64), rem = idx % (kTileN * 64);
     const int n = rem / 64, k = rem % 64;
     const int step = k >> 4, h = (k >> 3) & 1, nd = k & 7;
+    const bool nb_part = n >= kTileN / 2;
+    const int row = n & (kTileN / 2 - 1);
     double v = 0.0;
-    if (n < n1 && nd < n1) {
+    if (row < n1 && nd < n1 && nb_part == (step >= 2)) {
       const int own_face = t == 0 ? 0 : 2, nb_face = t == 0 ? 1 : 3;
       const int row_face = step < 2 ? own_face : nb_face;          // rows of S used
       const int col_face = (step & 1) * 2 + h;                      // W, E, S, N
-      v = S[(size_t)(row_face * n1 + n) * m + col_face * n1 + nd];
+      v = scale * S[(size_t)(row_face * n1 + row) * m + col_face * n1 + nd];
     }
     B[idx] = __float2bfloat16_rn((float)v);
   }
@@ -398,10 +418,16 @@ __global__ void pack_shared_b_kernel(const double* __restrict__ S, int n1, int K
 
 int shared_kp(int n1) { (void)n1; return 64; }
 
-cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s) {
+// The shared block of the tensor-core apply: S itself for a uniform kappa, or
+// S_ref = S_0 / kappa_0 with tau_K = kappa_K (every S_K = kappa_K S_ref; the
+// drain scales each element's part by its kappa). kappa0 is element 0's.
+cudaError_t prepare_shared_blocks(Context* c, double kappa0, cudaStream_t s) {
   const int n1 = c->k + 1;
+  if (n1 > kTileN / 2) return cudaSuccess;                    // degrees past 7: no shared-block apply
   HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->shared_B, (size_t)2 * kTileN * 64 * sizeof(__nv_bfloat16)));
-  pack_shared_b_kernel<<<8, 256, 0, s>>>(c->plev[c->k].Sdense, n1, 64, c->shared_B);
+  c->shared_scaled = c->opt.tau_kappa != 0;
+  pack_shared_b_kernel<<<8, 256, 0, s>>>(c->plev[c->k].Sdense, n1, c->shared_scaled ? 1.0 / kappa0 : 1.0,
+                                         c->shared_B);
   return cudaGetLastError();
 }
 
@@ -462,6 +488,7 @@ static cudaError_t make_edge_maps(const Context* c, const void* X, int nrhs, CUt
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s) {
   BatchedArgs a{};
   a.X = (const __nv_bfloat16*)X; a.Y = Y; a.B = c->shared_B;
+  a.kappa = c->shared_scaled ? c->kappa : nullptr;
   a.nx = c->mesh.nx; a.ny = c->mesh.ny; a.n1 = c->k + 1; a.Kp = shared_kp(a.n1);
   a.nrhs = nrhs; a.spr = (c->mesh.nx + kBS - 1) / kBS; a.nseg = a.spr * c->mesh.ny; a.err = c->err_flag;
   if (a.n1 > 8 || c->mesh.nx < 2 || c->mesh.ny < 2) return cudaErrorInvalidValue;

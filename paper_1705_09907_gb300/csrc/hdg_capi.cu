@@ -50,7 +50,7 @@ void hdg_default_options(hdg_options* o) {
   if (!o) return;
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
   o->autotune = 1; o->reduced = 1; o->tau_kappa = 0;
-  o->smoother = 0; o->max_device_bytes = 0; o->wait_probe = 0;
+  o->smoother = 0; o->fmg_start = 0; o->max_device_bytes = 0; o->wait_probe = 0;
 }
 
 const char* hdg_error_string(int s) {
@@ -194,7 +194,9 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     bool uni = true;
     for (int e = 1; e < c->nel && uni; ++e) uni = (hk[e] == hk[0]);
     c->uniform_kappa = uni;
-    if (uni) TRY(prepare_shared_blocks(c, s));
+    // one shared block for every element: S for a uniform kappa, S_ref with a
+    // per-element kappa scale when tau_K = kappa_K
+    if (uni || c->opt.tau_kappa) TRY(prepare_shared_blocks(c, hk[0], s));
   }
   for (int p = k; p >= 1; --p) TRY(launch_galerkin_coarsen(c, p, s));
   for (int p = k; p >= 0; --p) {
@@ -240,7 +242,7 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
   if (o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.coarse_n < 2 || !(o.tau > 0.0) ||
       o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2 ||
       o.tau_kappa < 0 || o.tau_kappa > 1 || o.wait_probe < 0 || o.wait_probe > 64 || o.smoother < 0 ||
-      o.smoother > 1)
+      o.smoother > 1 || o.fmg_start < 0 || o.fmg_start > 16)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);
@@ -365,7 +367,7 @@ int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void*
   Context* c = (Context*)ctx;
   if (!c || !X || !Y || nrhs < 64 || nrhs % 64 != 0) return HDG_ERR_INVALID_ARG;
   if (((uintptr_t)X % 16) != 0 || ((uintptr_t)Y % 16) != 0) return HDG_ERR_INVALID_ARG;
-  if (!c->uniform_kappa || !c->shared_B) return HDG_ERR_UNSUPPORTED;
+  if (!c->shared_B) return HDG_ERR_UNSUPPORTED;
   TRY(launch_batched_apply(c, X, Y, nrhs, (cudaStream_t)stream));
   return HDG_OK;
 }
@@ -393,6 +395,15 @@ int hdg_recover_local(void* ctx, const double* lambda, const double* f_q, double
   if (!c || !lambda || !f_q) return HDG_ERR_INVALID_ARG;
   if (!u && !q) return HDG_OK;
   TRY(launch_recover(c, lambda, f_q, u, q, (cudaStream_t)stream));
+  return HDG_OK;
+}
+
+int hdg_fmg(void* ctx, const double* b, double* lambda, int cycles, void* stream) {
+  Context* c = (Context*)ctx;
+  if (!c || !b || !lambda || b == lambda || cycles < 1 || cycles > 16) return HDG_ERR_INVALID_ARG;
+  const cudaError_t e = fmg_solve(c, b, lambda, cycles, (cudaStream_t)stream);
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HDG_ERR_OOM; }
+  TRY(e);
   return HDG_OK;
 }
 

@@ -117,6 +117,14 @@ struct VWork {
   void* red_z = nullptr;                    // batched reduced-apply scratch [4(k+1)][nel][nb]
 };
 
+// Per-level vectors of the full multigrid cycle (double, one right-hand side):
+// right-hand side, solution, residual and correction on every p-level and Q1 level
+struct FmgWork {
+  bool ready = false;
+  std::vector<double*> bp, xp, rp, zp;      // p-levels 0..k
+  std::vector<double*> bh, xh, rh, zh;      // Q1 levels, finest first
+};
+
 struct Context {
   hdg_mesh mesh{};
   hdg_options opt{};
@@ -158,6 +166,7 @@ struct Context {
   std::vector<void*> allocs;
   // V-cycle work: single vector (double, float family) and batched (on demand)
   VWork w1[2];                              // [0] double, [1] float
+  FmgWork fmg;                              // full multigrid work (first hdg_fmg call)
   VWork* wb[2] = {nullptr, nullptr};
   // the reduced-apply scratch of the batched work whose cycle, solve or apply
   // is being issued (launch_apply with nrhs > 1 uses it; null: dense columns)
@@ -167,6 +176,7 @@ struct Context {
   // uniform coefficient: the shared block for the tensor-core batched apply
   bool uniform_kappa = false;
   __nv_bfloat16* shared_B = nullptr;        // [2][16][Kp] BF16
+  bool shared_scaled = false;               // shared_B is S_ref (tau_K = kappa_K): scale by kappa_K
 };
 
 // vectors of a V-cycle / apply in this precision are double (else float)
@@ -184,7 +194,7 @@ cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s);
 cudaError_t launch_p0_diag(Context* c, cudaStream_t s);
 cudaError_t autotune_applies(Context* c, cudaStream_t s);
 // tensor-core batched apply of the shared block (hdg_batched.cu)
-cudaError_t prepare_shared_blocks(Context* c, cudaStream_t s);
+cudaError_t prepare_shared_blocks(Context* c, double kappa0, cudaStream_t s);
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s);
 // one persistent launch over several contexts (apply_multi.cu); returns hdg_status
 int apply_multi(Context* const* ctx, int n, const void* const* x, void* const* y, int prec, cudaStream_t s);
@@ -222,6 +232,8 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
 // its residual meets rtol
 int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rtol, int maxit, int inner,
                       hdg_solve_info* info, cudaStream_t s);
+// one full multigrid cycle with `cycles` FP64 V-cycles per level: x = FMG(b)
+cudaError_t fmg_solve(Context* c, const double* b, double* x, int cycles, cudaStream_t s);
 // releases the V-cycle works' graphs and the batched works' buffers
 void release_works(Context* c);
 // makes the batched work of nb right-hand sides (vector type of prec) current

@@ -966,6 +966,89 @@ cudaError_t use_batched_work(Context* c, int nb, int prec) {
   return cudaSuccess;
 }
 
+static cudaError_t alloc_vecs_d(Context* c, size_t n, std::initializer_list<double**> ps);
+
+__global__ void fmg_add_kernel(size_t n, const double* __restrict__ z, double* __restrict__ x) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    x[t] += z[t];
+}
+
+// Full multigrid (Sec. 7) with FP64 V-cycles, one right-hand side: b restricted
+// to every level, a direct solve on the coarsest mesh, then upwards level by
+// level the coarser solution interpolated as the start and `cycles` V-cycles of
+// that level's own hierarchy (hmg on the p = 0 and Q1 levels, pmg on the
+// p-levels) applied to its residual. The per-level right-hand sides, solutions,
+// residuals and corrections live in the context's FMG work (allocated on the
+// first call); the V-cycles use the single-vector work as usual.
+cudaError_t fmg_solve(Context* c, const double* b, double* x_out, int cycles, cudaStream_t s) {
+  FmgWork& f = c->fmg;
+  const int k = c->k, nh = (int)c->hlev.size();
+  const size_t ne = (size_t)c->n_edges;
+  if (!f.ready) {
+    f.bp.assign(k + 1, nullptr); f.xp.assign(k + 1, nullptr); f.rp.assign(k + 1, nullptr); f.zp.assign(k + 1, nullptr);
+    f.bh.assign(nh, nullptr); f.xh.assign(nh, nullptr); f.rh.assign(nh, nullptr); f.zh.assign(nh, nullptr);
+    for (int p = 0; p <= k; ++p)
+      HDG_CUDA_TRY(alloc_vecs_d(c, ne * c->plev[p].n1, {&f.bp[p], &f.xp[p], &f.rp[p], &f.zp[p]}));
+    for (int l = 0; l < nh; ++l)
+      HDG_CUDA_TRY(alloc_vecs_d(c, (size_t)c->hlev[l].nv, {&f.bh[l], &f.xh[l], &f.rh[l], &f.zh[l]}));
+    f.ready = true;
+  }
+  VWork& w = c->w1[0];
+  const int prec = HDG_PREC_FP64;
+  // right-hand sides on every level (R = P^T)
+  HDG_CUDA_TRY(cudaMemcpyAsync(f.bp[k], b, ne * (k + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (int p = k; p >= 1; --p)
+    HDG_CUDA_TRY(p_transfer<double>(true, c->plev[p - 1].n1, c->n_edges, 1, c->plev[p].Pp, f.bp[p], f.bp[p - 1], s));
+  restrict_J_kernel<double><<<grid_for((size_t)c->hlev[0].nv), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, 1, f.bp[0],
+                                                                           f.bh[0]);
+  HDG_CUDA_TRY(cudaGetLastError());
+  for (int l = 0; l + 1 < nh; ++l) {
+    HLevel& Hc = c->hlev[l + 1];
+    restrict_q_kernel<double><<<grid_for((size_t)Hc.nv), 256, 0, s>>>(Hc.nx, Hc.ny, 1, f.bh[l], f.bh[l + 1]);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  // coarsest mesh: direct solve
+  HDG_CUDA_TRY(hmg<double>(c, w, prec, nh - 1, f.bh[nh - 1], f.xh[nh - 1], s));
+  // up the Q1 levels
+  for (int l = nh - 2; l >= 0; --l) {
+    HLevel& H = c->hlev[l];
+    HLevel& Hc = c->hlev[l + 1];
+    HDG_CUDA_TRY(cudaMemsetAsync(f.xh[l], 0, (size_t)H.nv * sizeof(double), s));
+    prolong_q_add_kernel<double><<<grid_for((size_t)H.nv), 256, 0, s>>>(Hc.nx, Hc.ny, 1, f.xh[l + 1], f.xh[l]);
+    HDG_CUDA_TRY(cudaGetLastError());
+    for (int it = 0; it < cycles; ++it) {
+      HDG_CUDA_TRY(q_apply<double>(H, H.st64, f.xh[l], f.bh[l], f.rh[l], -1.0, 1.0, 1, s));
+      HDG_CUDA_TRY(hmg<double>(c, w, prec, l, f.rh[l], f.zh[l], s));
+      fmg_add_kernel<<<grid_for((size_t)H.nv), 256, 0, s>>>((size_t)H.nv, f.zh[l], f.xh[l]);
+      HDG_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  // the p = 0 level
+  HDG_CUDA_TRY(cudaMemsetAsync(f.xp[0], 0, ne * sizeof(double), s));
+  prolong_J_add_kernel<double><<<grid_for(ne), 256, 0, s>>>(c->mesh.nx, c->mesh.ny, 1, f.xh[0], f.xp[0]);
+  HDG_CUDA_TRY(cudaGetLastError());
+  for (int it = 0; it < cycles; ++it) {
+    HDG_CUDA_TRY(p0_apply(c, prec, f.xp[0], f.bp[0], f.rp[0], -1.0, 1.0, 1, s));
+    HDG_CUDA_TRY(hmg<double>(c, w, prec, -1, f.rp[0], f.zp[0], s));
+    fmg_add_kernel<<<grid_for(ne), 256, 0, s>>>(ne, f.zp[0], f.xp[0]);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  // up the p-levels
+  for (int p = 1; p <= k; ++p) {
+    const size_t n = ne * c->plev[p].n1;
+    HDG_CUDA_TRY(cudaMemsetAsync(f.xp[p], 0, n * sizeof(double), s));
+    HDG_CUDA_TRY(p_transfer<double>(false, c->plev[p - 1].n1, c->n_edges, 1, c->plev[p].Pp, f.xp[p - 1], f.xp[p], s));
+    for (int it = 0; it < cycles; ++it) {
+      HDG_CUDA_TRY(launch_apply(c, p, 0, prec, f.xp[p], f.bp[p], f.rp[p], -1.0, 1.0, 1, s));
+      HDG_CUDA_TRY(pmg<double>(c, w, prec, p, f.rp[p], f.zp[p], s));
+      fmg_add_kernel<<<grid_for(n), 256, 0, s>>>(n, f.zp[p], f.xp[p]);
+      HDG_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  HDG_CUDA_TRY(cudaMemcpyAsync(x_out, f.xp[k], ne * (k + 1) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return cudaSuccess;
+}
+
 cudaError_t vcycle(Context* c, int prec, const void* r, void* z, int nb, cudaStream_t s) {
   const bool dbl = prec_double(prec);
   if (nb == 1) return vcycle_typed(c, c->w1[dbl ? 0 : 1], prec, r, z, false, s);
@@ -1146,12 +1229,20 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
   // outer residual with the double-float blocks (FP64 vectors, ~48-bit products)
   const int outer = (inner == HDG_PREC_FP64) ? HDG_PREC_FP64 : HDG_PREC_F32X2;
 #define CK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return HDG_ERR_CUDA; } while (0)
-  CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
-  CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CK(dots<double>(c, n, b, b, nullptr, nullptr, nullptr, nullptr, sc + 4, s));
   CK(cudaMemcpyAsync(h, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const double bn = std::sqrt(h[0]);
+  if (c->opt.fmg_start > 0 && bn > 0.0) {
+    // start from one full multigrid cycle: x = FMG(b), r = b - A x
+    const cudaError_t e = fmg_solve(c, b, x, c->opt.fmg_start, s);
+    if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HDG_ERR_OOM; }
+    CK(e);
+    CK(launch_apply(c, c->k, 0, outer, x, b, r, -1.0, 1.0, 1, s));
+  } else {
+    CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+    CK(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
   if (info) { info->iterations = 0; info->relres = 0.0; info->relres_history[0] = 1.0; }
   if (!(bn > 0.0)) {
     if (info) info->relres = 0.0;

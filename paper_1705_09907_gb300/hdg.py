@@ -36,7 +36,8 @@ class hdg_options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_n", ctypes.c_int), ("tau", ctypes.c_double),
                 ("cheb_degree", ctypes.c_int), ("mixed", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("reduced", ctypes.c_int),
-                ("tau_kappa", ctypes.c_int), ("smoother", ctypes.c_int), ("max_device_bytes", ctypes.c_size_t),
+                ("tau_kappa", ctypes.c_int), ("smoother", ctypes.c_int), ("fmg_start", ctypes.c_int),
+                ("max_device_bytes", ctypes.c_size_t),
                 ("wait_probe", ctypes.c_int)]
 
 
@@ -75,12 +76,15 @@ def _load():
         "hdg_solve": (i, [vp, vp, vp, i, d, i, i, ctypes.POINTER(hdg_solve_info), vp]),
         "hdg_recover_local": (i, [vp, vp, vp, vp, vp, vp]),
         "hdg_postprocess": (i, [vp, vp, vp, vp, vp, vp]),
+        "hdg_fmg": (i, [vp, vp, vp, i, vp]),
         "hdg_adjoint_grad": (i, [vp, vp, vp, vp, d, i, vp, vp, vp, vp, vp]),
         "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_shared_batched": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_multi": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
         "hdg_setup_batch": (i, [i, ctypes.POINTER(hdg_mesh), ctypes.POINTER(i), ctypes.POINTER(vp),
                                 ctypes.POINTER(hdg_options), vp, ctypes.POINTER(vp)]),
+        "hdg_solve_multi": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), d, i, i,
+                                ctypes.POINTER(hdg_solve_info), ctypes.POINTER(i), vp]),
         "hdg_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -104,11 +108,13 @@ hdg_gmg_vcycle = _lib.hdg_gmg_vcycle
 hdg_solve = _lib.hdg_solve
 hdg_recover_local = _lib.hdg_recover_local
 hdg_postprocess = _lib.hdg_postprocess
+hdg_fmg = _lib.hdg_fmg
 hdg_adjoint_grad = _lib.hdg_adjoint_grad
 hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
 hdg_apply_shared_batched = _lib.hdg_apply_shared_batched
 hdg_apply_multi = _lib.hdg_apply_multi
 hdg_setup_batch = _lib.hdg_setup_batch
+hdg_solve_multi = _lib.hdg_solve_multi
 
 
 def setup_batch(problems, **options):
@@ -137,6 +143,27 @@ def apply_multi(solvers, xs, prec="fp64", outs=None):
     yp = arr(*[_ptr(y, VEC_DTYPE[prec]).value for y in ys])
     _check(_lib.hdg_apply_multi(n, ctxs, xp, yp, PREC[prec], _stream()), "hdg_apply_multi")
     return ys
+
+
+def solve_multi(solvers, bs, rtol=1e-10, maxit=200, inner="fp64", outs=None, raise_on_error=True):
+    """hdg_solve_multi: every HDGSolver's system at once (each on its own stream).
+    Returns the solutions and one info dict per instance."""
+    n = len(solvers)
+    lams = [torch.empty_like(b) for b in bs] if outs is None else outs
+    arr = ctypes.c_void_p * n
+    ctxs = arr(*[s.ctx.value for s in solvers])
+    bp = arr(*[_ptr(b, torch.float64).value for b in bs])
+    lp = arr(*[_ptr(x, torch.float64).value for x in lams])
+    infos = (hdg_solve_info * n)()
+    sts = (ctypes.c_int * n)()
+    st = _lib.hdg_solve_multi(n, ctxs, bp, lp, float(rtol), int(maxit), PREC[inner], infos, sts, _stream())
+    out = [{"status": sts[q], "iterations": infos[q].iterations, "relres": infos[q].relres,
+            "solve_ms": infos[q].solve_ms} for q in range(n)]
+    if raise_on_error:
+        _check(st, "hdg_solve_multi")
+    return lams, out
+
+
 hdg_destroy = _lib.hdg_destroy
 
 
@@ -285,6 +312,13 @@ class HDGSolver:
         _check(_lib.hdg_recover_local(self.ctx, _ptr(lam, torch.float64), _ptr(f_q), _ptr(u), _ptr(q), _stream()),
                "hdg_recover_local")
         return u, q
+
+    def fmg(self, b, cycles=1, out=None):
+        """One full multigrid cycle (Sec. 7) with `cycles` V-cycles per level."""
+        lam = torch.empty_like(b) if out is None else out
+        _check(_lib.hdg_fmg(self.ctx, _ptr(b, torch.float64), _ptr(lam, torch.float64), int(cycles), _stream()),
+               "hdg_fmg")
+        return lam
 
     def postprocess(self, u, q, flux=True):
         """u*, and q* = -kappa grad u* if flux, from the recovered (u, q): values at

@@ -45,3 +45,30 @@ def test_shared_batched_requires_uniform_kappa():
         s.apply_shared_batched(X)
     assert e.value.status == hdg.HDG_ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("k,nx,ny", [(4, 24, 10), (2, 13, 9)])
+def test_shared_batched_tau_kappa_vs_oracle(k, nx, ny):
+    """tau_K = kappa_K with a lognormal kappa: every S_K = kappa_K S_ref, one
+    shared block with each element's part scaled by its kappa, against the
+    oracle's assembled operator of that discretisation on the same BF16 inputs."""
+    from paper_1705_09907_gb300 import hdg, inputs
+    m = omesh.Mesh(nx, ny)
+    kap = np.exp(inputs.gaussian_field(nx, seed=k, corr_len=0.2, ny=ny))
+    prob = ohdg.HDGProblem(m, k, kap, tau="kappa")
+    A, idx = prob.assemble_interior()
+    rng = np.random.default_rng(30 + k)
+    X = torch.as_tensor(rng.standard_normal((prob.ndof, 64)), dtype=torch.bfloat16, device="cuda")
+    Xh = X.float().cpu().numpy().astype(np.float64)
+    s = hdg.HDGSolver(nx, ny, k, torch.as_tensor(kap, device="cuda"), tau_kappa=1)
+    Y = s.apply_shared_batched(X)
+    torch.cuda.synchronize()
+    Y = Y.cpu().numpy().astype(np.float64)
+    ref = np.zeros_like(Xh)
+    ref[idx] = A @ Xh[idx]
+    bound = np.zeros_like(Xh)
+    bound[idx] = abs(A) @ np.abs(Xh[idx])
+    assert np.all(np.abs(Y - ref) <= 8e-3 * bound + 1e-30)
+    bnd = np.setdiff1d(np.arange(prob.ndof), idx)
+    assert np.all(Y[bnd] == 0.0)
+    s.close()

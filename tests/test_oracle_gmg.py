@@ -332,3 +332,28 @@ def test_lognormal_field_statistics():
     lag = 6                                   # r = 6 / 128
     c = np.mean(G[:, :, :-lag] * G[:, :, lag:])
     assert abs(c - np.exp(-(lag / n) ** 2 / (2 * 0.05 ** 2))) < 0.08
+
+
+def test_fmg_converges_to_direct_solve_and_is_linear():
+    """Full multigrid (Sec. 7): with many V-cycles per level it reaches the
+    direct solution; it is linear in b; one FMG pass leaves a smaller residual
+    than one V-cycle from zero (it starts every level from the interpolated
+    coarser solution)."""
+    m = omesh.Mesh(16, 16)
+    kap = np.exp(np.random.default_rng(2).normal(size=m.nel))
+    G = gmg.NestedGMG(m, 3, kap)
+    top = G.plevels[3]
+    rng = np.random.default_rng(5)
+    b1 = np.zeros(top.ndof)
+    b2 = np.zeros(top.ndof)
+    b1[top.idx] = rng.normal(size=len(top.idx))
+    b2[top.idx] = rng.normal(size=len(top.idx))
+    x_ref = np.zeros(top.ndof)
+    x_ref[top.idx] = spla.spsolve(top.A.tocsc(), b1[top.idx])
+    x40 = G.fmg(b1, cycles=40)
+    assert np.linalg.norm(x40 - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+    lin = G.fmg(2.5 * b1 + b2) - (2.5 * G.fmg(b1) + G.fmg(b2))
+    assert np.linalg.norm(lin) <= 1e-12 * np.linalg.norm(G.fmg(b1))
+    r_fmg = np.linalg.norm(b1 - G.apply(G.fmg(b1)))
+    r_v = np.linalg.norm(b1 - G.apply(G.vcycle(b1)))
+    assert r_fmg < r_v
