@@ -369,6 +369,34 @@ class NestedGMG:
         v = v + self.Pp[p] @ vc
         return lev.smooth(r, v, self.nu2)
 
+    def fmg(self, b_full, cycles=1):
+        """Full multigrid (Sec. 7): the right-hand side restricted to every level
+        (R = P^T), a direct solve on the coarsest mesh, then level by level
+        upwards: the coarser solution interpolated (P) as the start, improved
+        by `cycles` V-cycles of that level's own hierarchy (Alg. 1 on the h-levels,
+        Alg. 2 on the p-levels) applied to its residual. Returns the finest
+        p-level solution on ALL trace dofs (boundary entries 0)."""
+        top = self.plevels[self.k]
+        bp = {self.k: np.asarray(b_full)[top.idx]}
+        for p in range(self.k, 0, -1):
+            bp[p - 1] = self.Pp[p].T @ bp[p]
+        bh = [bp[0]]                       # h-level 0 is the p = 0 level
+        for l in range(len(self.hA) - 1):
+            bh.append(self.hP[l].T @ bh[l])
+        L = len(self.hA) - 1
+        x = sla.cho_solve(self.coarse, bh[L]) if self.coarse is not None else np.zeros_like(bh[L])
+        for l in range(L - 1, -1, -1):
+            x = self.hP[l] @ x
+            for _ in range(cycles):
+                x = x + self.hmg(l, bh[l] - self.hA[l] @ x)
+        for p in range(1, self.k + 1):
+            x = self.Pp[p] @ x
+            for _ in range(cycles):
+                x = x + self.pmg(p, bp[p] - self.plevels[p].A @ x)
+        out = np.zeros(top.ndof)
+        out[top.idx] = x
+        return out
+
     def vcycle(self, r_full):
         top = self.plevels[self.k]
         z = np.zeros(top.ndof)
