@@ -782,13 +782,16 @@ def run_ours(args):
     # nominal), so it is bound by the FP64 pipe, not by HBM.
     # DRAM read+write of one such FP64 level-k launch at 512 x 512, k = 4 (ncu,
     # one-pass dram__bytes_read.sum + dram__bytes_write.sum, warm launches of
-    # the set-up autotuner's choice, the 4-warp segment kernel): 860.0 MB + 18.3 MB
-    traffic = 878.3e6 if (N, k) == (512, 4) else None
+    # the set-up autotuner's choice, the 4-warp segment kernel, taken after the
+    # kernel's last change): 859.9 MB + 18.2 MB
+    traffic = 878.1e6 if (N, k) == (512, 4) else None
     roof = {"kernel": "FP64 Schwarz-block apply at level k (autotuned; apply_seg_kernel<5,double,double,double,0,4> "
                       "on GB300), timed on the condensed blocks of a reduced=0 context (same kernel, same bytes)",
             "bound": "alu", "achieved": tflops, "peak": 1.25, "unit": "TFLOP/s", "frac": tflops / 1.25,
             "peak_source": "nominal FP64 rate of GB300 (recipe table); HBM fraction in trace_apply_dense",
-            "traffic": traffic, "algorithmic_bytes": fp["algorithmic_bytes"]}
+            "traffic": traffic, "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at "
+                                                  "512x512 k=4 (profiles/apply_k4_512_dram.md); null at other sizes",
+            "algorithmic_bytes": fp["algorithmic_bytes"]}
     roof["peak_fp64_measured"] = fp64_tf
     roof["peak_fp64_measured_source"] = "cuBLAS DGEMM through torch.matmul, 4096^3 float64, best of 5 (this run)"
     roof["frac_of_measured_fp64"] = tflops / fp64_tf if fp64_tf > 0 else None
