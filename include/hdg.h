@@ -269,6 +269,24 @@ int hdg_apply_multi(int n, void* const* ctxs, const void* const* x, void* const*
 int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void* stream);
 
 /*
+ * FP64 batched apply for a uniform coefficient on the BF16 tensor cores, by
+ * exact integer splitting (the Ozaki scheme): Y = A X with X, Y device FP64
+ * [ndof][nrhs] (right-hand side fastest), nrhs a multiple of 64, 16-byte
+ * aligned, X and Y distinct. Each column of X is scaled by a power of two and
+ * cut into 8 BF16 slices of 7 bits (56 bits in all), the shared element block
+ * likewise at set-up; the products of slices are exact in the tensor cores'
+ * FP32 accumulation and the groups of equal weight are recombined as 128-bit
+ * integers and rounded once to FP64, so the result agrees with an FP64
+ * evaluation to about the FP64 rounding of |S||x| (terms below 2^-56 of the
+ * column's and the block's scale are dropped; entries below 2^-1022 count as
+ * zero). Same face formula, boundary rules and layouts as
+ * hdg_apply_shared_batched. The slices of X (8 x 2 bytes per entry) are
+ * scratch owned by the context, grown on demand. Errors: INVALID_ARG,
+ * UNSUPPORTED (kappa not uniform, tau_kappa, or k > 7), OOM.
+ */
+int hdg_apply_shared_fp64(void* ctx, const double* X, double* Y, int nrhs, void* stream);
+
+/*
  * One nested V-cycle z = V r (Algs. 2 then 1, zero initial guess): p-levels
  * k..1 with nu1/nu2 weighted additive Schwarz steps (Sec. 6.4.2), restriction
  * R = P^T and prolongation P per edge (Eqs. eq_mg_pro, eq_mg_res), the p = 0

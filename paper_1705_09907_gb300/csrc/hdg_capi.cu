@@ -197,6 +197,7 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
     // one shared block for every element: S for a uniform kappa, S_ref with a
     // per-element kappa scale when tau_K = kappa_K
     if (uni || c->opt.tau_kappa) TRY(prepare_shared_blocks(c, hk[0], s));
+    if (uni && !c->opt.tau_kappa) TRY(prepare_ozaki_blocks(c, s));
   }
   for (int p = k; p >= 1; --p) TRY(launch_galerkin_coarsen(c, p, s));
   for (int p = k; p >= 0; --p) {
@@ -372,6 +373,17 @@ int hdg_apply_shared_batched(void* ctx, const void* X, float* Y, int nrhs, void*
   return HDG_OK;
 }
 
+int hdg_apply_shared_fp64(void* ctx, const double* X, double* Y, int nrhs, void* stream) {
+  Context* c = (Context*)ctx;
+  if (!c || !X || !Y || X == Y || nrhs < 64 || nrhs % 64 != 0) return HDG_ERR_INVALID_ARG;
+  if (((uintptr_t)X % 16) != 0 || ((uintptr_t)Y % 16) != 0) return HDG_ERR_INVALID_ARG;
+  if (!c->oz_B) return HDG_ERR_UNSUPPORTED;
+  const cudaError_t e = launch_ozaki_apply(c, X, Y, nrhs, (cudaStream_t)stream);
+  if (e == cudaErrorMemoryAllocation) { cudaGetLastError(); return HDG_ERR_OOM; }
+  TRY(e);
+  return HDG_OK;
+}
+
 int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol, int maxit, int inner,
               hdg_solve_info* info, void* stream) {
   Context* c = (Context*)ctx;
@@ -472,6 +484,8 @@ void hdg_destroy(void* ctx) {
   for (auto& L : c->plev)
     if (L.Sdense) cudaFree(L.Sdense);
   for (void* p : c->allocs) cudaFree(p);
+  if (c->oz_XS) cudaFree(c->oz_XS);
+  if (c->oz_ecol) cudaFree(c->oz_ecol);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   delete c;
 }

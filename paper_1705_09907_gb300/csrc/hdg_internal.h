@@ -177,6 +177,15 @@ struct Context {
   bool uniform_kappa = false;
   __nv_bfloat16* shared_B = nullptr;        // [2][16][Kp] BF16
   bool shared_scaled = false;               // shared_B is S_ref (tau_K = kappa_K): scale by kappa_K
+  // FP64 shared-block apply by integer splitting (hdg_ozaki.cu): the block's
+  // BF16 slices [8][2][16][64] and exponent, the slices of X and the column
+  // exponents (scratch of the last nrhs, grown on demand)
+  uint16_t* oz_B = nullptr;
+  int oz_eS = 0;
+  void* oz_XS = nullptr;
+  size_t oz_xs_bytes = 0;
+  int* oz_ecol = nullptr;
+  int oz_ecol_n = 0;
 };
 
 // vectors of a V-cycle / apply in this precision are double (else float)
@@ -196,6 +205,9 @@ cudaError_t autotune_applies(Context* c, cudaStream_t s);
 // tensor-core batched apply of the shared block (hdg_batched.cu)
 cudaError_t prepare_shared_blocks(Context* c, double kappa0, cudaStream_t s);
 cudaError_t launch_batched_apply(Context* c, const void* X, float* Y, int nrhs, cudaStream_t s);
+// FP64 shared-block apply on the tensor cores by exact splitting (hdg_ozaki.cu)
+cudaError_t prepare_ozaki_blocks(Context* c, cudaStream_t s);
+cudaError_t launch_ozaki_apply(Context* c, const double* X, double* Y, int nrhs, cudaStream_t s);
 // one persistent launch over several contexts (apply_multi.cu); returns hdg_status
 int apply_multi(Context* const* ctx, int n, const void* const* x, void* const* y, int prec, cudaStream_t s);
 

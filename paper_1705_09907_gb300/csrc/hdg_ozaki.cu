@@ -1,0 +1,615 @@
+// FP64 shared-block batched apply on the BF16 tensor cores by exact integer
+// splitting (the Ozaki scheme), for a uniform coefficient: Y = A X with X, Y in
+// FP64 [ndof][nrhs], every S_K equal to one block S.
+//
+// Splitting. Column c of X is scaled by 2^-e_c (e_c the smallest integer with
+// |X[:, c]| < 2^e_c over the interior dofs) and written in fixed point with 56
+// fraction bits, F = trunc(|x| 2^(56 - e_c)) (integer operations on the FP64
+// bits), then cut into 8 slices of 7 bits, x = sign 2^e_c sum_t d_t 2^-7(t+1),
+// d_t in [-127, 127]; S likewise with one exponent e_S for the whole block
+// (set-up, host). Every slice is an integer that BF16 holds exactly, and for
+// each group g = t + u the sum over the pairs (t, u) of the products of slices
+// is an integer below 8 * 48 * 127^2 < 2^23, so the FP32 accumulation of the
+// MMAs is exact. The result is
+//   y = 2^(e_c + e_S - 63) sum_{g=0..7} D_g 2^7(7-g),   D_g = sum_{t+u=g} S_u X_t,
+// the pairs with t + u >= 8 (below 2^-56 of the scale) dropped; the sum is
+// formed as a 128-bit integer and rounded once to FP64 with integer operations
+// (no FP64 arithmetic on the slow FP64 pipe).
+//
+// Kernels: ozaki_exp_kernel (column exponents), ozaki_split_kernel (X -> 8 BF16
+// slice arrays, [8][ndof][nrhs]), ozaki_apply_kernel (persistent CTAs, one per
+// SM: items of 4 elements x 64 right-hand sides; for each slice t one TMA load
+// of its x window (the interior-edge tensor maps of the BF16 apply, with the
+// slice as a fifth dimension), then the MMAs of the pairs (t, u), u <= 7 - t,
+// into the accumulator of group t + u: 8 groups x 4 tiles x 16 columns = all
+// 512 TMEM columns; 8 drain warps combine the groups and store FP64 Y).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include "hdg_internal.h"
+
+namespace hdg {
+
+namespace {
+
+constexpr int kOzSlices = 8, kOzBits = 7;
+constexpr int kOzBS = 4;                           // elements per item
+constexpr int kOzRows = 5, kOzSlots = kOzBS + 2;   // window: 5 edge rows x 6 slots
+constexpr uint32_t kOzSlotB = 1024u, kOzRowB = kOzSlots * kOzSlotB, kOzWinB = kOzRows * kOzRowB;
+constexpr int kOzTileN = 16;
+constexpr uint32_t kOzTileB = kOzTileN * 64 * 2;   // one B tile (K = 64) in bytes
+enum { OV1 = 0, OV0 = 1, OHM = 2, OH0 = 3, OH1 = 4 };
+constexpr int kOzDrainWarps = 8;
+constexpr int kOzThreads = 32 * (kOzDrainWarps + 2);
+constexpr int kOzCols = 512;                       // 8 groups x 4 tiles x 16 columns
+
+struct OzArgs {
+  double* Y;                  // [ndof][nrhs]
+  const __nv_bfloat16* B;     // [8 slices][2 types][16][64] shared block slices
+  const int* ecol;            // [nrhs] column exponents
+  int eS;                     // exponent of the block
+  int nx, ny, n1, nrhs, spr, nseg;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t oz_su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t oz_desc(uint32_t addr, uint32_t lbo, uint32_t sbo, bool sw128) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3fff);
+  d |= (uint64_t)((lbo >> 4) & 0x3fff) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3fff) << 32;
+  d |= (uint64_t)1 << 46;
+  if (sw128) d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor: D F32, A and B BF16, A MN-major, B K-major,
+// N = 16, M = 128.
+constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(kOzTileN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ bool oz_try(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(oz_su32(bar)), "r"(parity), "r"(100000u)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait (~1 s of device time)
+__device__ __forceinline__ bool oz_wait(uint64_t* bar, unsigned parity) {
+  if (oz_try(bar, parity)) return true;
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+  for (unsigned it = 0;; ++it) {
+    if (oz_try(bar, parity)) return true;
+    if ((it & 15u) == 15u) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+      if (t - t0 > 1000000000ull) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void oz_named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// interior trace dof? (the trace is zero on boundary edges and they are ignored)
+__device__ __forceinline__ bool oz_interior_dof(size_t dof, int n1, int nx, int ny) {
+  const long e = (long)(dof / (size_t)n1);
+  const long nv = (long)(nx + 1) * ny;
+  if (e < nv) {
+    const int i = (int)(e % (nx + 1));
+    return i >= 1 && i <= nx - 1;
+  }
+  const int j = (int)((e - nv) / nx);
+  return j >= 1 && j <= ny - 1;
+}
+
+// e_c = 1 + the largest unbiased exponent in column c over the interior dofs,
+// so that |X[:, c]| < 2^e_c (entries below 2^-1022 count as zero). Each block
+// reduces 4 rows x 64 columns at a time, then one atomicMax per column.
+__global__ void ozaki_exp_kernel(const double* __restrict__ X, size_t ndof, int nrhs, int n1, int nx, int ny,
+                                 int* __restrict__ ecol) {
+  __shared__ int red[256];
+  const int tid = threadIdx.x, lc = tid & 63, rl = tid >> 6;
+  const int col = blockIdx.y * 64 + lc;
+  int emax = -4000;
+  for (size_t r = (size_t)blockIdx.x * 4 + rl; r < ndof; r += (size_t)gridDim.x * 4) {
+    if (!oz_interior_dof(r, n1, nx, ny)) continue;
+    const long long b = __double_as_longlong(X[r * nrhs + col]);
+    const int E = (int)((b >> 52) & 0x7ff);
+    if (E != 0) emax = max(emax, E - 1022);
+  }
+  red[tid] = emax;
+  __syncthreads();
+  if (rl == 0) {
+    const int e = max(max(red[lc], red[64 + lc]), max(red[128 + lc], red[192 + lc]));
+    atomicMax(&ecol[col], e);
+  }
+}
+
+// X -> 8 BF16 slices S_t[dof][col] (integers in [-127, 127]) of the 56-bit
+// fixed point F = trunc(|x| 2^(56 - e_c)), x ~ sign 2^e_c sum_t d_t 2^-7(t+1).
+// Boundary dofs are not written (the tensor maps never read them).
+__global__ void ozaki_split_kernel(const double* __restrict__ X, size_t ndof, int nrhs, int n1, int nx, int ny,
+                                   const int* __restrict__ ecol, __nv_bfloat16* __restrict__ XS) {
+  const size_t total = ndof * (size_t)nrhs, plane = total;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = idx / (size_t)nrhs;
+    if (!oz_interior_dof(r, n1, nx, ny)) continue;
+    const int col = (int)(idx - r * nrhs);
+    const long long b = __double_as_longlong(X[idx]);
+    const int E = (int)((b >> 52) & 0x7ff);
+    unsigned long long F = 0ull;
+    if (E != 0) {
+      const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | (1ull << 52);
+      const int s = E - 1019 - ecol[col];          // F = m 2^s, s <= 3
+      if (s >= 0) F = m << s;
+      else if (s > -64) F = m >> (-s);
+    }
+    const bool neg = b < 0;
+#pragma unroll
+    for (int t = 0; t < kOzSlices; ++t) {
+      const int d = (int)((F >> (kOzBits * (kOzSlices - 1 - t))) & 127ull);
+      XS[(size_t)t * plane + idx] = __float2bfloat16_rn((float)(neg ? -d : d));
+    }
+  }
+}
+
+// value T * 2^e rounded to the nearest FP64 (ties to even), T a signed 128-bit
+// integer with |T| < 2^100, by integer operations only
+__device__ __forceinline__ double oz_i128_to_double(__int128 T, int e) {
+  if (T == 0) return 0.0;
+  const bool neg = T < 0;
+  unsigned __int128 U = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+  const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long mant;
+  int shift = msb - 52;                             // value = mant 2^(shift + e), mant in [2^52, 2^53)
+  if (shift > 0) {
+    const unsigned __int128 q = U >> shift;
+    const unsigned __int128 rem = U - (q << shift);
+    const unsigned __int128 half = (unsigned __int128)1 << (shift - 1);
+    mant = (unsigned long long)q;
+    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+    if (mant == (1ull << 53)) { mant >>= 1; ++shift; }
+  } else {
+    mant = (unsigned long long)(U << (-shift));
+  }
+  // unbiased exponent msb + e, plus one if the rounding carried into 2^53
+  const int biased = msb + e + 1023 + (shift - (msb - 52));
+  if (biased >= 2047)                               // overflow: infinity
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | 0x7ff0000000000000ull));
+  if (biased <= 0) return neg ? -0.0 : 0.0;        // below the normal range: flushed
+  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
+                                  (mant & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+// One slice window (segment seg, right-hand sides chunk*64.., slice t) by five
+// TMA copies of the slice tensor maps (interior edges only; the rest reads as 0).
+__device__ __forceinline__ void oz_load_window(const OzArgs& a, const CUtensorMap* tv, const CUtensorMap* th,
+                                               unsigned char* W, int seg, int chunk, int t, uint64_t* bar) {
+  const int j = seg / a.spr, i0 = (seg % a.spr) * kOzBS;
+  const int x = chunk * 64;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(oz_su32(bar)), "r"(kOzWinB) : "memory");
+  const int rows[5] = {OV1, OV0, OHM, OH0, OH1};
+  const CUtensorMap* maps[5] = {tv, tv, th, th, th};
+  const int c2[5] = {i0 - 2, i0 - 2, i0 - 1, i0 - 1, i0 - 1};
+  const int c3[5] = {j - 1, j, j - 2, j - 1, j};
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+        ::"r"(oz_su32(W + rows[r] * kOzRowB)), "l"((uint64_t)maps[r]), "r"(x), "r"(0), "r"(c2[r]), "r"(c3[r]), "r"(t),
+        "r"(oz_su32(bar))
+        : "memory");
+}
+
+// The MMAs of the pairs (t, u), u = 0 .. 7 - t, for one loaded slice window:
+// 4 tiles (2 W face pairs, 2 S face pairs) x 4 K16 steps each, into group t + u
+// (TMEM columns 64 (t + u) + 16 tile). The first write of a group in an item is
+// at t = 0 (u = g), which overwrites.
+__device__ __forceinline__ void oz_issue(const unsigned char* W, const unsigned char* Bbuf, uint32_t tmem, int t) {
+  const uint64_t dslot = oz_desc(0u, kOzSlotB, kOzSlotB, true), drow = oz_desc(0u, kOzSlotB, kOzRowB, true);
+  const uint32_t wb4 = oz_su32(W) >> 4;
+  for (int u = 0; u + t < kOzSlices; ++u) {
+    const uint32_t gcol = (uint32_t)(64 * (t + u));
+#pragma unroll
+    for (int tile = 0; tile < 4; ++tile) {
+      const int type = tile >> 1, L = 2 * (tile & 1);
+      const int sl = L + 1;                                   // slot of the own element's W edge
+      const uint64_t bd0 = oz_desc(oz_su32(Bbuf + (uint32_t)(u * 2 + type) * kOzTileB), 128u, 1024u, false);
+      uint64_t ad[4];
+      ad[0] = dslot + wb4 + (uint32_t)(OV0 * kOzSlots + sl) * (kOzSlotB >> 4);
+      ad[1] = drow + wb4 + (uint32_t)(OH0 * kOzSlots + sl) * (kOzSlotB >> 4);
+      if (type == 0) {
+        ad[2] = dslot + wb4 + (uint32_t)(OV0 * kOzSlots + sl - 1) * (kOzSlotB >> 4);
+        ad[3] = drow + wb4 + (uint32_t)(OH0 * kOzSlots + sl - 1) * (kOzSlotB >> 4);
+      } else {
+        ad[2] = dslot + wb4 + (uint32_t)(OV1 * kOzSlots + sl) * (kOzSlotB >> 4);
+        ad[3] = drow + wb4 + (uint32_t)(OHM * kOzSlots + sl) * (kOzSlotB >> 4);
+      }
+      const uint32_t dcol = tmem + gcol + (uint32_t)(tile * kOzTileN);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const uint64_t bd = bd0 + (uint32_t)p * 16u;
+        const uint32_t acc = (t > 0 || p > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+            "l"(ad[p]), "l"(bd), "r"(kOzIdesc), "r"(acc)
+            : "memory");
+      }
+    }
+  }
+}
+
+// Drain of one item: warp w reads TMEM lane quadrant w % 4 (M rows 32(w%4)..:
+// face half s = row / 64, right-hand side row % 64) of tiles 2(w/4), 2(w/4)+1;
+// per output it sums the own and neighbour columns of every group as exact
+// integers into T = sum_g D_g 2^7(7-g) (two 64-bit halves) and rounds
+// T 2^(e_c + e_S - 63) to FP64.
+__device__ __forceinline__ void oz_drain(const OzArgs& a, uint32_t tmem, int seg, int chunk, int warp, int lane) {
+  const int n1 = a.n1;
+  const int nx = a.nx, ny = a.ny, nv = (nx + 1) * ny;
+  const int j = seg / a.spr, i0 = (seg % a.spr) * kOzBS;
+  const int quad = warp & 3;
+  const int mrow = quad * 32 + lane;
+  const int s = mrow >> 6, r = mrow & 63;
+  const int col = chunk * 64 + r;
+  const int escale = a.ecol[col] + a.eS - 63;
+  double* ybase = a.Y + col;
+  for (int tt = 0; tt < 2; ++tt) {
+    const int tile = 2 * (warp >> 2) + tt;
+    long long hi[8], lo[8];                 // T = hi 2^28 + lo, per output node
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { hi[q] = 0; lo[q] = 0; }
+#pragma unroll
+    for (int g = 0; g < kOzSlices; ++g) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(64 * g + tile * kOzTileN);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        // own part (column q) plus the neighbour's (column 8 + q): exact integers
+        const long long d = (long long)__float2int_rn(__uint_as_float(v[q])) +
+                            (long long)__float2int_rn(__uint_as_float(v[8 + q]));
+        if (g < 4) hi[q] += d << (kOzBits * (3 - g));
+        else lo[q] += d << (kOzBits * (7 - g));
+      }
+    }
+    const int type = tile >> 1;
+    const int i = i0 + 2 * (tile & 1) + s;
+    if (i >= nx) continue;
+    const bool bndrow = type == 0 ? (i == 0) : (j == 0);
+    const int eout = type == 0 ? i + (nx + 1) * j : nv + i + nx * j;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (q >= n1) break;
+      const __int128 T = ((__int128)hi[q] << 28) + (__int128)lo[q];
+      ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0 : oz_i128_to_double(T, escale);
+    }
+    if (type == 0 && i == nx - 1) {
+      const int eb = nx + (nx + 1) * j;
+      for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0;
+    }
+    if (type == 1 && j == ny - 1) {
+      const int eb = nv + i + nx * ny;
+      for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0;
+    }
+  }
+}
+
+// Persistent CTAs (one per SM: the 512 TMEM columns of the eight group
+// accumulators). Roles:
+//   warp 8 (one thread): the slice windows, in order (item, t), into buffer
+//     seq % 2 after the MMAs that read seq - 2 completed (window_free);
+//   warp 9 (one thread): per item, waits for the accumulators to be drained,
+//     then per slice waits for its window, issues its pairs' MMAs and commits
+//     them to window_free[buf]; after slice 7 commits to acc_full;
+//   drain warps 0..7: wait for acc_full, combine and store, release acc_free.
+// Every wait is bounded (1 s); before exit after a give-up the last copy and
+// commit on each barrier get one more bounded wait.
+__global__ void __launch_bounds__(kOzThreads)
+    ozaki_apply_kernel(OzArgs a, const __grid_constant__ CUtensorMap tv, const __grid_constant__ CUtensorMap th) {
+  extern __shared__ __align__(1024) unsigned char oz_raw[];
+  unsigned char* sm = oz_raw + ((1024u - (oz_su32(oz_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char* Bbuf = sm + 2 * kOzWinB;                                   // [8][2][tile]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bbuf + kOzSlices * 2 * kOzTileB);   // [2]
+  uint64_t* wfree = full + 2;                                                  // [2]
+  uint64_t* acc_full = wfree + 2;
+  uint64_t* acc_free = acc_full + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 1);
+  // [0] drain, [1] load, [2] issue gave up; [3] [4] loads per buffer; [5] [6]
+  // window commits per buffer; [7] accumulator commits
+  volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz_su32(tmem_slot)),
+                 "r"(kOzCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(full + q)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(wfree + q)) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(acc_full)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_su32(acc_free)), "r"(kOzDrainWarps) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < 8; ++q) flags[q] = 0;
+  }
+  if (tid == 32 * kOzDrainWarps) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tv) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&th) : "memory");
+  }
+  // the block slices, K-major without swizzle (core matrices of 8 n x 16 bytes)
+  for (int idx = tid; idx < kOzSlices * 2 * kOzTileN * 64; idx += kOzThreads) {
+    const int tb = idx / (kOzTileN * 64), rem = idx % (kOzTileN * 64);
+    const int n = rem / 64, k = rem % 64;
+    const uint32_t off = (uint32_t)(n >> 3) * 1024u + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u +
+                         (uint32_t)(k & 7) * 2u;
+    *reinterpret_cast<__nv_bfloat16*>(Bbuf + (uint32_t)tb * kOzTileB + off) = a.B[idx];
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const int chunks = a.nrhs / 64;
+  const long items = (long)a.nseg * chunks;
+  const long first = blockIdx.x, step = gridDim.x;
+
+  if (warp < kOzDrainWarps) {
+    unsigned pa = 0u;
+    for (long item = first; item < items; item += step) {
+      if (tid == 0 && !oz_wait(acc_full, pa)) flags[0] = 1;
+      oz_named_sync(1, 32 * kOzDrainWarps);
+      if (flags[0]) break;
+      pa ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      oz_drain(a, tmem, (int)(item / chunks), (int)(item % chunks), warp, lane);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(acc_free)) : "memory");
+    }
+  } else if (warp == kOzDrainWarps) {
+    if (lane == 0) {
+      unsigned pf[2] = {0u, 0u};
+      long seq = 0;
+      bool stop = false;
+      for (long item = first; item < items && !stop; item += step) {
+        for (int t = 0; t < kOzSlices; ++t, ++seq) {
+          const int buf = (int)(seq & 1);
+          if (seq >= 2) {     // the window was read by the MMAs of seq - 2
+            if (!oz_wait(wfree + buf, pf[buf])) { flags[1] = 1; stop = true; break; }
+            pf[buf] ^= 1u;
+          }
+          oz_load_window(a, &tv, &th, sm + (buf ? kOzWinB : 0u), (int)(item / chunks), (int)(item % chunks), t,
+                         full + buf);
+          flags[3 + buf] = flags[3 + buf] + 1;
+        }
+      }
+    }
+  } else if (lane == 0) {
+    unsigned pw[2] = {0u, 0u}, pfree = 0u;
+    long seq = 0, n = 0;
+    bool stop = false;
+    for (long item = first; item < items && !stop; item += step, ++n) {
+      if (n >= 1) {           // the accumulators of item n - 1 were drained
+        if (!oz_wait(acc_free, pfree)) { flags[2] = 1; break; }
+        pfree ^= 1u;
+      }
+      for (int t = 0; t < kOzSlices; ++t, ++seq) {
+        const int buf = (int)(seq & 1);
+        if (!oz_wait(full + buf, pw[buf])) { flags[2] = 1; stop = true; break; }
+        pw[buf] ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        oz_issue(sm + (buf ? kOzWinB : 0u), Bbuf, tmem, t);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         oz_su32(wfree + buf))
+                     : "memory");
+        flags[5 + buf] = flags[5 + buf] + 1;
+      }
+      if (stop) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       oz_su32(acc_full))
+                   : "memory");
+      flags[7] = flags[7] + 1;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (flags[0] || flags[1] || flags[2]) {
+    if (tid == 0) {
+      atomicExch(a.err, 2);
+      for (int q = 0; q < 2; ++q) {
+        if (flags[3 + q] > 0) (void)oz_wait(full + q, (unsigned)((flags[3 + q] - 1) & 1));
+        if (flags[5 + q] > 0) (void)oz_wait(wfree + q, (unsigned)((flags[5 + q] - 1) & 1));
+      }
+      if (flags[7] > 0) (void)oz_wait(acc_full, (unsigned)((flags[7] - 1) & 1));
+    }
+    __syncthreads();
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzCols) : "memory");
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+
+static PFN_cuTensorMapEncodeTiled_v12000 oz_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// The BF16 block slices [8][2][16][64] of the shared block S (m x m, row-major,
+// host) and its exponent: S / 2^e_S in 56-bit fixed point, 7 bits per slice,
+// laid out like the BF16 apply's block (own element's rows 0..7, neighbour's
+// 8..15, K = own (W, E), own (S, N), neighbour (W, E), neighbour (S, N)).
+static void oz_block_slices(const std::vector<double>& S, int n1, std::vector<uint16_t>& B, int& eS) {
+  const int m = 4 * n1;
+  double mx = 0.0;
+  for (double v : S) mx = std::max(mx, std::fabs(v));
+  int e = 0;
+  if (mx > 0.0) std::frexp(mx, &e);                 // mx < 2^e
+  eS = e;
+  B.assign((size_t)kOzSlices * 2 * kOzTileN * 64, 0);
+  for (int u = 0; u < kOzSlices; ++u)
+    for (int ty = 0; ty < 2; ++ty)
+      for (int n = 0; n < kOzTileN; ++n)
+        for (int k = 0; k < 64; ++k) {
+          const int step = k >> 4, h = (k >> 3) & 1, nd = k & 7;
+          const bool nb_part = n >= kOzTileN / 2;
+          const int row = n & (kOzTileN / 2 - 1);
+          if (row >= n1 || nd >= n1 || nb_part != (step >= 2)) continue;
+          const int own_face = ty == 0 ? 0 : 2, nb_face = ty == 0 ? 1 : 3;
+          const int row_face = step < 2 ? own_face : nb_face;
+          const int col_face = (step & 1) * 2 + h;
+          const double v = S[(size_t)(row_face * n1 + row) * m + col_face * n1 + nd];
+          const unsigned long long F = (unsigned long long)std::ldexp(std::fabs(v), 56 - eS);   // truncates
+          const int d = (int)((F >> (kOzBits * (kOzSlices - 1 - u))) & 127ull);
+          const float f = (float)(v < 0 ? -d : d);      // an integer of at most 7 bits: exact in BF16
+          uint32_t fb;
+          std::memcpy(&fb, &f, sizeof(fb));
+          B[(((size_t)u * 2 + ty) * kOzTileN + n) * 64 + k] = (uint16_t)(fb >> 16);
+        }
+}
+
+cudaError_t prepare_ozaki_blocks(Context* c, cudaStream_t s) {
+  const int n1 = c->k + 1, m = 4 * n1;
+  if (n1 > kOzTileN / 2) return cudaSuccess;
+  std::vector<double> S((size_t)m * m);
+  HDG_CUDA_TRY(cudaMemcpyAsync(S.data(), c->plev[c->k].Sdense, S.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HDG_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<uint16_t> B;
+  oz_block_slices(S, n1, B, c->oz_eS);
+  HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->oz_B, B.size() * sizeof(uint16_t)));
+  HDG_CUDA_TRY(cudaMemcpyAsync(c->oz_B, B.data(), B.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+  return cudaStreamSynchronize(s);
+}
+
+static cudaError_t oz_maps(const Context* c, const void* XS, int nrhs, CUtensorMap* tv, CUtensorMap* th) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = oz_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const int nx = c->mesh.nx, ny = c->mesh.ny, n1 = c->k + 1;
+  const cuuint64_t rowB = (cuuint64_t)nrhs * 2, edgeB = rowB * n1;
+  const cuuint64_t plane = (cuuint64_t)c->ndof * nrhs * 2;
+  const size_t nv = (size_t)(nx + 1) * ny;
+  const cuuint32_t box[5] = {64, 8, (cuuint32_t)kOzSlots, 1, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  {
+    char* base = (char*)XS + edgeB;
+    const cuuint64_t dims[5] = {(cuuint64_t)nrhs, (cuuint64_t)n1, (cuuint64_t)(nx - 1), (cuuint64_t)ny,
+                                (cuuint64_t)kOzSlices};
+    const cuuint64_t str[4] = {rowB, edgeB, edgeB * (cuuint64_t)(nx + 1), plane};
+    if (enc(tv, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    char* base = (char*)XS + edgeB * (cuuint64_t)(nv + (size_t)nx);
+    const cuuint64_t dims[5] = {(cuuint64_t)nrhs, (cuuint64_t)n1, (cuuint64_t)nx, (cuuint64_t)(ny - 1),
+                                (cuuint64_t)kOzSlices};
+    const cuuint64_t str[4] = {rowB, edgeB, edgeB * (cuuint64_t)nx, plane};
+    if (enc(th, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+size_t ozaki_smem_bytes() {
+  // two slice windows, the block slices, barriers + TMEM slot + flags, alignment
+  // slack; at least 120 KB so that one CTA holds an SM (and all 512 TMEM columns)
+  const size_t need = (size_t)2 * kOzWinB + (size_t)kOzSlices * 2 * kOzTileB + 128 + 1024;
+  return need > 120 * 1024 ? need : 120 * 1024;
+}
+
+cudaError_t launch_ozaki_apply(Context* c, const double* X, double* Y, int nrhs, cudaStream_t s) {
+  if (!c->oz_B || c->k + 1 > 8 || c->mesh.nx < 2 || c->mesh.ny < 2) return cudaErrorInvalidValue;
+  const size_t ndof = (size_t)c->ndof;
+  // scratch: the slices [8][ndof][nrhs] BF16 and the column exponents
+  const size_t xs_bytes = (size_t)kOzSlices * ndof * nrhs * 2;
+  if (c->opt.max_device_bytes && c->oz_xs_bytes < xs_bytes &&
+      c->bytes + xs_bytes + (size_t)nrhs * sizeof(int) > c->opt.max_device_bytes)
+    return cudaErrorMemoryAllocation;                 // the context's memory cap
+  if (c->oz_xs_bytes < xs_bytes) {
+    if (c->oz_XS) { cudaFree(c->oz_XS); c->oz_XS = nullptr; c->oz_xs_bytes = 0; }
+    HDG_CUDA_TRY(cudaMalloc(&c->oz_XS, xs_bytes));
+    c->oz_xs_bytes = xs_bytes;
+  }
+  if (c->oz_ecol_n < nrhs) {
+    if (c->oz_ecol) { cudaFree(c->oz_ecol); c->oz_ecol = nullptr; c->oz_ecol_n = 0; }
+    HDG_CUDA_TRY(cudaMalloc((void**)&c->oz_ecol, (size_t)nrhs * sizeof(int)));
+    c->oz_ecol_n = nrhs;
+  }
+  HDG_CUDA_TRY(cudaMemsetAsync(c->oz_ecol, 0x80, (size_t)nrhs * sizeof(int), s));   // very negative
+  {
+    long bx = (long)((ndof + 3) / 4);
+    if (bx > (long)c->num_sms * 2) bx = (long)c->num_sms * 2;
+    dim3 grid((unsigned)bx, (unsigned)(nrhs / 64));
+    ozaki_exp_kernel<<<grid, 256, 0, s>>>(X, ndof, nrhs, c->k + 1, c->mesh.nx, c->mesh.ny, c->oz_ecol);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    size_t b = (ndof * nrhs + 255) / 256;
+    const size_t cap = (size_t)c->num_sms * 16;
+    if (b > cap) b = cap;
+    ozaki_split_kernel<<<(unsigned)b, 256, 0, s>>>(X, ndof, nrhs, c->k + 1, c->mesh.nx, c->mesh.ny, c->oz_ecol,
+                                                   (__nv_bfloat16*)c->oz_XS);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  alignas(64) CUtensorMap tv, th;
+  HDG_CUDA_TRY(oz_maps(c, c->oz_XS, nrhs, &tv, &th));
+  OzArgs a{};
+  a.Y = Y; a.B = (const __nv_bfloat16*)c->oz_B; a.ecol = c->oz_ecol; a.eS = c->oz_eS;
+  a.nx = c->mesh.nx; a.ny = c->mesh.ny; a.n1 = c->k + 1; a.nrhs = nrhs;
+  a.spr = (c->mesh.nx + kOzBS - 1) / kOzBS; a.nseg = a.spr * c->mesh.ny; a.err = c->err_flag;
+  const size_t smem = ozaki_smem_bytes();
+  if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
+  HDG_CUDA_TRY(cudaFuncSetAttribute(ozaki_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long items = (long)a.nseg * (nrhs / 64);
+  long blocks = c->num_sms;
+  if (blocks > items) blocks = items;
+  ozaki_apply_kernel<<<(int)blocks, kOzThreads, smem, s>>>(a, tv, th);
+  return cudaGetLastError();
+}
+
+}  // namespace hdg

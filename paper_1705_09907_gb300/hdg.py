@@ -80,6 +80,7 @@ def _load():
         "hdg_adjoint_grad": (i, [vp, vp, vp, vp, d, i, vp, vp, vp, vp, vp]),
         "hdg_condense_rhs_noalloc": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_shared_batched": (i, [vp, vp, vp, i, vp]),
+        "hdg_apply_shared_fp64": (i, [vp, vp, vp, i, vp]),
         "hdg_apply_multi": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]),
         "hdg_setup_batch": (i, [i, ctypes.POINTER(hdg_mesh), ctypes.POINTER(i), ctypes.POINTER(vp),
                                 ctypes.POINTER(hdg_options), vp, ctypes.POINTER(vp)]),
@@ -112,6 +113,7 @@ hdg_fmg = _lib.hdg_fmg
 hdg_adjoint_grad = _lib.hdg_adjoint_grad
 hdg_condense_rhs_noalloc = _lib.hdg_condense_rhs_noalloc
 hdg_apply_shared_batched = _lib.hdg_apply_shared_batched
+hdg_apply_shared_fp64 = _lib.hdg_apply_shared_fp64
 hdg_apply_multi = _lib.hdg_apply_multi
 hdg_setup_batch = _lib.hdg_setup_batch
 hdg_solve_multi = _lib.hdg_solve_multi
@@ -280,6 +282,16 @@ class HDGSolver:
         Y = torch.empty(X.shape, dtype=torch.float32, device="cuda") if out is None else out
         _check(_lib.hdg_apply_shared_batched(self.ctx, _ptr(X), _ptr(Y, torch.float32), X.shape[1], _stream()),
                "hdg_apply_shared_batched")
+        return Y
+
+    def apply_shared_fp64(self, X, out=None):
+        """Y = A X in FP64 for a uniform coefficient on the tensor cores (exact
+        slice splitting): X, Y float64 [ndof, nrhs], nrhs a multiple of 64."""
+        if X.dtype != torch.float64 or X.dim() != 2:
+            raise ValueError("X must be a 2-D float64 CUDA tensor [ndof, nrhs]")
+        Y = torch.empty_like(X) if out is None else out
+        _check(_lib.hdg_apply_shared_fp64(self.ctx, _ptr(X), _ptr(Y, torch.float64), X.shape[1], _stream()),
+               "hdg_apply_shared_fp64")
         return Y
 
     def vcycle(self, r, prec="fp64", out=None):
