@@ -120,6 +120,15 @@ typedef struct {
                                  (f - A x), G lower triangular on the pattern
                                  of the level operator, unit diagonal of
                                  G A G^T                                      */
+  int tensor_apply;           /* 1: hdg_solve with nrhs a multiple of 64 (at
+                                 most 2048) applies the outer operator of the
+                                 batched CG on the tensor cores in FP64 by
+                                 exact slice splitting (hdg_apply_shared_fp64)
+                                 when every element shares one block (uniform
+                                 kappa, tau not tied to kappa, k <= 7); its
+                                 slices of the CG direction are scratch of the
+                                 context (16 bytes per entry); 0: the CUDA-core
+                                 column kernels (1)                           */
   int fmg_start;              /* hdg_solve with one right-hand side starts CG
                                  from one full multigrid cycle (Sec. 7) with
                                  this many V-cycles per level instead of from

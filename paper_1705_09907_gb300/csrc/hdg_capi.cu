@@ -50,7 +50,7 @@ void hdg_default_options(hdg_options* o) {
   if (!o) return;
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
   o->autotune = 1; o->reduced = 1; o->tau_kappa = 0;
-  o->smoother = 0; o->fmg_start = 0; o->max_device_bytes = 0; o->wait_probe = 0;
+  o->smoother = 0; o->tensor_apply = 1; o->fmg_start = 0; o->max_device_bytes = 0; o->wait_probe = 0;
 }
 
 const char* hdg_error_string(int s) {
@@ -243,7 +243,8 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
   if (o.nu1 < 1 || o.nu2 < 1 || o.nu1 > 16 || o.nu2 > 16 || o.coarse_n < 2 || !(o.tau > 0.0) ||
       o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2 ||
       o.tau_kappa < 0 || o.tau_kappa > 1 || o.wait_probe < 0 || o.wait_probe > 64 || o.smoother < 0 ||
-      o.smoother > 1 || o.fmg_start < 0 || o.fmg_start > 16)
+      o.smoother > 1 || o.fmg_start < 0 || o.fmg_start > 16 ||
+      o.tensor_apply < 0 || o.tensor_apply > 1)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);

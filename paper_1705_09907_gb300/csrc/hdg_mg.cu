@@ -1447,6 +1447,7 @@ int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rto
   double* h = w->h_sc;
   const bool flexible = inner != HDG_PREC_FP64;
   const int outer = (inner == HDG_PREC_FP64) ? HDG_PREC_FP64 : HDG_PREC_F32X2;
+  const bool use_tc = c->opt.tensor_apply && c->oz_B && nb % 64 == 0 && nb <= 2048;
   auto S = [&](int slot) { return sc + (size_t)slot * nb; };
 #define CK(expr) do { cudaError_t _e = (expr); if (_e != cudaSuccess) return HDG_ERR_CUDA; } while (0)
   CK(cudaMemsetAsync(x, 0, n * sizeof(double), s));
@@ -1462,7 +1463,10 @@ int pcg_solve_batched(Context* c, const double* b, double* x, int nb, double rto
   double relmax = 0.0;
   int status = HDG_ERR_NOT_CONVERGED;
   for (it = 1; it <= maxit; ++it) {
-    CK(launch_apply(c, c->k, 0, outer, p, nullptr, q, 1.0, 0.0, nb, s));
+    // the outer operator on the tensor cores (FP64 by exact slice splitting) when
+    // every element shares one block and the columns come in groups of 64
+    if (use_tc) CK(launch_ozaki_apply(c, p, q, nb, s));
+    else CK(launch_apply(c, c->k, 0, outer, p, nullptr, q, 1.0, 0.0, nb, s));
     CK(cdots(w, (size_t)c->ndof, p, q, nullptr, nullptr, S(kPq), nullptr, s));
     cgb_alpha_kernel<<<gs, 256, 0, s>>>(nb, sc);
     CK(cudaGetLastError());

@@ -9,7 +9,7 @@
 // d_t in [-127, 127]; S likewise with one exponent e_S for the whole block
 // (set-up, host). Every slice is an integer that BF16 holds exactly, and for
 // each group g = t + u the sum over the pairs (t, u) of the products of slices
-// is an integer below 8 * 48 * 127^2 < 2^23, so the FP32 accumulation of the
+// is an integer below 8 * 64 * 127^2 < 2^23, so the FP32 accumulation of the
 // MMAs is exact. The result is
 //   y = 2^(e_c + e_S - 63) sum_{g=0..7} D_g 2^7(7-g),   D_g = sum_{t+u=g} S_u X_t,
 // the pairs with t + u >= 8 (below 2^-56 of the scale) dropped; the sum is
@@ -21,8 +21,10 @@
 // SM: items of 4 elements x 64 right-hand sides; for each slice t one TMA load
 // of its x window (the interior-edge tensor maps of the BF16 apply, with the
 // slice as a fifth dimension), then the MMAs of the pairs (t, u), u <= 7 - t,
-// into the accumulator of group t + u: 8 groups x 4 tiles x 16 columns = all
-// 512 TMEM columns; 8 drain warps combine the groups and store FP64 Y).
+// into the accumulator of group t + u (one MMA per tile and K step covers all
+// pairs of a slice: the block slices are stacked along N); two accumulator sets
+// of 4 tiles x 8 groups x 8 columns fill the 512 TMEM columns, so 8 drain warps
+// combine the groups of one item and store FP64 Y while the next item's MMAs run).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -43,11 +45,15 @@ constexpr int kOzBS = 4;                           // elements per item
 constexpr int kOzRows = 5, kOzSlots = kOzBS + 2;   // window: 5 edge rows x 6 slots
 constexpr uint32_t kOzSlotB = 1024u, kOzRowB = kOzSlots * kOzSlotB, kOzWinB = kOzRows * kOzRowB;
 constexpr int kOzTileN = 16;
-constexpr uint32_t kOzTileB = kOzTileN * 64 * 2;   // one B tile (K = 64) in bytes
 enum { OV1 = 0, OV0 = 1, OHM = 2, OH0 = 3, OH1 = 4 };
 constexpr int kOzDrainWarps = 8;
 constexpr int kOzThreads = 32 * (kOzDrainWarps + 2);
-constexpr int kOzCols = 512;                       // 8 groups x 4 tiles x 16 columns
+constexpr int kOzGroupN = 8;                         // TMEM columns per group (k + 1 <= 8 outputs)
+constexpr int kOzTileCols = kOzSlices * kOzGroupN;   // 64 TMEM columns per tile: 8 groups x 8
+constexpr int kOzAccCols = 4 * kOzTileCols;          // one accumulator set: 4 tiles, 256 columns
+constexpr int kOzCols = 2 * kOzAccCols;              // two sets (double-buffered): all 512 TMEM columns
+constexpr int kOzBRows = 8 + kOzSlices * kOzGroupN;  // per face type: 8 zero rows, then slice u at 8 + 8u
+constexpr uint32_t kOzTypeB = (uint32_t)(kOzBRows / 8) * 1024u;   // 9 core-matrix groups of 8 rows
 
 struct OzArgs {
   double* Y;                  // [ndof][nrhs]
@@ -70,10 +76,6 @@ __device__ __forceinline__ uint64_t oz_desc(uint32_t addr, uint32_t lbo, uint32_
   return d;
 }
 
-// kind::f16 instruction descriptor: D F32, A and B BF16, A MN-major, B K-major,
-// N = 16, M = 128.
-constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(kOzTileN >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
 
 __device__ __forceinline__ bool oz_try(uint64_t* bar, unsigned parity) {
   uint32_t ok;
@@ -117,53 +119,90 @@ __device__ __forceinline__ bool oz_interior_dof(size_t dof, int n1, int nx, int 
 }
 
 // e_c = 1 + the largest unbiased exponent in column c over the interior dofs,
-// so that |X[:, c]| < 2^e_c (entries below 2^-1022 count as zero). Each block
-// reduces 4 rows x 64 columns at a time, then one atomicMax per column.
+// so that |X[:, c]| < 2^e_c (entries below 2^-1022 count as zero). A thread
+// takes 8 consecutive columns of a row (one 64-byte read); a block covers 256 / g
+// rows at a time (g = nrhs / 8 threads per row), reduces in shared memory, and
+// then issues one atomicMax per column.
 __global__ void ozaki_exp_kernel(const double* __restrict__ X, size_t ndof, int nrhs, int n1, int nx, int ny,
                                  int* __restrict__ ecol) {
-  __shared__ int red[256];
-  const int tid = threadIdx.x, lc = tid & 63, rl = tid >> 6;
-  const int col = blockIdx.y * 64 + lc;
-  int emax = -4000;
-  for (size_t r = (size_t)blockIdx.x * 4 + rl; r < ndof; r += (size_t)gridDim.x * 4) {
-    if (!oz_interior_dof(r, n1, nx, ny)) continue;
-    const long long b = __double_as_longlong(X[r * nrhs + col]);
-    const int E = (int)((b >> 52) & 0x7ff);
-    if (E != 0) emax = max(emax, E - 1022);
+  __shared__ int red[256 * 8];
+  const int g = nrhs / 8, tid = threadIdx.x;
+  const int cg = tid % g, rl = tid / g, rows = 256 / g;
+  int emax[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) emax[q] = -4000;
+  if (rl < rows) {
+    for (size_t r = (size_t)blockIdx.x * rows + rl; r < ndof; r += (size_t)gridDim.x * rows) {
+      if (!oz_interior_dof(r, n1, nx, ny)) continue;
+      // four 16-byte loads (X is 16-byte aligned)
+      const longlong2* src = reinterpret_cast<const longlong2*>(X + r * nrhs + cg * 8);
+      const longlong2 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
+      const long long b[8] = {v0.x, v0.y, v1.x, v1.y, v2.x, v2.y, v3.x, v3.y};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int E = (int)((b[q] >> 52) & 0x7ff);
+        if (E != 0) emax[q] = max(emax[q], E - 1022);
+      }
+    }
   }
-  red[tid] = emax;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) red[tid * 8 + q] = emax[q];
   __syncthreads();
-  if (rl == 0) {
-    const int e = max(max(red[lc], red[64 + lc]), max(red[128 + lc], red[192 + lc]));
-    atomicMax(&ecol[col], e);
+  // thread c < nrhs reduces column c over the block's row lanes
+  for (int c = tid; c < nrhs; c += blockDim.x) {
+    const int cgc = c / 8, q = c % 8;
+    int e = -4000;
+    for (int r = 0; r < rows; ++r) e = max(e, red[(r * g + cgc) * 8 + q]);
+    atomicMax(&ecol[c], e);
   }
 }
 
 // X -> 8 BF16 slices S_t[dof][col] (integers in [-127, 127]) of the 56-bit
 // fixed point F = trunc(|x| 2^(56 - e_c)), x ~ sign 2^e_c sum_t d_t 2^-7(t+1).
-// Boundary dofs are not written (the tensor maps never read them).
+// A thread takes 8 consecutive columns of a row: one 64-byte read, then one
+// 16-byte store per slice. Boundary dofs are not written (the tensor maps never
+// read them).
 __global__ void ozaki_split_kernel(const double* __restrict__ X, size_t ndof, int nrhs, int n1, int nx, int ny,
                                    const int* __restrict__ ecol, __nv_bfloat16* __restrict__ XS) {
-  const size_t total = ndof * (size_t)nrhs, plane = total;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+  const int g = nrhs / 8;
+  const size_t plane = ndof * (size_t)nrhs, groups = ndof * (size_t)g;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < groups;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = idx / (size_t)nrhs;
+    const size_t r = idx / (size_t)g;
     if (!oz_interior_dof(r, n1, nx, ny)) continue;
-    const int col = (int)(idx - r * nrhs);
-    const long long b = __double_as_longlong(X[idx]);
-    const int E = (int)((b >> 52) & 0x7ff);
-    unsigned long long F = 0ull;
-    if (E != 0) {
-      const unsigned long long m = ((unsigned long long)b & 0xfffffffffffffull) | (1ull << 52);
-      const int s = E - 1019 - ecol[col];          // F = m 2^s, s <= 3
-      if (s >= 0) F = m << s;
-      else if (s > -64) F = m >> (-s);
+    const int c0 = (int)(idx - r * g) * 8;
+    const size_t off = r * nrhs + c0;
+    const longlong2* src = reinterpret_cast<const longlong2*>(X + off);   // X is 16-byte aligned
+    const longlong2 v0 = src[0], v1 = src[1], v2 = src[2], v3 = src[3];
+    const long long b[8] = {v0.x, v0.y, v1.x, v1.y, v2.x, v2.y, v3.x, v3.y};
+    unsigned long long F[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int E = (int)((b[q] >> 52) & 0x7ff);
+      F[q] = 0ull;
+      if (E != 0) {
+        const unsigned long long m = ((unsigned long long)b[q] & 0xfffffffffffffull) | (1ull << 52);
+        const int s = E - 1019 - ecol[c0 + q];         // F = m 2^s, s <= 3
+        if (s >= 0) F[q] = m << s;
+        else if (s > -64) F[q] = m >> (-s);
+      }
     }
-    const bool neg = b < 0;
 #pragma unroll
     for (int t = 0; t < kOzSlices; ++t) {
-      const int d = (int)((F >> (kOzBits * (kOzSlices - 1 - t))) & 127ull);
-      XS[(size_t)t * plane + idx] = __float2bfloat16_rn((float)(neg ? -d : d));
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        uint32_t pair = 0u;
+#pragma unroll
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int q = 2 * h + e2;
+          const int d = (int)((F[q] >> (kOzBits * (kOzSlices - 1 - t))) & 127ull);
+          const __nv_bfloat16 bv = __float2bfloat16_rn((float)(b[q] < 0 ? -d : d));
+          pair |= (uint32_t)__bfloat16_as_ushort(bv) << (16 * e2);
+        }
+        w[h] = pair;
+      }
+      *reinterpret_cast<uint4*>(XS + (size_t)t * plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }
@@ -218,48 +257,56 @@ __device__ __forceinline__ void oz_load_window(const OzArgs& a, const CUtensorMa
         : "memory");
 }
 
-// The MMAs of the pairs (t, u), u = 0 .. 7 - t, for one loaded slice window:
-// 4 tiles (2 W face pairs, 2 S face pairs) x 4 K16 steps each, into group t + u
-// (TMEM columns 64 (t + u) + 16 tile). The first write of a group in an item is
-// at t = 0 (u = g), which overwrites.
+// The MMAs of the pairs (t, u), u = 0 .. 7 - t, for one loaded slice window.
+// The block slices are stacked along N behind 8 zero rows (slice u at rows
+// 8 + 8u .. 8 + 8u + 7, the own element's and the neighbour's rows summed into
+// the same 8 outputs), so one MMA writes pair (t, u) to TMEM columns 8 (t + u) of
+// the tile's 64 (group g = t + u in the same place for every t): N = 8 (8 - t)
+// from B row 8 at column 8t, or, when 8 - t is odd (N must be a multiple of 16),
+// N = 8 (9 - t) from the zero rows at column 8 (t - 1), which adds 0 to the
+// finished group t - 1. Per tile (2 W face pairs, 2 S face pairs) 4 K16 steps.
+// Slice 0 (N = 64) writes every group first and overwrites.
 __device__ __forceinline__ void oz_issue(const unsigned char* W, const unsigned char* Bbuf, uint32_t tmem, int t) {
   const uint64_t dslot = oz_desc(0u, kOzSlotB, kOzSlotB, true), drow = oz_desc(0u, kOzSlotB, kOzRowB, true);
   const uint32_t wb4 = oz_su32(W) >> 4;
-  for (int u = 0; u + t < kOzSlices; ++u) {
-    const uint32_t gcol = (uint32_t)(64 * (t + u));
+  const bool odd = ((kOzSlices - t) & 1) != 0;
+  const uint32_t ncols = (uint32_t)(kOzGroupN * (kOzSlices - t + (odd ? 1 : 0)));
+  const uint32_t col0 = (uint32_t)(kOzGroupN * (t - (odd ? 1 : 0)));
+  const uint32_t brow0 = odd ? 0u : 1024u;          // zero rows first, or slice 0 first
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((ncols >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
 #pragma unroll
-    for (int tile = 0; tile < 4; ++tile) {
-      const int type = tile >> 1, L = 2 * (tile & 1);
-      const int sl = L + 1;                                   // slot of the own element's W edge
-      const uint64_t bd0 = oz_desc(oz_su32(Bbuf + (uint32_t)(u * 2 + type) * kOzTileB), 128u, 1024u, false);
-      uint64_t ad[4];
-      ad[0] = dslot + wb4 + (uint32_t)(OV0 * kOzSlots + sl) * (kOzSlotB >> 4);
-      ad[1] = drow + wb4 + (uint32_t)(OH0 * kOzSlots + sl) * (kOzSlotB >> 4);
-      if (type == 0) {
-        ad[2] = dslot + wb4 + (uint32_t)(OV0 * kOzSlots + sl - 1) * (kOzSlotB >> 4);
-        ad[3] = drow + wb4 + (uint32_t)(OH0 * kOzSlots + sl - 1) * (kOzSlotB >> 4);
-      } else {
-        ad[2] = dslot + wb4 + (uint32_t)(OV1 * kOzSlots + sl) * (kOzSlotB >> 4);
-        ad[3] = drow + wb4 + (uint32_t)(OHM * kOzSlots + sl) * (kOzSlotB >> 4);
-      }
-      const uint32_t dcol = tmem + gcol + (uint32_t)(tile * kOzTileN);
+  for (int tile = 0; tile < 4; ++tile) {
+    const int type = tile >> 1, L = 2 * (tile & 1);
+    const int sl = L + 1;                                     // slot of the own element's W edge
+    const uint64_t bd0 = oz_desc(oz_su32(Bbuf + (uint32_t)type * kOzTypeB + brow0), 128u, 1024u, false);
+    uint64_t ad[4];
+    ad[0] = dslot + wb4 + (uint32_t)(OV0 * kOzSlots + sl) * (kOzSlotB >> 4);
+    ad[1] = drow + wb4 + (uint32_t)(OH0 * kOzSlots + sl) * (kOzSlotB >> 4);
+    if (type == 0) {
+      ad[2] = dslot + wb4 + (uint32_t)(OV0 * kOzSlots + sl - 1) * (kOzSlotB >> 4);
+      ad[3] = drow + wb4 + (uint32_t)(OH0 * kOzSlots + sl - 1) * (kOzSlotB >> 4);
+    } else {
+      ad[2] = dslot + wb4 + (uint32_t)(OV1 * kOzSlots + sl) * (kOzSlotB >> 4);
+      ad[3] = drow + wb4 + (uint32_t)(OHM * kOzSlots + sl) * (kOzSlotB >> 4);
+    }
+    const uint32_t dcol = tmem + (uint32_t)(tile * kOzTileCols) + col0;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const uint64_t bd = bd0 + (uint32_t)p * 16u;
-        const uint32_t acc = (t > 0 || p > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
-            "l"(ad[p]), "l"(bd), "r"(kOzIdesc), "r"(acc)
-            : "memory");
-      }
+    for (int p = 0; p < 4; ++p) {
+      const uint64_t bd = bd0 + (uint32_t)p * 16u;
+      const uint32_t acc = (t > 0 || p > 0) ? 1u : 0u;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dcol),
+          "l"(ad[p]), "l"(bd), "r"(idesc), "r"(acc)
+          : "memory");
     }
   }
 }
 
-// Drain of one item: warp w reads TMEM lane quadrant w % 4 (M rows 32(w%4)..:
-// face half s = row / 64, right-hand side row % 64) of tiles 2(w/4), 2(w/4)+1;
-// per output it sums the own and neighbour columns of every group as exact
+// Drain of one item from the accumulator set at `tmem`: warp w reads TMEM lane
+// quadrant w % 4 (M rows 32(w%4)..: face half s = row / 64, right-hand side
+// row % 64) of tiles 2(w/4), 2(w/4)+1; per output it sums the groups as exact
 // integers into T = sum_g D_g 2^7(7-g) (two 64-bit halves) and rounds
 // T 2^(e_c + e_S - 63) to FP64.
 __device__ __forceinline__ void oz_drain(const OzArgs& a, uint32_t tmem, int seg, int chunk, int warp, int lane) {
@@ -274,27 +321,33 @@ __device__ __forceinline__ void oz_drain(const OzArgs& a, uint32_t tmem, int seg
   double* ybase = a.Y + col;
   for (int tt = 0; tt < 2; ++tt) {
     const int tile = 2 * (warp >> 2) + tt;
-    long long hi[8], lo[8];                 // T = hi 2^28 + lo, per output node
+    // per output node: P[m] = D_2m 2^7 + D_2m+1 (exact in 32 bits: |D| < 2^23)
+    int P[4][8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { hi[q] = 0; lo[q] = 0; }
-#pragma unroll
-    for (int g = 0; g < kOzSlices; ++g) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(64 * g + tile * kOzTileN);
+    for (int half = 0; half < 2; ++half) {  // groups 4 half .. 4 half + 3: 32 columns
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tile * kOzTileCols + 32 * half);
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
           : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        // own part (column q) plus the neighbour's (column 8 + q): exact integers
-        const long long d = (long long)__float2int_rn(__uint_as_float(v[q])) +
-                            (long long)__float2int_rn(__uint_as_float(v[8 + q]));
-        if (g < 4) hi[q] += d << (kOzBits * (3 - g));
-        else lo[q] += d << (kOzBits * (7 - g));
+      for (int pp = 0; pp < 2; ++pp) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q >= n1) break;
+          // exact integers below 2^23 (own and neighbour parts summed by the MMA)
+          const int d0 = __float2int_rn(__uint_as_float(v[kOzGroupN * (2 * pp) + q]));
+          const int d1 = __float2int_rn(__uint_as_float(v[kOzGroupN * (2 * pp + 1) + q]));
+          P[2 * half + pp][q] = d0 * (1 << kOzBits) + d1;
+        }
       }
     }
     const int type = tile >> 1;
@@ -305,7 +358,10 @@ __device__ __forceinline__ void oz_drain(const OzArgs& a, uint32_t tmem, int seg
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       if (q >= n1) break;
-      const __int128 T = ((__int128)hi[q] << 28) + (__int128)lo[q];
+      // T = sum_g D_g 2^7(7-g) = hi 2^28 + lo, hi = P0 2^14 + P1, lo = P2 2^14 + P3
+      const long long hi = (long long)P[0][q] * (1ll << 14) + P[1][q];
+      const long long lo = (long long)P[2][q] * (1ll << 14) + P[3][q];
+      const __int128 T = ((__int128)hi << 28) + (__int128)lo;
       ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0 : oz_i128_to_double(T, escale);
     }
     if (type == 0 && i == nx - 1) {
@@ -319,14 +375,16 @@ __device__ __forceinline__ void oz_drain(const OzArgs& a, uint32_t tmem, int seg
   }
 }
 
-// Persistent CTAs (one per SM: the 512 TMEM columns of the eight group
-// accumulators). Roles:
+// Persistent CTAs (one per SM: all 512 TMEM columns, two accumulator sets of
+// 4 tiles x 8 groups x 8 columns). Roles:
 //   warp 8 (one thread): the slice windows, in order (item, t), into buffer
 //     seq % 2 after the MMAs that read seq - 2 completed (window_free);
-//   warp 9 (one thread): per item, waits for the accumulators to be drained,
-//     then per slice waits for its window, issues its pairs' MMAs and commits
-//     them to window_free[buf]; after slice 7 commits to acc_full;
-//   drain warps 0..7: wait for acc_full, combine and store, release acc_free.
+//   warp 9 (one thread): item n into accumulator set n % 2 once the drain of
+//     item n - 2 released it; per slice waits for its window, issues its MMAs
+//     and commits them to window_free[buf]; after slice 7 commits to
+//     acc_full[n % 2];
+//   drain warps 0..7: wait for acc_full[n % 2], combine and store, release
+//     acc_free[n % 2] -- while the MMAs of item n + 1 run on the other set.
 // Every wait is bounded (1 s); before exit after a give-up the last copy and
 // commit on each barrier get one more bounded wait.
 __global__ void __launch_bounds__(kOzThreads)
@@ -334,14 +392,14 @@ __global__ void __launch_bounds__(kOzThreads)
   extern __shared__ __align__(1024) unsigned char oz_raw[];
   unsigned char* sm = oz_raw + ((1024u - (oz_su32(oz_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  unsigned char* Bbuf = sm + 2 * kOzWinB;                                   // [8][2][tile]
-  uint64_t* full = reinterpret_cast<uint64_t*>(Bbuf + kOzSlices * 2 * kOzTileB);   // [2]
-  uint64_t* wfree = full + 2;                                                  // [2]
-  uint64_t* acc_full = wfree + 2;
-  uint64_t* acc_free = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 1);
+  unsigned char* Bbuf = sm + 2 * kOzWinB;                                   // [2 types][kOzTypeB]
+  uint64_t* full = reinterpret_cast<uint64_t*>(Bbuf + 2 * kOzTypeB);        // [2]
+  uint64_t* wfree = full + 2;                                                // [2]
+  uint64_t* acc_full = wfree + 2;                                            // [2]
+  uint64_t* acc_free = acc_full + 2;                                         // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_free + 2);
   // [0] drain, [1] load, [2] issue gave up; [3] [4] loads per buffer; [5] [6]
-  // window commits per buffer; [7] accumulator commits
+  // window commits per buffer; [7] [8] accumulator commits per set
   volatile int* flags = reinterpret_cast<volatile int*>(tmem_slot + 1);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz_su32(tmem_slot)),
@@ -353,23 +411,31 @@ __global__ void __launch_bounds__(kOzThreads)
     for (int q = 0; q < 2; ++q) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(full + q)) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(wfree + q)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(acc_full + q)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_su32(acc_free + q)), "r"(kOzDrainWarps)
+                   : "memory");
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz_su32(acc_full)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(oz_su32(acc_free)), "r"(kOzDrainWarps) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int q = 0; q < 8; ++q) flags[q] = 0;
+    for (int q = 0; q < 9; ++q) flags[q] = 0;
   }
   if (tid == 32 * kOzDrainWarps) {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tv) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&th) : "memory");
   }
-  // the block slices, K-major without swizzle (core matrices of 8 n x 16 bytes)
+  // the block slices, K-major without swizzle (core matrices of 8 n x 16 bytes):
+  // per face type 8 zero rows, then slice u at rows 8 + 8u .. 8 + 8u + 7
+  for (uint32_t o = (uint32_t)tid * 16u; o < 2u * kOzTypeB; o += kOzThreads * 16u)
+    *reinterpret_cast<uint4*>(Bbuf + o) = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
   for (int idx = tid; idx < kOzSlices * 2 * kOzTileN * 64; idx += kOzThreads) {
     const int tb = idx / (kOzTileN * 64), rem = idx % (kOzTileN * 64);
-    const int n = rem / 64, k = rem % 64;
+    const int u = tb >> 1, type = tb & 1;
+    const int nl = rem / 64, k = rem % 64;
+    if (nl >= kOzGroupN) continue;                           // rows 8..15 of a slice are zero
+    const int n = 8 + kOzGroupN * u + nl;
     const uint32_t off = (uint32_t)(n >> 3) * 1024u + (uint32_t)(k >> 3) * 128u + (uint32_t)(n & 7) * 16u +
                          (uint32_t)(k & 7) * 2u;
-    *reinterpret_cast<__nv_bfloat16*>(Bbuf + (uint32_t)tb * kOzTileB + off) = a.B[idx];
+    *reinterpret_cast<__nv_bfloat16*>(Bbuf + (uint32_t)type * kOzTypeB + off) = a.B[idx];
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -381,17 +447,20 @@ __global__ void __launch_bounds__(kOzThreads)
   const long first = blockIdx.x, step = gridDim.x;
 
   if (warp < kOzDrainWarps) {
-    unsigned pa = 0u;
-    for (long item = first; item < items; item += step) {
-      if (tid == 0 && !oz_wait(acc_full, pa)) flags[0] = 1;
+    unsigned pa[2] = {0u, 0u};
+    long n = 0;
+    for (long item = first; item < items; item += step, ++n) {
+      const int set = (int)(n & 1);
+      if (tid == 0 && !oz_wait(acc_full + set, pa[set])) flags[0] = 1;
       oz_named_sync(1, 32 * kOzDrainWarps);
       if (flags[0]) break;
-      pa ^= 1u;
+      pa[set] ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      oz_drain(a, tmem, (int)(item / chunks), (int)(item % chunks), warp, lane);
+      oz_drain(a, tmem + (uint32_t)(set * kOzAccCols), (int)(item / chunks), (int)(item % chunks), warp, lane);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(acc_free)) : "memory");
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(oz_su32(acc_free + set)) : "memory");
     }
   } else if (warp == kOzDrainWarps) {
     if (lane == 0) {
@@ -412,20 +481,22 @@ __global__ void __launch_bounds__(kOzThreads)
       }
     }
   } else if (lane == 0) {
-    unsigned pw[2] = {0u, 0u}, pfree = 0u;
+    unsigned pw[2] = {0u, 0u}, pfree[2] = {0u, 0u};
     long seq = 0, n = 0;
     bool stop = false;
     for (long item = first; item < items && !stop; item += step, ++n) {
-      if (n >= 1) {           // the accumulators of item n - 1 were drained
-        if (!oz_wait(acc_free, pfree)) { flags[2] = 1; break; }
-        pfree ^= 1u;
+      const int set = (int)(n & 1);
+      if (n >= 2) {           // the accumulators of item n - 2 were drained
+        if (!oz_wait(acc_free + set, pfree[set])) { flags[2] = 1; break; }
+        pfree[set] ^= 1u;
       }
+      const uint32_t acc = tmem + (uint32_t)(set * kOzAccCols);
       for (int t = 0; t < kOzSlices; ++t, ++seq) {
         const int buf = (int)(seq & 1);
         if (!oz_wait(full + buf, pw[buf])) { flags[2] = 1; stop = true; break; }
         pw[buf] ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        oz_issue(sm + (buf ? kOzWinB : 0u), Bbuf, tmem, t);
+        oz_issue(sm + (buf ? kOzWinB : 0u), Bbuf, acc, t);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          oz_su32(wfree + buf))
                      : "memory");
@@ -433,9 +504,9 @@ __global__ void __launch_bounds__(kOzThreads)
       }
       if (stop) break;
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       oz_su32(acc_full))
+                       oz_su32(acc_full + set))
                    : "memory");
-      flags[7] = flags[7] + 1;
+      flags[7 + set] = flags[7 + set] + 1;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -446,8 +517,8 @@ __global__ void __launch_bounds__(kOzThreads)
       for (int q = 0; q < 2; ++q) {
         if (flags[3 + q] > 0) (void)oz_wait(full + q, (unsigned)((flags[3 + q] - 1) & 1));
         if (flags[5 + q] > 0) (void)oz_wait(wfree + q, (unsigned)((flags[5 + q] - 1) & 1));
+        if (flags[7 + q] > 0) (void)oz_wait(acc_full + q, (unsigned)((flags[7 + q] - 1) & 1));
       }
-      if (flags[7] > 0) (void)oz_wait(acc_full, (unsigned)((flags[7] - 1) & 1));
     }
     __syncthreads();
   }
@@ -478,9 +549,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 oz_encoder() {
 }
 
 // The BF16 block slices [8][2][16][64] of the shared block S (m x m, row-major,
-// host) and its exponent: S / 2^e_S in 56-bit fixed point, 7 bits per slice,
-// laid out like the BF16 apply's block (own element's rows 0..7, neighbour's
-// 8..15, K = own (W, E), own (S, N), neighbour (W, E), neighbour (S, N)).
+// host) and its exponent: S / 2^e_S in 56-bit fixed point, 7 bits per slice.
+// Row n < k+1 of face type 0 (W faces) holds, along K = own (W, E), own (S, N),
+// neighbour (W, E), neighbour (S, N), the W row n of S on the own element's
+// edges and the E row n on the west neighbour's (type 1: S / N rows, south
+// neighbour), so one output column sums both elements' parts; rows 8..15 are 0.
 static void oz_block_slices(const std::vector<double>& S, int n1, std::vector<uint16_t>& B, int& eS) {
   const int m = 4 * n1;
   double mx = 0.0;
@@ -491,16 +564,14 @@ static void oz_block_slices(const std::vector<double>& S, int n1, std::vector<ui
   B.assign((size_t)kOzSlices * 2 * kOzTileN * 64, 0);
   for (int u = 0; u < kOzSlices; ++u)
     for (int ty = 0; ty < 2; ++ty)
-      for (int n = 0; n < kOzTileN; ++n)
+      for (int n = 0; n < n1; ++n)
         for (int k = 0; k < 64; ++k) {
           const int step = k >> 4, h = (k >> 3) & 1, nd = k & 7;
-          const bool nb_part = n >= kOzTileN / 2;
-          const int row = n & (kOzTileN / 2 - 1);
-          if (row >= n1 || nd >= n1 || nb_part != (step >= 2)) continue;
+          if (nd >= n1) continue;
           const int own_face = ty == 0 ? 0 : 2, nb_face = ty == 0 ? 1 : 3;
           const int row_face = step < 2 ? own_face : nb_face;
           const int col_face = (step & 1) * 2 + h;
-          const double v = S[(size_t)(row_face * n1 + row) * m + col_face * n1 + nd];
+          const double v = S[(size_t)(row_face * n1 + n) * m + col_face * n1 + nd];
           const unsigned long long F = (unsigned long long)std::ldexp(std::fabs(v), 56 - eS);   // truncates
           const int d = (int)((F >> (kOzBits * (kOzSlices - 1 - u))) & 127ull);
           const float f = (float)(v < 0 ? -d : d);      // an integer of at most 7 bits: exact in BF16
@@ -558,7 +629,7 @@ static cudaError_t oz_maps(const Context* c, const void* XS, int nrhs, CUtensorM
 size_t ozaki_smem_bytes() {
   // two slice windows, the block slices, barriers + TMEM slot + flags, alignment
   // slack; at least 120 KB so that one CTA holds an SM (and all 512 TMEM columns)
-  const size_t need = (size_t)2 * kOzWinB + (size_t)kOzSlices * 2 * kOzTileB + 128 + 1024;
+  const size_t need = (size_t)2 * kOzWinB + (size_t)2 * kOzTypeB + 128 + 1024;
   return need > 120 * 1024 ? need : 120 * 1024;
 }
 
@@ -581,15 +652,16 @@ cudaError_t launch_ozaki_apply(Context* c, const double* X, double* Y, int nrhs,
     c->oz_ecol_n = nrhs;
   }
   HDG_CUDA_TRY(cudaMemsetAsync(c->oz_ecol, 0x80, (size_t)nrhs * sizeof(int), s));   // very negative
+  if (nrhs > 2048) return cudaErrorInvalidValue;     // 8 columns per thread, <= 256 threads per row
   {
-    long bx = (long)((ndof + 3) / 4);
-    if (bx > (long)c->num_sms * 2) bx = (long)c->num_sms * 2;
-    dim3 grid((unsigned)bx, (unsigned)(nrhs / 64));
-    ozaki_exp_kernel<<<grid, 256, 0, s>>>(X, ndof, nrhs, c->k + 1, c->mesh.nx, c->mesh.ny, c->oz_ecol);
+    const long rows = 256 / (nrhs / 8);
+    long bx = (long)((ndof + rows - 1) / rows);
+    if (bx > (long)c->num_sms * 4) bx = (long)c->num_sms * 4;
+    ozaki_exp_kernel<<<(unsigned)bx, 256, 0, s>>>(X, ndof, nrhs, c->k + 1, c->mesh.nx, c->mesh.ny, c->oz_ecol);
     HDG_CUDA_TRY(cudaGetLastError());
   }
   {
-    size_t b = (ndof * nrhs + 255) / 256;
+    size_t b = (ndof * (nrhs / 8) + 255) / 256;
     const size_t cap = (size_t)c->num_sms * 16;
     if (b > cap) b = cap;
     ozaki_split_kernel<<<(unsigned)b, 256, 0, s>>>(X, ndof, nrhs, c->k + 1, c->mesh.nx, c->mesh.ny, c->oz_ecol,

@@ -36,7 +36,8 @@ class hdg_options(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarse_n", ctypes.c_int), ("tau", ctypes.c_double),
                 ("cheb_degree", ctypes.c_int), ("mixed", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("reduced", ctypes.c_int),
-                ("tau_kappa", ctypes.c_int), ("smoother", ctypes.c_int), ("fmg_start", ctypes.c_int),
+                ("tau_kappa", ctypes.c_int), ("smoother", ctypes.c_int), ("tensor_apply", ctypes.c_int),
+                ("fmg_start", ctypes.c_int),
                 ("max_device_bytes", ctypes.c_size_t),
                 ("wait_probe", ctypes.c_int)]
 

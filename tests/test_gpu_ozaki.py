@@ -50,3 +50,31 @@ def test_ozaki_fp64_requires_uniform_kappa():
         s.apply_shared_fp64(X)
     assert e.value.status == hdg.HDG_ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_batched_solve_with_tensor_core_outer_apply(inner):
+    """hdg_solve with 64 right-hand sides and a uniform coefficient applies the
+    outer operator of the batched CG with hdg_apply_shared_fp64 (tensor_apply =
+    1, the default): the solutions match the oracle's direct solves and the
+    CUDA-core path (tensor_apply = 0) column by column."""
+    from paper_1705_09907_gb300 import hdg, inputs
+    nx, ny, k, nb = 24, 16, 3, 64
+    m = omesh.Mesh(nx, ny)
+    prob = ohdg.HDGProblem(m, k, np.ones(m.nel))
+    fq = np.random.default_rng(5).normal(size=(nb, m.nel, k + 2, k + 2))
+    kap = torch.ones(m.nel, dtype=torch.float64, device="cuda")
+    s1 = hdg.HDGSolver(nx, ny, k, kap)
+    s0 = hdg.HDGSolver(nx, ny, k, kap, tensor_apply=0)
+    B = s1.condense_rhs(torch.as_tensor(fq, device="cuda"))
+    L1, i1 = s1.solve(B, rtol=1e-12, maxit=300, inner=inner)
+    L0, i0 = s0.solve(B, rtol=1e-12, maxit=300, inner=inner)
+    assert abs(i1["iterations"] - i0["iterations"]) <= 1
+    L1h, L0h = L1.cpu().numpy(), L0.cpu().numpy()
+    for j in (0, 17, 63):
+        ref = prob.solve_direct(prob.condense_rhs(fq[j]))
+        nr = np.linalg.norm(ref)
+        assert np.linalg.norm(L1h[:, j] - ref) <= 1e-10 * nr
+        assert np.linalg.norm(L1h[:, j] - L0h[:, j]) <= 1e-10 * nr
+    s1.close()
+    s0.close()
