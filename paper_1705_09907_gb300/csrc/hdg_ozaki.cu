@@ -13,8 +13,8 @@
 // MMAs is exact. The result is
 //   y = 2^(e_c + e_S - 63) sum_{g=0..7} D_g 2^7(7-g),   D_g = sum_{t+u=g} S_u X_t,
 // the pairs with t + u >= 8 (below 2^-56 of the scale) dropped; the sum is
-// formed as a 128-bit integer and rounded once to FP64 with integer operations
-// (no FP64 arithmetic on the slow FP64 pipe).
+// formed as a 128-bit integer (two 64-bit words) and rounded once to FP64 with
+// integer operations (no FP64 arithmetic on the slow FP64 pipe).
 //
 // Kernels: ozaki_exp_kernel (column exponents), ozaki_split_kernel (X -> 8 BF16
 // slice arrays, [8][ndof][nrhs]), ozaki_apply_kernel (persistent CTAs, one per
@@ -207,34 +207,42 @@ __global__ void ozaki_split_kernel(const double* __restrict__ X, size_t ndof, in
   }
 }
 
-// value T * 2^e rounded to the nearest FP64 (ties to even), T a signed 128-bit
-// integer with |T| < 2^100, by integer operations only
-__device__ __forceinline__ double oz_i128_to_double(__int128 T, int e) {
-  if (T == 0) return 0.0;
-  const bool neg = T < 0;
-  unsigned __int128 U = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
-  const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
-  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  unsigned long long mant;
-  int shift = msb - 52;                             // value = mant 2^(shift + e), mant in [2^52, 2^53)
-  if (shift > 0) {
-    const unsigned __int128 q = U >> shift;
-    const unsigned __int128 rem = U - (q << shift);
-    const unsigned __int128 half = (unsigned __int128)1 << (shift - 1);
-    mant = (unsigned long long)q;
-    if (rem > half || (rem == half && (mant & 1ull))) ++mant;
-    if (mant == (1ull << 53)) { mant >>= 1; ++shift; }
-  } else {
-    mant = (unsigned long long)(U << (-shift));
+// value (hi 2^28 + lo) 2^e rounded to the nearest FP64 (ties to even), |hi|,
+// |lo| < 2^46, by integer operations only: the 128-bit sum is normalised into a
+// 64-bit window (top bit at 63) plus a sticky bit for what falls off, then
+// rounded to 53 bits.
+__device__ __forceinline__ double oz_to_double(long long hi, long long lo, int e) {
+  // two's complement 128-bit T = hi 2^28 + lo as (w1, w0)
+  unsigned long long w0 = ((unsigned long long)hi << 28) + (unsigned long long)lo;
+  const unsigned long long carry = w0 < ((unsigned long long)hi << 28) ? 1ull : 0ull;
+  unsigned long long w1 = (unsigned long long)(hi >> 36) + (unsigned long long)(lo >> 63) + carry;
+  const bool neg = (long long)w1 < 0;
+  if (neg) {                                        // magnitude
+    w0 = ~w0 + 1ull;
+    w1 = ~w1 + (w0 == 0ull ? 1ull : 0ull);
   }
-  // unbiased exponent msb + e, plus one if the rounding carried into 2^53
-  const int biased = msb + e + 1023 + (shift - (msb - 52));
+  if (w1 == 0ull && w0 == 0ull) return 0.0;
+  const int msb = w1 ? 127 - __clzll((long long)w1) : 63 - __clzll((long long)w0);
+  const int sh = msb - 63;                          // right shift bringing the top bit to 63
+  unsigned long long M;
+  bool sticky = false;
+  if (sh > 0) {
+    M = (w1 << (64 - sh)) | (w0 >> sh);
+    sticky = (w0 << (64 - sh)) != 0ull;
+  } else {
+    M = w0 << (-sh);
+  }
+  unsigned long long mant = M >> 11;                // 53 bits
+  const unsigned long long rem = M & 0x7ffull;
+  if (rem > 0x400ull || (rem == 0x400ull && (sticky || (mant & 1ull)))) ++mant;
+  int ex = msb + e;                                 // unbiased exponent of the leading bit
+  if (mant >> 53) { mant >>= 1; ++ex; }
+  const int biased = ex + 1023;
   if (biased >= 2047)                               // overflow: infinity
     return __longlong_as_double((long long)(((unsigned long long)neg << 63) | 0x7ff0000000000000ull));
   if (biased <= 0) return neg ? -0.0 : 0.0;        // below the normal range: flushed
-  const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) |
-                                  (mant & 0xfffffffffffffull);
-  return __longlong_as_double((long long)bits);
+  return __longlong_as_double(
+      (long long)(((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) | (mant & 0xfffffffffffffull)));
 }
 
 // One slice window (segment seg, right-hand sides chunk*64.., slice t) by five
@@ -361,8 +369,7 @@ __device__ __forceinline__ void oz_drain(const OzArgs& a, uint32_t tmem, int seg
       // T = sum_g D_g 2^7(7-g) = hi 2^28 + lo, hi = P0 2^14 + P1, lo = P2 2^14 + P3
       const long long hi = (long long)P[0][q] * (1ll << 14) + P[1][q];
       const long long lo = (long long)P[2][q] * (1ll << 14) + P[3][q];
-      const __int128 T = ((__int128)hi << 28) + (__int128)lo;
-      ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0 : oz_i128_to_double(T, escale);
+      ybase[((size_t)eout * n1 + q) * a.nrhs] = bndrow ? 0.0 : oz_to_double(hi, lo, escale);
     }
     if (type == 0 && i == nx - 1) {
       const int eb = nx + (nx + 1) * j;
