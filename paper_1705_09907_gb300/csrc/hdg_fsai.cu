@@ -181,56 +181,21 @@ __global__ void fsai_setup_kernel(FsaiMesh m, const double* __restrict__ S, doub
   }
 }
 
-// w = G t for nb columns ([dof][nb], column fastest): one thread per (row dof,
-// column); boundary rows give 0.
-template <typename TG, typename T>
-__global__ void fsai_g_kernel(FsaiMesh m, const TG* __restrict__ Gv, const TG* __restrict__ Gh,
-                              const T* __restrict__ t, T* __restrict__ w, int nb) {
-  const int n1 = m.n1;
-  const int n_edges = m.nv() + m.nx * (m.ny + 1);
-  const size_t total = (size_t)n_edges * n1 * nb;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int col = (int)(idx % nb);
-    const size_t rowd = idx / nb;
-    const int e = (int)(rowd / n1), a = (int)(rowd % n1);
-    const int nslots = e < m.nv() ? kFsaiVSlots : kFsaiHSlots;
-    const TG* Grow = fsai_row(Gv, Gh, m, e) + (size_t)a * n1;
-    T acc = T(0);
-    for (int s = 0; s < nslots; ++s) {
-      const int ec = m.slot_edge(e, s);
-      if (ec < 0) continue;
-      const int nbn = (s == nslots - 1) ? a + 1 : n1;
-      const TG* g = Grow + (size_t)s * n1 * n1;
-      const T* tc = t + (size_t)ec * n1 * nb + col;
-      for (int b = 0; b < nbn; ++b) acc += (T)g[b] * tc[(size_t)b * nb];
-    }
-    w[idx] = acc;
-  }
-}
-
-// z = c + G^T w (c may be null; z may alias c): one thread per (column dof
-// (e', b), column) sums G[i, (e', b)] w_i over the rows i whose pattern holds
-// e', in a fixed order: the row edges listed below, each over its nodes a.
-template <typename TG, typename T>
-__global__ void fsai_gt_kernel(FsaiMesh m, const TG* __restrict__ Gv, const TG* __restrict__ Gh,
-                               const T* __restrict__ w, const T* c, T* z, int nb) {
-  const int n1 = m.n1, b2 = n1 * n1;
+// Index tables of the apply (built once per mesh at set-up, the same for every
+// p-level): rowslots[e][s] = the column edge of slot s of row edge e (-1:
+// empty), colrows[e'][q] = 8 * (row edge) + slot for the q-th row whose pattern
+// holds edge e' (own row first, -1 after the last), so the apply kernels read
+// their neighbours instead of computing them.
+__global__ void fsai_tables_kernel(FsaiMesh m, int* __restrict__ rowslots, int* __restrict__ colrows) {
   const int nv = m.nv(), n_edges = nv + m.nx * (m.ny + 1);
-  const size_t total = (size_t)n_edges * n1 * nb;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int col = (int)(idx % nb);
-    const size_t cold = idx / nb;
-    const int ep = (int)(cold / n1), b = (int)(cold % n1);
-    // (row edge, slot) pairs whose slot is e'; up to 6
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n_edges; e += gridDim.x * blockDim.x) {
+    const int nslots = e < nv ? kFsaiVSlots : kFsaiHSlots;
+    for (int s = 0; s < kFsaiHSlots; ++s) rowslots[e * kFsaiHSlots + s] = s < nslots ? m.slot_edge(e, s) : -1;
     int re[6], rs[6], nr = 0;
-    bool interior;
-    if (ep < nv) {
-      const int i = ep % (m.nx + 1), j = ep / (m.nx + 1);
-      interior = m.vin(i, j);
-      if (interior) {
-        re[nr] = ep; rs[nr] = 1; ++nr;                                        // own row
+    if (e < nv) {
+      const int i = e % (m.nx + 1), j = e / (m.nx + 1);
+      if (m.vin(i, j)) {
+        re[nr] = e; rs[nr] = 1; ++nr;
         if (m.vin(i + 1, j)) { re[nr] = m.vedge(i + 1, j); rs[nr] = 0; ++nr; }
         if (m.hin(i, j + 1)) { re[nr] = m.hedge(i, j + 1); rs[nr] = 0; ++nr; }
         if (m.hin(i - 1, j + 1)) { re[nr] = m.hedge(i - 1, j + 1); rs[nr] = 1; ++nr; }
@@ -238,22 +203,84 @@ __global__ void fsai_gt_kernel(FsaiMesh m, const TG* __restrict__ Gv, const TG* 
         if (m.hin(i - 1, j)) { re[nr] = m.hedge(i - 1, j); rs[nr] = 3; ++nr; }
       }
     } else {
-      const int hh = ep - nv, i = hh % m.nx, j = hh / m.nx;
-      interior = m.hin(i, j);
-      if (interior) {
-        re[nr] = ep; rs[nr] = 5; ++nr;                                        // own row
+      const int hh = e - nv, i = hh % m.nx, j = hh / m.nx;
+      if (m.hin(i, j)) {
+        re[nr] = e; rs[nr] = 5; ++nr;
         if (m.hin(i, j + 1)) { re[nr] = m.hedge(i, j + 1); rs[nr] = 4; ++nr; }
       }
     }
+    for (int q = 0; q < 6; ++q) colrows[e * 6 + q] = q < nr ? 8 * re[q] + rs[q] : -1;
+  }
+}
+
+// w = G t for nb columns ([dof][nb], column fastest): one thread per (row dof,
+// column); boundary rows give 0.
+template <int N1, typename TG, typename T>
+__global__ void __launch_bounds__(256) fsai_g_kernel(int nv, int n_edges, const int* __restrict__ rowslots,
+                                                     const TG* __restrict__ Gv, const TG* __restrict__ Gh,
+                                                     const T* __restrict__ t, T* __restrict__ w, int nb) {
+  constexpr int B2 = N1 * N1;
+  const size_t total = (size_t)n_edges * N1 * nb;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    size_t rowd = idx;
+    int col = 0;
+    if (nb > 1) { rowd = idx / (size_t)nb; col = (int)(idx - rowd * nb); }
+    const int e = (int)(rowd / N1), a = (int)(rowd - (size_t)e * N1);
+    const bool vert = e < nv;
+    const int nslots = vert ? kFsaiVSlots : kFsaiHSlots;
+    const TG* Grow = (vert ? Gv + (size_t)e * kFsaiVSlots * B2 : Gh + (size_t)(e - nv) * kFsaiHSlots * B2) + a * N1;
+    const int* tab = rowslots + (size_t)e * kFsaiHSlots;
     T acc = T(0);
-    for (int q = 0; q < nr; ++q) {
-      const TG* g = fsai_row(Gv, Gh, m, re[q]) + (size_t)rs[q] * b2 + b;   // + a * n1
-      const T* wr = w + (size_t)re[q] * n1 * nb + col;
-      const int a0 = (re[q] == ep) ? b : 0;                                   // own row: a >= b
-      for (int a = a0; a < n1; ++a) acc += (T)g[(size_t)a * n1] * wr[(size_t)a * nb];
+#pragma unroll
+    for (int s = 0; s < kFsaiHSlots; ++s) {
+      if (s >= nslots) break;
+      const int ec = __ldg(tab + s);
+      if (ec < 0) continue;
+      const TG* g = Grow + s * B2;
+      const T* tc = t + (size_t)ec * N1 * nb + col;
+      const int nbn = (s == nslots - 1) ? a + 1 : N1;
+#pragma unroll
+      for (int b = 0; b < N1; ++b)
+        if (b < nbn) acc += (T)__ldg(g + b) * __ldg(tc + (size_t)b * nb);
+    }
+    w[idx] = acc;
+  }
+}
+
+// z = c + G^T w (c may be null; z may alias c): one thread per (column dof
+// (e', b), column) sums G[i, (e', b)] w_i over the rows i whose pattern holds
+// e' (colrows, own row first), each over its nodes a (a >= b on the own row).
+template <int N1, typename TG, typename T>
+__global__ void __launch_bounds__(256) fsai_gt_kernel(int nv, int n_edges, const int* __restrict__ colrows,
+                                                      const TG* __restrict__ Gv, const TG* __restrict__ Gh,
+                                                      const T* __restrict__ w, const T* c, T* z, int nb) {
+  constexpr int B2 = N1 * N1;
+  const size_t total = (size_t)n_edges * N1 * nb;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    size_t cold = idx;
+    int col = 0;
+    if (nb > 1) { cold = idx / (size_t)nb; col = (int)(idx - cold * nb); }
+    const int ep = (int)(cold / N1), b = (int)(cold - (size_t)ep * N1);
+    const int* tab = colrows + (size_t)ep * 6;
+    const int first = __ldg(tab);
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int code = q == 0 ? first : __ldg(tab + q);
+      if (code < 0) break;
+      const int re = code >> 3, sl = code & 7;
+      const TG* g = (re < nv ? Gv + (size_t)re * kFsaiVSlots * B2 : Gh + (size_t)(re - nv) * kFsaiHSlots * B2) +
+                    sl * B2 + b;
+      const T* wr = w + (size_t)re * N1 * nb + col;
+      const int a0 = (q == 0) ? b : 0;                                       // own row: a >= b
+#pragma unroll
+      for (int aa = 0; aa < N1; ++aa)
+        if (aa >= a0) acc += (T)__ldg(g + aa * N1) * __ldg(wr + (size_t)aa * nb);
     }
     const T base = c ? c[idx] : T(0);
-    z[idx] = interior ? base + acc : T(0);
+    z[idx] = first >= 0 ? base + acc : T(0);
   }
 }
 
@@ -278,6 +305,14 @@ cudaError_t launch_fsai_setup(Context* c, int p, cudaStream_t s) {
   const int n1 = L.n1, nmax = kFsaiHSlots * n1;
   const size_t nvr = (size_t)(c->mesh.nx + 1) * c->mesh.ny, nhr = (size_t)c->mesh.nx * (c->mesh.ny + 1);
   const size_t ent = (nvr * kFsaiVSlots + nhr * kFsaiHSlots) * n1 * n1;
+  if (!c->fsai_rowslots) {
+    HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->fsai_rowslots, (size_t)c->n_edges * kFsaiHSlots * sizeof(int)));
+    HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->fsai_colrows, (size_t)c->n_edges * 6 * sizeof(int)));
+    FsaiMesh m0{c->mesh.nx, c->mesh.ny, n1};
+    fsai_tables_kernel<<<fsai_grid((size_t)c->n_edges, c->num_sms), 256, 0, s>>>(m0, c->fsai_rowslots,
+                                                                                c->fsai_colrows);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
   HDG_CUDA_TRY(ctx_alloc(c, (void**)&L.G64, ent * sizeof(double)));
   if (c->opt.mixed) HDG_CUDA_TRY(ctx_alloc(c, (void**)&L.G32, ent * sizeof(float)));
   L.fsai_entries = ent;
@@ -302,29 +337,49 @@ cudaError_t launch_fsai_setup(Context* c, int p, cudaStream_t s) {
   return cudaSuccess;
 }
 
+template <int N1, typename TG, typename T>
+static void fsai_pair(const Context* c, const TG* G, size_t off, const T* in, const T* add, T* out, T* wbuf, int nb,
+                      cudaStream_t s) {
+  const int nv = (c->mesh.nx + 1) * c->mesh.ny;
+  const size_t n = (size_t)c->n_edges * N1 * nb;
+  const int g = fsai_grid(n, c->num_sms);
+  fsai_g_kernel<N1, TG, T><<<g, 256, 0, s>>>(nv, c->n_edges, c->fsai_rowslots, G, G + off, in, wbuf, nb);
+  fsai_gt_kernel<N1, TG, T><<<g, 256, 0, s>>>(nv, c->n_edges, c->fsai_colrows, G, G + off, wbuf, add, out, nb);
+}
+
+template <typename TG, typename T>
+static cudaError_t fsai_dispatch(const Context* c, int n1, const TG* G, size_t off, const T* in, const T* add, T* out,
+                                 T* wbuf, int nb, cudaStream_t s) {
+  switch (n1) {
+    case 2: fsai_pair<2>(c, G, off, in, add, out, wbuf, nb, s); break;
+    case 3: fsai_pair<3>(c, G, off, in, add, out, wbuf, nb, s); break;
+    case 4: fsai_pair<4>(c, G, off, in, add, out, wbuf, nb, s); break;
+    case 5: fsai_pair<5>(c, G, off, in, add, out, wbuf, nb, s); break;
+    case 6: fsai_pair<6>(c, G, off, in, add, out, wbuf, nb, s); break;
+    case 7: fsai_pair<7>(c, G, off, in, add, out, wbuf, nb, s); break;
+    case 8: fsai_pair<8>(c, G, off, in, add, out, wbuf, nb, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // out = add + G^T G in (add may be null or alias out) on level p for nb columns,
 // through the scratch wbuf ([ndof_p][nb], the vector type); double vectors use
 // the FP64 factor, float vectors the FP32 one.
 cudaError_t launch_fsai_smooth(Context* c, int p, int prec, const void* in, const void* add, void* out, void* wbuf,
                                int nb, cudaStream_t s) {
   PLevel& L = c->plev[p];
-  FsaiMesh m{c->mesh.nx, c->mesh.ny, L.n1};
   const size_t nvr = (size_t)(c->mesh.nx + 1) * c->mesh.ny;
   const size_t off = nvr * kFsaiVSlots * L.n1 * L.n1;
-  const size_t n = (size_t)c->n_edges * L.n1 * nb;
-  const int g = fsai_grid(n, c->num_sms);
+  if (!c->fsai_rowslots || !c->fsai_colrows) return cudaErrorInvalidValue;
   if (prec_double(prec)) {
     if (!L.G64) return cudaErrorInvalidValue;
-    fsai_g_kernel<double, double><<<g, 256, 0, s>>>(m, L.G64, L.G64 + off, (const double*)in, (double*)wbuf, nb);
-    fsai_gt_kernel<double, double><<<g, 256, 0, s>>>(m, L.G64, L.G64 + off, (const double*)wbuf,
-                                                     (const double*)add, (double*)out, nb);
-  } else {
-    if (!L.G32) return cudaErrorInvalidValue;
-    fsai_g_kernel<float, float><<<g, 256, 0, s>>>(m, L.G32, L.G32 + off, (const float*)in, (float*)wbuf, nb);
-    fsai_gt_kernel<float, float><<<g, 256, 0, s>>>(m, L.G32, L.G32 + off, (const float*)wbuf, (const float*)add,
-                                                   (float*)out, nb);
+    return fsai_dispatch<double, double>(c, L.n1, L.G64, off, (const double*)in, (const double*)add, (double*)out,
+                                         (double*)wbuf, nb, s);
   }
-  return cudaGetLastError();
+  if (!L.G32) return cudaErrorInvalidValue;
+  return fsai_dispatch<float, float>(c, L.n1, L.G32, off, (const float*)in, (const float*)add, (float*)out,
+                                     (float*)wbuf, nb, s);
 }
 
 }  // namespace hdg

@@ -143,6 +143,8 @@ struct Context {
   size_t off_ZT = 0, off_EbT = 0, off_MiBtT = 0, off_MiCT = 0, off_VfT = 0;   // transposes
   double* elem_scratch = nullptr;           // [nel][m] per-element partial results
   double* d_post = nullptr;                 // postprocessing tables: Hq^T [2][n][ns], mu [n], Dn^T [2][ns][ns]
+  int* fsai_rowslots = nullptr;             // FSAI apply tables [n_edges][6] (hdg_fsai.cu)
+  int* fsai_colrows = nullptr;
   int post_ns = 0;                          // (k+2)^2
   void* red_z = nullptr;                    // [m][nel] element products of the reduced apply
   // finest-level local operators: A_u^-1 (symmetric, stored full) and G = A_u^-1 W
