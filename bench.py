@@ -369,6 +369,14 @@ def run_ours(args):
         sbm.solve(B, rtol=1e-10, maxit=400, inner="fp32")
         torch.cuda.nvtx.range_pop()
         sbm.close()
+        # the FP64 step with the FSAI smoother (NVTX range fsai_fp64_step)
+        sfs = hdg.HDGSolver(N, N, k, kap_d, smoother=1)
+        bf = sfs.condense_rhs(fq_d)
+        sfs.solve(bf, rtol=rtol, maxit=200)
+        torch.cuda.nvtx.range_push("fsai_fp64_step")
+        sfs.solve(bf, rtol=rtol, maxit=200)
+        torch.cuda.nvtx.range_pop()
+        sfs.close()
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": True, "iterations": last["info"]["iterations"],
                           "relres": last["info"]["relres"], "vcycle_kernels": solver.get_info()["vcycle_kernels"]}))

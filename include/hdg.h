@@ -87,7 +87,13 @@ typedef struct {
   int cheb_degree;            /* Chebyshev degree per h-level smoothing step (2) */
   int mixed;                  /* also build FP32, BF16 and F32X2 copies of the
                                  level blocks (1)                             */
-  int use_graphs;             /* capture V-cycles in CUDA graphs (1)         */
+  int use_graphs;             /* capture V-cycles in CUDA graphs, and run the
+                                 iterations of a one-right-hand-side hdg_solve
+                                 as one graph launch (a conditional WHILE node
+                                 whose body ends in the stopping test: no host
+                                 round trip per iteration, the same iterates
+                                 as the host loop); 0: host loop and direct
+                                 launches (1)                                 */
   int autotune;               /* 1: time the apply kernels (the ring kernel's
                                  launch shapes and the one-CTA-per-segment
                                  kernel) per level and precision at set-up and
@@ -148,6 +154,16 @@ typedef struct {
                                  (hdg_solve, hdg_adjoint_grad) returns
                                  HDG_ERR_TIMEOUT; later calls run normally.
                                  0 <= wait_probe <= 64                        */
+  int coarse_fuse;            /* 1: the coarse Q1 levels run as one single-CTA
+                                 kernel per V-cycle: from the first level
+                                 whose stencils and vectors, with every
+                                 coarser level's, fit in one CTA's shared
+                                 memory, smoothing, residuals, transfers and
+                                 the coarsest solve (through the inverse of
+                                 its Cholesky factorisation, when it has at
+                                 most 1024 unknowns) are phases of one launch
+                                 (default); 0: one launch per step on every
+                                 level                                        */
 } hdg_options;
 
 typedef struct {

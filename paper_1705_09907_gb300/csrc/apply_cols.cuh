@@ -39,6 +39,15 @@ struct alignas(4 * sizeof(TS)) Quad {
   TS v[4];
 };
 
+// type of the staged blocks: BF16 records are widened to float as they are
+// staged (once per CTA) instead of in the product loop, where every lane of a
+// warp would convert the same broadcast entries again
+template <typename TS> struct StagedT { using type = TS; };
+template <> struct StagedT<__nv_bfloat16> { using type = float; };
+__device__ __forceinline__ float stage_conv(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+template <typename TS>
+__device__ __forceinline__ TS stage_conv(TS v, TS) { return v; }
+
 // columns per lane: float accumulators take two (one block load feeds two
 // FMAs), the wider double / double-float accumulators one
 template <typename TA>
@@ -53,8 +62,9 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
   constexpr int M = ColsShape<N1>::M, R = ColsShape<N1>::R;
   constexpr int CPL = ColsPerLane<TA>::value;
   constexpr int VEC = 16 / sizeof(TS);             // entries per 16-byte global load
+  using TSS = typename StagedT<TS>::type;
   extern __shared__ __align__(128) unsigned char cols_smem[];
-  TS* sS = reinterpret_cast<TS*>(cols_smem);       // [16][R], element-major
+  TSS* sS = reinterpret_cast<TSS*>(cols_smem);     // [16][R], element-major
   const int seg = blockIdx.x;
   // stage: global [(seg*R + r)*16 + t] -> sS[t*R + r], up to 8 16-byte loads
   // in flight per thread before their stores
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
         if (b0 + u < PER && idx < NV) {
           const int r = (idx * VEC) / kSeg, t0 = (idx * VEC) % kSeg;
 #pragma unroll
-          for (int q = 0; q < VEC; ++q) sS[(t0 + q) * R + r] = buf[u].s[q];
+          for (int q = 0; q < VEC; ++q) sS[(t0 + q) * R + r] = stage_conv(buf[u].s[q], TSS{});
         }
       }
     }
@@ -96,6 +106,10 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
   // y = A v, y = c - A v and y = c + A v take no multiply (FP64 ops are slow here)
   const int form = (al == TO(1) && (!cv || be == TO(0))) ? 0
                    : (cv && be == TO(1) && al == TO(-1)) ? 1 : (cv && be == TO(1) && al == TO(1)) ? 2 : 3;
+  // two float columns per lane with nb a multiple of 64: the lane's columns are
+  // adjacent, every row of x, y and c one float2 access per lane
+  const bool pair = CPL == 2 && sizeof(TV) == 4 && (nb % CPW) == 0 &&
+                    (((uintptr_t)a.v | (uintptr_t)a.cvec | (uintptr_t)a.y) & 7) == 0;
   for (int item = warp; item < 32 * nchunk; item += (kColsThreads >> 5)) {
     // warp-uniform: element t of the segment, owned face (W or S), column chunk
     const int chunk = item >> 5, face = (item >> 4) & 1, t = item & 15;
@@ -105,7 +119,8 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
     bool live[CPL];
 #pragma unroll
     for (int u = 0; u < CPL; ++u) {
-      const int col = chunk * CPW + u * 32 + lane;
+      // paired columns (2 lane, 2 lane + 1) move as one 8-byte access
+      const int col = pair ? chunk * CPW + 2 * lane + u : chunk * CPW + u * 32 + lane;
       live[u] = col < nb;
       colc[u] = live[u] ? col : nb - 1;            // dead lanes load a valid column
     }
@@ -137,6 +152,18 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
         for (int f = 0; f < 4; ++f) {
           if (!bnd[f]) {                           // warp-uniform branch
             const TV* bp = v + (size_t)edge[f] * N1 * nb;
+            if constexpr (CPL == 2 && sizeof(TV) == 4) {
+              if (pair) {
+                const float2* bp2 = reinterpret_cast<const float2*>(bp + colc[0]);
+#pragma unroll
+                for (int b = 0; b < N1; ++b) {
+                  const float2 w2 = bp2[(size_t)b * (nb >> 1)];
+                  xv[0][f * N1 + b] = to_acc(w2.x, TA{});
+                  xv[1][f * N1 + b] = to_acc(w2.y, TA{});
+                }
+                continue;
+              }
+            }
 #pragma unroll
             for (int b = 0; b < N1; ++b)
 #pragma unroll
@@ -165,17 +192,32 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
         if (side == 1 && cv) {
           // the addend's loads are issued before the last products so their
           // latency overlaps them
+          bool done = false;
+          if constexpr (CPL == 2 && sizeof(TV) == 4) {
+            if (pair) {
+              const float2* cp2 = reinterpret_cast<const float2*>(cv + (size_t)eout * N1 * nb + colc[0]);
 #pragma unroll
-          for (int u = 0; u < CPL; ++u)
+              for (int q = 0; q < N1; ++q) {
+                const float2 w2 = cp2[(size_t)q * (nb >> 1)];
+                cpre[0][q] = (TO)w2.x;
+                cpre[1][q] = (TO)w2.y;
+              }
+              done = true;
+            }
+          }
+          if (!done) {
 #pragma unroll
-            for (int q = 0; q < N1; ++q) cpre[u][q] = (TO)cv[((size_t)eout * N1 + q) * nb + colc[u]];
+            for (int u = 0; u < CPL; ++u)
+#pragma unroll
+              for (int q = 0; q < N1; ++q) cpre[u][q] = (TO)cv[((size_t)eout * N1 + q) * nb + colc[u]];
+          }
         }
-        const TS* rows = sS + t * R + (face * 2 + side) * N1 * M;
+        const TSS* rows = sS + t * R + (face * 2 + side) * N1 * M;
 #pragma unroll
         for (int q = 0; q < N1; ++q)
 #pragma unroll
           for (int c = 0; c < M; c += 4) {
-            const Quad<TS> s4 = *reinterpret_cast<const Quad<TS>*>(rows + q * M + c);
+            const Quad<TSS> s4 = *reinterpret_cast<const Quad<TSS>*>(rows + q * M + c);
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
               const TA sv = to_acc(s4.v[w], TA{});
@@ -185,13 +227,11 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
           }
       }
     }
+    TO outv[CPL][N1];
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) {
-      if (!live[u]) continue;
-      const int col = colc[u];
+    for (int u = 0; u < CPL; ++u)
 #pragma unroll
       for (int q = 0; q < N1; ++q) {
-        const size_t o = ((size_t)eout * N1 + q) * nb + col;
         TO val = TO(0);
         if (!bndrow) {
           const TO sum = finish(acc[u][q]);
@@ -203,7 +243,22 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
             if (cv) val = mac(be, cpre[u][q], val);
           }
         }
-        y[o] = (TV)val;
+        outv[u][q] = val;
+      }
+    if constexpr (CPL == 2 && sizeof(TV) == 4) {
+      if (pair) {
+        float2* yp2 = reinterpret_cast<float2*>(y + (size_t)eout * N1 * nb + colc[0]);
+#pragma unroll
+        for (int q = 0; q < N1; ++q) yp2[(size_t)q * (nb >> 1)] = make_float2((float)outv[0][q], (float)outv[1][q]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) {
+      if (!live[u]) continue;
+      const int col = colc[u];
+      if (!pair) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) y[((size_t)eout * N1 + q) * nb + col] = (TV)outv[u][q];
       }
       // the E / N domain-boundary edges have no owner element: zero them here
       if (face == 0 && i == nx - 1) {
@@ -222,7 +277,7 @@ __global__ void __launch_bounds__(kColsThreads, 3) apply_cols_kernel(ColsArgs a)
 
 template <int N1, typename TS, typename TV, typename TA, bool DIFF>
 cudaError_t cols_launch(const Context* c, const ColsArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)ColsShape<N1>::R * kSeg * sizeof(TS);
+  const size_t smem = (size_t)ColsShape<N1>::R * kSeg * sizeof(typename StagedT<TS>::type);
   if ((size_t)c->smem_optin < smem) return cudaErrorInvalidValue;
   auto kern = apply_cols_kernel<N1, TS, TV, TA, DIFF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_optin);

@@ -51,6 +51,7 @@ void hdg_default_options(hdg_options* o) {
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
   o->autotune = 1; o->reduced = 1; o->tau_kappa = 0;
   o->smoother = 0; o->tensor_apply = 1; o->fmg_start = 0; o->max_device_bytes = 0; o->wait_probe = 0;
+  o->coarse_fuse = 1;
 }
 
 const char* hdg_error_string(int s) {
@@ -214,6 +215,12 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
   const size_t nd = (size_t)c->ndof;
   for (double** p : {&c->cg_r, &c->cg_z, &c->cg_p, &c->cg_q, &c->cg_zold})
     TRY(ctx_alloc(c, (void**)p, nd * sizeof(double)));
+  if (c->opt.use_graphs) {   // the device-resident CG loop's iterate, history and control words
+    TRY(ctx_alloc(c, (void**)&c->cg_x, nd * sizeof(double)));
+    TRY(ctx_alloc(c, (void**)&c->cg_hist, 256 * sizeof(double)));
+    TRY(ctx_alloc(c, (void**)&c->cg_ctl, 4 * sizeof(int)));
+    TRY(cudaMallocHost((void**)&c->h_cg, 264 * sizeof(double)));
+  }
   if (c->opt.autotune) TRY(autotune_applies(c, s));
   TRY(build_hierarchy(c, s));
   TRY(noalloc_prepare_device(c->dev));
@@ -244,7 +251,7 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
       o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2 ||
       o.tau_kappa < 0 || o.tau_kappa > 1 || o.wait_probe < 0 || o.wait_probe > 64 || o.smoother < 0 ||
       o.smoother > 1 || o.fmg_start < 0 || o.fmg_start > 16 ||
-      o.tensor_apply < 0 || o.tensor_apply > 1)
+      o.tensor_apply < 0 || o.tensor_apply > 1 || o.coarse_fuse < 0 || o.coarse_fuse > 1)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);

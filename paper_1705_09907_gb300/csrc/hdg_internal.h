@@ -153,6 +153,7 @@ struct Context {
   std::vector<PLevel> plev;                 // index p = 0..k
   std::vector<HLevel> hlev;                 // finest Q1 first
   double* coarse_L = nullptr;               // dense FP64 Cholesky factor [nc][nc]
+  double* coarse_AinvT = nullptr;           // its inverse, transposed (fused coarse cycle; nc <= 1024)
   int coarse_dim = 0;
   double* coarse_rhs = nullptr;             // [nc] FP64 scratch
   // CG / reduction scratch
@@ -163,6 +164,13 @@ struct Context {
   float* cg_r32 = nullptr;
   float* cg_z32 = nullptr;
   int* err_flag = nullptr;                  // device error flag (timeouts)
+  // device-resident CG loop (one graph per inner precision, built on first use)
+  cudaGraphExec_t cg_graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool cg_graph_failed = false;             // conditional graphs unavailable: host loop
+  double* cg_x = nullptr;                   // the loop's iterate
+  double* cg_hist = nullptr;                // relative residual per iteration [256]
+  int* cg_ctl = nullptr;                    // iterations, status, maxit
+  double* h_cg = nullptr;                   // pinned host copy of the loop's results [264]
   size_t bytes = 0;
   double setup_ms = 0.0;
   std::vector<void*> allocs;

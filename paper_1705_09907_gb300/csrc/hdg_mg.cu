@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "hdg_internal.h"
@@ -122,25 +123,34 @@ static int grid_for(size_t n) {
 // with x given (d = c0 * dinv .* t; x += d), later steps (d = a1 d + a2 dinv .* t;
 // x += d). Vectors hold nb right-hand sides per unknown (right-hand side
 // fastest); n counts unknowns x columns.
+// The per-entry bodies are device functions shared by the one-launch-per-step
+// kernels and the fused coarse-level kernel; their vector arguments carry no
+// __restrict__ (the fused kernel reads in one phase what it wrote in the last).
+template <typename T>
+__device__ __forceinline__ void cheb_first_zero_at(size_t t, int nb, const T* dinv, const T* f, T* x, T* d, T c0) {
+  int col;
+  const T v = c0 * dinv[divmod(t, nb, &col)] * f[t];
+  x[t] = v;
+  d[t] = v;
+}
+template <typename T>
+__device__ __forceinline__ void cheb_step_at(size_t t, int nb, const T* dinv, const T* r, T* x, T* d, T a1, T a2) {
+  int col;
+  const T v = a1 * d[t] + a2 * dinv[divmod(t, nb, &col)] * r[t];
+  d[t] = v;
+  x[t] += v;
+}
 template <typename T>
 __global__ void cheb_first_zero_kernel(size_t n, int nb, const T* __restrict__ dinv, const T* __restrict__ f,
                                        T* __restrict__ x, T* __restrict__ d, T c0) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const T v = c0 * dinv[divmod(t, nb, &col)] * f[t];
-    x[t] = v;
-    d[t] = v;
-  }
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    cheb_first_zero_at<T>(t, nb, dinv, f, x, d, c0);
 }
 template <typename T>
 __global__ void cheb_step_kernel(size_t n, int nb, const T* __restrict__ dinv, const T* __restrict__ r,
                                  T* __restrict__ x, T* __restrict__ d, T a1, T a2) {
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const T v = a1 * d[t] + a2 * dinv[divmod(t, nb, &col)] * r[t];
-    d[t] = v;
-    x[t] += v;
-  }
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    cheb_step_at<T>(t, nb, dinv, r, x, d, a1, a2);
 }
 
 // ---------------------------------------------------------------------------
@@ -256,43 +266,11 @@ __global__ void prolong_J_add_kernel(int nx, int ny, int nb, const T* __restrict
 // the product is taken in difference form, sum_{o != centre} a_o (x_{v+o} - x_v)
 // + rsum_v x_v: exact in exact arithmetic, and the rounded stencil then sees the
 // variation of x around v rather than its (smooth, large) value.
-template <typename T>
-__global__ void stencil_apply_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ x,
-                                     const T* __restrict__ c, T* __restrict__ y, T alpha, T beta,
-                                     const T* __restrict__ rsum) {
-  const int nvx = nx - 1, nvy = ny - 1, nvert = nvx * nvy;
-  const size_t total = (size_t)nvert * nb;
-  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const int t = (int)divmod(tt, nb, &col);
-    const int I = t % nvx, J = t / nvx;
-    const T xc = x[tt];
-    T s = rsum ? rsum[t] * xc : T(0);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int I2 = I + dx, J2 = J + dy;
-        if (I2 < 0 || J2 < 0 || I2 >= nvx || J2 >= nvy) continue;
-        const T a = st[((dy + 1) * 3 + dx + 1) * (size_t)nvert + t];
-        const T xn = x[((size_t)I2 + (size_t)nvx * J2) * nb + col];
-        if (rsum) {
-          if (dx != 0 || dy != 0) s += a * (xn - xc);
-        } else {
-          s += a * xn;
-        }
-      }
-    T v = alpha * s;
-    if (c) v += beta * c[tt];
-    y[tt] = v;
-  }
-}
-
 // (A x)_v for vertex t, column col of a Q1 stencil level (difference form with
-// row sums for float levels, as in stencil_apply_kernel)
+// row sums when rsum is given)
 template <typename T>
-__device__ __forceinline__ T stencil_row(int nvx, int nvy, int nb, int t, int col, const T* __restrict__ st,
-                                         const T* __restrict__ x, const T* __restrict__ rsum) {
+__device__ __forceinline__ T stencil_row(int nvx, int nvy, int nb, int t, int col, const T* st, const T* x,
+                                         const T* rsum) {
   const int nvert = nvx * nvy;
   const int I = t % nvx, J = t / nvx;
   const T xc = x[(size_t)t * nb + col];
@@ -314,6 +292,24 @@ __device__ __forceinline__ T stencil_row(int nvx, int nvy, int nb, int t, int co
   return s;
 }
 
+template <typename T>
+__device__ __forceinline__ void stencil_apply_at(size_t tt, int nx, int ny, int nb, const T* st, const T* x,
+                                                 const T* c, T* y, T alpha, T beta, const T* rsum) {
+  int col;
+  const int t = (int)divmod(tt, nb, &col);
+  T v = alpha * stencil_row<T>(nx - 1, ny - 1, nb, t, col, st, x, rsum);
+  if (c) v += beta * c[tt];
+  y[tt] = v;
+}
+template <typename T>
+__global__ void stencil_apply_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ x,
+                                     const T* __restrict__ c, T* __restrict__ y, T alpha, T beta,
+                                     const T* __restrict__ rsum) {
+  const size_t total = (size_t)(nx - 1) * (ny - 1) * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x)
+    stencil_apply_at<T>(tt, nx, ny, nb, st, x, c, y, alpha, beta, rsum);
+}
+
 // Fused Chebyshev steps on a Q1 level (stencil A, Jacobi D), two launches per
 // degree-2 step instead of four:
 //   cheb_resid: r = f - A x, d = c0 D^-1 r             (x is not touched)
@@ -321,35 +317,42 @@ __device__ __forceinline__ T stencil_row(int nvx, int nvy, int nb, int t, int co
 //               x += d' (+ d when x does not hold d yet); d' goes to a second
 //               buffer, so no thread writes what its neighbours read
 template <typename T>
+__device__ __forceinline__ void cheb_resid_at(size_t tt, int nx, int ny, int nb, const T* st, const T* rsum,
+                                              const T* dinv, const T* f, const T* x, T* r, T* d, T c0) {
+  int col;
+  const int t = (int)divmod(tt, nb, &col);
+  const T rv = f[tt] - stencil_row<T>(nx - 1, ny - 1, nb, t, col, st, x, rsum);
+  r[tt] = rv;
+  d[tt] = c0 * dinv[t] * rv;
+}
+template <typename T>
+__device__ __forceinline__ void cheb_next_at(size_t tt, int nx, int ny, int nb, const T* st, const T* rsum,
+                                             const T* dinv, const T* rin, T* rout, const T* d, T* dn, T* x, T a1,
+                                             T a2, int add_d) {
+  int col;
+  const int t = (int)divmod(tt, nb, &col);
+  const T rv = rin[tt] - stencil_row<T>(nx - 1, ny - 1, nb, t, col, st, d, rsum);
+  const T dv = d[tt];
+  const T dnv = a1 * dv + a2 * dinv[t] * rv;
+  rout[tt] = rv;
+  dn[tt] = dnv;
+  x[tt] += add_d ? dv + dnv : dnv;
+}
+template <typename T>
 __global__ void cheb_resid_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ rsum,
                                   const T* __restrict__ dinv, const T* __restrict__ f, const T* __restrict__ x,
                                   T* __restrict__ r, T* __restrict__ d, T c0) {
-  const int nvx = nx - 1, nvy = ny - 1;
-  const size_t total = (size_t)nvx * nvy * nb;
-  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const int t = (int)divmod(tt, nb, &col);
-    const T rv = f[tt] - stencil_row<T>(nvx, nvy, nb, t, col, st, x, rsum);
-    r[tt] = rv;
-    d[tt] = c0 * dinv[t] * rv;
-  }
+  const size_t total = (size_t)(nx - 1) * (ny - 1) * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x)
+    cheb_resid_at<T>(tt, nx, ny, nb, st, rsum, dinv, f, x, r, d, c0);
 }
 template <typename T>
 __global__ void cheb_next_kernel(int nx, int ny, int nb, const T* __restrict__ st, const T* __restrict__ rsum,
                                  const T* __restrict__ dinv, const T* rin, T* rout, const T* __restrict__ d,
                                  T* __restrict__ dn, T* __restrict__ x, T a1, T a2, int add_d) {
-  const int nvx = nx - 1, nvy = ny - 1;
-  const size_t total = (size_t)nvx * nvy * nb;
-  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const int t = (int)divmod(tt, nb, &col);
-    const T rv = rin[tt] - stencil_row<T>(nvx, nvy, nb, t, col, st, d, rsum);
-    const T dv = d[tt];
-    const T dnv = a1 * dv + a2 * dinv[t] * rv;
-    rout[tt] = rv;
-    dn[tt] = dnv;
-    x[tt] += add_d ? dv + dnv : dnv;
-  }
+  const size_t total = (size_t)(nx - 1) * (ny - 1) * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x)
+    cheb_next_at<T>(tt, nx, ny, nb, st, rsum, dinv, rin, rout, d, dn, x, a1, a2, add_d);
 }
 
 // row sums of a stencil level (FP64), stored in float for the difference form
@@ -363,47 +366,53 @@ __global__ void stencil_rowsum_kernel(int nvert, const double* __restrict__ st, 
 
 // full weighting R = P^T of bilinear interpolation
 template <typename T>
-__global__ void restrict_q_kernel(int nxc, int nyc, int nb, const T* __restrict__ rf, T* __restrict__ rc) {
+__device__ __forceinline__ void restrict_q_at(size_t tt, int nxc, int nyc, int nb, const T* rf, T* rc) {
   const int nxf = 2 * nxc, nyf = 2 * nyc;
   const int nvxc = nxc - 1, nvxf = nxf - 1;
+  int col;
+  const int t = (int)divmod(tt, nb, &col);
+  const int I = t % nvxc + 1, J = t / nvxc + 1;
+  T s = 0;
+  for (int b = -1; b <= 1; ++b)
+    for (int a = -1; a <= 1; ++a) {
+      const int i = 2 * I + a, j = 2 * J + b;
+      if (i <= 0 || j <= 0 || i >= nxf || j >= nyf) continue;
+      const T w = (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5));
+      s += w * rf[((size_t)(i - 1) + (size_t)nvxf * (j - 1)) * nb + col];
+    }
+  rc[tt] = s;
+}
+template <typename T>
+__global__ void restrict_q_kernel(int nxc, int nyc, int nb, const T* __restrict__ rf, T* __restrict__ rc) {
   const size_t total = (size_t)(nxc - 1) * (nyc - 1) * nb;
-  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const int t = (int)divmod(tt, nb, &col);
-    const int I = t % nvxc + 1, J = t / nvxc + 1;
-    T s = 0;
-    for (int b = -1; b <= 1; ++b)
-      for (int a = -1; a <= 1; ++a) {
-        const int i = 2 * I + a, j = 2 * J + b;
-        if (i <= 0 || j <= 0 || i >= nxf || j >= nyf) continue;
-        const T w = (a == 0 ? T(1) : T(0.5)) * (b == 0 ? T(1) : T(0.5));
-        s += w * rf[((size_t)(i - 1) + (size_t)nvxf * (j - 1)) * nb + col];
-      }
-    rc[tt] = s;
-  }
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x)
+    restrict_q_at<T>(tt, nxc, nyc, nb, rf, rc);
 }
 
 template <typename T>
-__global__ void prolong_q_add_kernel(int nxc, int nyc, int nb, const T* __restrict__ xc, T* __restrict__ xf) {
-  const int nxf = 2 * nxc, nyf = 2 * nyc;
+__device__ __forceinline__ void prolong_q_add_at(size_t tt, int nxc, int nyc, int nb, const T* xc, T* xf) {
+  const int nxf = 2 * nxc;
   const int nvxf = nxf - 1, nvxc = nxc - 1;
-  const size_t total = (size_t)(nxf - 1) * (nyf - 1) * nb;
-  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x) {
-    int col;
-    const int t = (int)divmod(tt, nb, &col);
-    const int i = t % nvxf + 1, j = t / nvxf + 1;
-    const int i0 = i / 2, j0 = j / 2;
-    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
-    const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
-    T s = 0;
-    for (int b = 0; b < nj; ++b)
-      for (int a = 0; a < ni; ++a) {
-        const int I = i0 + a, J = j0 + b;
-        if (I <= 0 || J <= 0 || I >= nxc || J >= nyc) continue;
-        s += wx * wy * xc[((size_t)(I - 1) + (size_t)nvxc * (J - 1)) * nb + col];
-      }
-    xf[tt] += s;
-  }
+  int col;
+  const int t = (int)divmod(tt, nb, &col);
+  const int i = t % nvxf + 1, j = t / nvxf + 1;
+  const int i0 = i / 2, j0 = j / 2;
+  const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1;
+  const T wx = (i & 1) ? T(0.5) : T(1), wy = (j & 1) ? T(0.5) : T(1);
+  T s = 0;
+  for (int b = 0; b < nj; ++b)
+    for (int a = 0; a < ni; ++a) {
+      const int I = i0 + a, J = j0 + b;
+      if (I <= 0 || J <= 0 || I >= nxc || J >= nyc) continue;
+      s += wx * wy * xc[((size_t)(I - 1) + (size_t)nvxc * (J - 1)) * nb + col];
+    }
+  xf[tt] += s;
+}
+template <typename T>
+__global__ void prolong_q_add_kernel(int nxc, int nyc, int nb, const T* __restrict__ xc, T* __restrict__ xf) {
+  const size_t total = (size_t)(2 * nxc - 1) * (2 * nyc - 1) * nb;
+  for (size_t tt = blockIdx.x * (size_t)blockDim.x + threadIdx.x; tt < total; tt += (size_t)gridDim.x * blockDim.x)
+    prolong_q_add_at<T>(tt, nxc, nyc, nb, xc, xf);
 }
 
 // conforming Q1 stiffness (kappa grad u, grad v) on the finest mesh:
@@ -535,6 +544,179 @@ __global__ void coarse_solve_kernel(int n, int nb, const double* __restrict__ L,
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[(size_t)i * nb + col] = (T)w[i];
+}
+
+// column j of the coarsest operator's inverse (L L^T)^-1 e_j for the fused
+// coarse cycle: one CTA per column, the substitutions of coarse_solve_kernel on
+// the unit vector in shared memory; stored transposed, AinvT[j][i] = (A^-1)_ij
+__global__ void coarse_inverse_kernel(int n, const double* __restrict__ L, double* __restrict__ AinvT) {
+  extern __shared__ double cw[];
+  const int col = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cw[i] = (i == col) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) cw[j] /= L[(size_t)j * n + j];
+    __syncthreads();
+    const double wj = cw[j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) cw[i] -= L[(size_t)i * n + j] * wj;
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) cw[j] /= L[(size_t)j * n + j];
+    __syncthreads();
+    const double wj = cw[j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) cw[i] -= L[(size_t)j * n + i] * wj;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) AinvT[(size_t)col * n + i] = cw[i];
+}
+
+// ---------------------------------------------------------------------------
+// Coarse Q1 levels in one launch. From the first Q1 level whose data, with
+// every coarser level's, fits in one CTA's shared memory, the rest of Alg. 1
+// -- Chebyshev pre-smoothing, residual, restriction, the coarsest solve,
+// prolongation and post-smoothing on the way up -- runs in one CTA: stencils,
+// diagonals and vectors of those levels are staged in shared memory, and every
+// step is a phase over the level's entries with the per-entry arithmetic of
+// the one-launch-per-step kernels, phases separated by __syncthreads. On
+// meshes of a few hundred vertices each step is launch-latency bound as its own
+// kernel; here it costs a barrier and shared-memory latency. The coarsest solve
+// is x = A_c^-1 r with the inverse formed at set-up from the Cholesky factor
+// (its 2n dependent substitution steps would cost more than the whole cycle).
+constexpr int kHfMaxLevels = 8;
+constexpr int kHfMaxCoef = 7;         // cheb_degree <= 8
+constexpr int kHfThreads = 1024;
+constexpr int kHfMaxCoarse = 1024;    // largest coarsest system solved through its inverse
+
+// one fused level: global sources of its read-only data, offsets (in entries
+// of T) of its arrays in the shared-memory image, Chebyshev coefficients
+template <typename T>
+struct HfLevel {
+  int nx, ny;
+  const T* st_g;                       // stencil [9][nv] (global)
+  const T* rs_g;                       // row sums (float levels) or null
+  const T* dinv_g;                     // Jacobi diagonal inverse
+  int o_st, o_rs, o_dinv;              // shared offsets (o_rs < 0: none)
+  int o_r, o_x, o_t, o_d, o_d2;        // vectors [nv][nb]
+  T c0, a1[kHfMaxCoef], a2[kHfMaxCoef];
+};
+template <typename T>
+struct HfArgs {
+  int nlev, nb, nu1, nu2, ncoef, nc;   // fused levels (the last is the coarsest), coarsest unknowns
+  const double* AinvT;                 // [nc][nc] transposed inverse of the coarsest operator
+  const T* r_top;                      // right-hand side of the top fused level (global)
+  T* x_top;                            // its correction (global)
+  HfLevel<T> L[kHfMaxLevels];
+};
+
+// shared-memory view of a fused level
+template <typename T>
+struct HfView {
+  int nx, ny;
+  const T *st, *rs, *dinv;
+  T *r, *x, *t, *d, *d2;
+};
+template <typename T>
+__device__ __forceinline__ HfView<T> hf_view(const HfLevel<T>& L, T* sm) {
+  HfView<T> v;
+  v.nx = L.nx; v.ny = L.ny;
+  v.st = sm + L.o_st; v.rs = L.o_rs >= 0 ? sm + L.o_rs : nullptr; v.dinv = sm + L.o_dinv;
+  v.r = sm + L.o_r; v.x = sm + L.o_x; v.t = sm + L.o_t; v.d = sm + L.o_d; v.d2 = sm + L.o_d2;
+  return v;
+}
+
+// nu Chebyshev steps on a fused level (the phases of cheb_smooth's Q1 branch)
+template <typename T>
+__device__ void hf_smooth(const HfView<T>& L, const HfLevel<T>& C, int nb, int ncoef, bool x_zero, int nu) {
+  const size_t n = (size_t)(L.nx - 1) * (L.ny - 1) * nb;
+  T* da = L.d;
+  T* db = L.d2;
+  for (int step = 0; step < nu; ++step) {
+    const T* rin;
+    int add_d;
+    if (step == 0 && x_zero) {
+      for (size_t tt = threadIdx.x; tt < n; tt += blockDim.x) cheb_first_zero_at<T>(tt, nb, L.dinv, L.r, L.x, da, C.c0);
+      rin = L.r;
+      add_d = 0;
+    } else {
+      for (size_t tt = threadIdx.x; tt < n; tt += blockDim.x)
+        cheb_resid_at<T>(tt, L.nx, L.ny, nb, L.st, L.rs, L.dinv, L.r, L.x, L.t, da, C.c0);
+      rin = L.t;
+      add_d = 1;
+    }
+    __syncthreads();
+    for (int i = 0; i < ncoef; ++i) {
+      for (size_t tt = threadIdx.x; tt < n; tt += blockDim.x)
+        cheb_next_at<T>(tt, L.nx, L.ny, nb, L.st, L.rs, L.dinv, rin, L.t, da, db, L.x, C.a1[i], C.a2[i], add_d);
+      __syncthreads();
+      T* tmp = da; da = db; db = tmp;
+      rin = L.t;
+      add_d = 0;
+    }
+    if (add_d) {   // degree 1: x += d
+      for (size_t tt = threadIdx.x; tt < n; tt += blockDim.x) cheb_step_at<T>(tt, nb, L.dinv, L.t, L.x, da, T(1), T(0));
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kHfThreads, 1) hcoarse_kernel(const __grid_constant__ HfArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char hf_smem[];
+  T* sm = reinterpret_cast<T*>(hf_smem);
+  const int nb = A.nb;
+  // stage the levels' stencils and diagonals and the top right-hand side
+  for (int l = 0; l + 1 < A.nlev; ++l) {
+    const HfLevel<T>& C = A.L[l];
+    const int nv = (C.nx - 1) * (C.ny - 1);
+    for (int i = threadIdx.x; i < 9 * nv; i += blockDim.x) sm[C.o_st + i] = C.st_g[i];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      sm[C.o_dinv + i] = C.dinv_g[i];
+      if (C.o_rs >= 0) sm[C.o_rs + i] = C.rs_g[i];
+    }
+  }
+  {
+    const HfLevel<T>& C = A.L[0];
+    const int n = (C.nx - 1) * (C.ny - 1) * nb;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[C.o_r + i] = A.r_top[i];
+  }
+  __syncthreads();
+  for (int l = 0; l + 1 < A.nlev; ++l) {                  // down: smooth, residual, restrict
+    const HfView<T> L = hf_view(A.L[l], sm);
+    const HfView<T> Lc = hf_view(A.L[l + 1], sm);
+    hf_smooth<T>(L, A.L[l], nb, A.ncoef, true, A.nu1);
+    const size_t n = (size_t)(L.nx - 1) * (L.ny - 1) * nb;
+    for (size_t tt = threadIdx.x; tt < n; tt += blockDim.x)
+      stencil_apply_at<T>(tt, L.nx, L.ny, nb, L.st, L.x, L.r, L.t, T(-1), T(1), L.rs);
+    __syncthreads();
+    const size_t nc = (size_t)(Lc.nx - 1) * (Lc.ny - 1) * nb;
+    for (size_t tt = threadIdx.x; tt < nc; tt += blockDim.x) restrict_q_at<T>(tt, Lc.nx, Lc.ny, nb, L.t, Lc.r);
+    __syncthreads();
+  }
+  {                                                       // coarsest: x = A_c^-1 r in FP64
+    const HfView<T> Lc = hf_view(A.L[A.nlev - 1], sm);
+    const int n = A.nc;
+    for (size_t tt = threadIdx.x; tt < (size_t)n * nb; tt += blockDim.x) {
+      const int i = (int)(tt / nb), col = (int)(tt - (size_t)i * nb);
+      double acc = 0.0;
+      for (int j = 0; j < n; ++j) acc += A.AinvT[(size_t)j * n + i] * (double)Lc.r[(size_t)j * nb + col];
+      Lc.x[tt] = (T)acc;
+    }
+    __syncthreads();
+  }
+  for (int l = A.nlev - 2; l >= 0; --l) {                 // up: prolong, smooth
+    const HfView<T> L = hf_view(A.L[l], sm);
+    const HfView<T> Lc = hf_view(A.L[l + 1], sm);
+    const size_t n = (size_t)(L.nx - 1) * (L.ny - 1) * nb;
+    for (size_t tt = threadIdx.x; tt < n; tt += blockDim.x) prolong_q_add_at<T>(tt, Lc.nx, Lc.ny, nb, Lc.x, L.x);
+    __syncthreads();
+    hf_smooth<T>(L, A.L[l], nb, A.ncoef, false, A.nu2);
+  }
+  {
+    const HfLevel<T>& C = A.L[0];
+    const int n = (C.nx - 1) * (C.ny - 1) * nb;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) A.x_top[i] = sm[C.o_x + i];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -672,12 +854,110 @@ static cudaError_t cheb_smooth(Context* c, int prec, HLevel* H, const T* f, T* x
   return cudaSuccess;
 }
 
+// Shared-memory image of the fused levels l0..nh-1 for nb right-hand sides in
+// vector type T: per smoothed level the stencil, diagonal (and row sums for
+// float), and r, x, t, d, d2; r and x of the coarsest. Offsets in entries of T,
+// each array starting on a 16-byte boundary. Returns the image's size in bytes.
+template <typename T>
+static size_t hfuse_layout(const Context* c, int l0, int nb, HfLevel<T>* L) {
+  const int nh = (int)c->hlev.size();
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    const size_t o = off;
+    off += (n * sizeof(T) + 15) / 16 * 16 / sizeof(T);
+    return (int)o;
+  };
+  for (int l = l0; l < nh; ++l) {
+    const HLevel& H = c->hlev[l];
+    const size_t nv = (size_t)H.nv, nvb = nv * nb;
+    HfLevel<T> z{};
+    HfLevel<T>& C = L ? L[l - l0] : z;
+    C.nx = H.nx;
+    C.ny = H.ny;
+    C.o_st = C.o_rs = C.o_dinv = C.o_t = C.o_d = C.o_d2 = -1;
+    if (l < nh - 1) {
+      C.o_st = take(9 * nv);
+      C.o_dinv = take(nv);
+      if (sizeof(T) == 4) C.o_rs = take(nv);
+      C.o_t = take(nvb);
+      C.o_d = take(nvb);
+      C.o_d2 = take(nvb);
+    }
+    C.o_r = take(nvb);
+    C.o_x = take(nvb);
+  }
+  return off * sizeof(T);
+}
+
+// First Q1 level of the fused coarse cycle for nb right-hand sides (-1: none):
+// the first level whose image with all coarser levels fits in shared memory,
+// at most kHfMaxLevels from the coarsest, and above it (a lone coarsest solve
+// gains nothing). Double levels also keep to kHfMaxDoubleEntries entries: one
+// SM retires only about two FP64 FMAs per clock on this GPU, so a 961-vertex
+// level costs ~3 us per phase in one CTA, more than a launch of its own.
+constexpr long kHfMaxDoubleEntries = 512;
+template <typename T>
+static int hfuse_level(const Context* c, int nb, size_t* bytes) {
+  const int nh = (int)c->hlev.size();
+  if (!c->opt.coarse_fuse || !c->coarse_AinvT || nh < 2) return -1;
+  const size_t budget = (size_t)c->smem_optin;
+  for (int l0 = std::max(0, nh - kHfMaxLevels); l0 <= nh - 2; ++l0) {
+    if (sizeof(T) == 8 && (long)c->hlev[l0].nv * nb > kHfMaxDoubleEntries) continue;
+    const size_t b = hfuse_layout<T>(c, l0, nb, nullptr);
+    if (b <= budget) {
+      if (bytes) *bytes = b;
+      return l0;
+    }
+  }
+  return -1;
+}
+
+// The cycle below Q1 level l0 in one launch (hcoarse_kernel): r, x are level
+// l0's vectors; the coarser levels live in the kernel's shared memory.
+template <typename T>
+static cudaError_t launch_hcoarse(Context* c, int prec, int l0, size_t bytes, int nb, const T* r, T* x,
+                                  cudaStream_t s) {
+  const int nh = (int)c->hlev.size();
+  HfArgs<T> A{};
+  A.nlev = nh - l0;
+  A.nb = nb;
+  A.nu1 = c->opt.nu1;
+  A.nu2 = c->opt.nu2;
+  A.nc = c->coarse_dim;
+  A.AinvT = c->coarse_AinvT;
+  A.r_top = r;
+  A.x_top = x;
+  hfuse_layout<T>(c, l0, nb, A.L);
+  for (int i = 0; i + 1 < A.nlev; ++i) {
+    const HLevel& H = c->hlev[l0 + i];
+    HfLevel<T>& L = A.L[i];
+    L.st_g = (const T*)(prec_double(prec) ? (const void*)H.st64 : (const void*)H.st32);
+    L.rs_g = (sizeof(T) == 4) ? (const T*)(const void*)H.rsum32 : nullptr;
+    L.dinv_g = (const T*)(prec_double(prec) ? (const void*)H.dinv64 : (const void*)H.dinv32);
+    const ChebCoef cc = cheb_coefficients(H.lmax, c->opt.cheb_degree);
+    if ((int)cc.a1.size() > kHfMaxCoef) return cudaErrorInvalidValue;
+    L.c0 = (T)cc.c0;
+    A.ncoef = (int)cc.a1.size();
+    for (size_t j = 0; j < cc.a1.size(); ++j) {
+      L.a1[j] = (T)cc.a1[j];
+      L.a2[j] = (T)cc.a2[j];
+    }
+  }
+  HDG_CUDA_TRY(cudaFuncSetAttribute(hcoarse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  hcoarse_kernel<T><<<1, kHfThreads, bytes, s>>>(A);
+  return cudaGetLastError();
+}
+
 // Alg. 1 on the h-levels: level l = -1 is the p = 0 HDG space, l >= 0 the Q1
 // levels (finest first); the last Q1 level is solved directly.
 template <typename T>
 static cudaError_t hmg(Context* c, VWork& w, int prec, int l, const T* r, T* x, cudaStream_t s) {
   const int nh = (int)c->hlev.size();
   const int nb = w.nb;
+  if (l >= 0) {
+    size_t hb = 0;
+    if (l == hfuse_level<T>(c, nb, &hb)) return launch_hcoarse<T>(c, prec, l, hb, nb, r, x, s);
+  }
   if (l == nh - 1) {
     HLevel& H = c->hlev[l];
     coarse_solve_kernel<T><<<nb, 256, 0, s>>>(H.nv, nb, c->coarse_L, r, x, w.coarse_w);
@@ -843,6 +1123,12 @@ static void release_work(VWork& w) {
 }
 
 void release_works(Context* c) {
+  for (int g = 0; g < 4; ++g) {
+    if (c->cg_graph[g]) cudaGraphExecDestroy(c->cg_graph[g]);
+    c->cg_graph[g] = nullptr;
+  }
+  if (c->h_cg) cudaFreeHost(c->h_cg);
+  c->h_cg = nullptr;
   for (int f = 0; f < 2; ++f) {
     release_work(c->w1[f]);
     if (c->wb[f]) {
@@ -1187,6 +1473,11 @@ cudaError_t build_hierarchy(Context* c, cudaStream_t s) {
   HDG_CUDA_TRY(cudaGetLastError());
   cholesky_block_kernel<<<1, 256, 0, s>>>(nc, c->coarse_L, c->err_flag);
   HDG_CUDA_TRY(cudaGetLastError());
+  if (c->opt.coarse_fuse && nc <= kHfMaxCoarse && c->hlev.size() >= 2) {   // for the fused coarse cycle
+    HDG_CUDA_TRY(ctx_alloc(c, (void**)&c->coarse_AinvT, (size_t)nc * nc * sizeof(double)));
+    coarse_inverse_kernel<<<nc, 256, (size_t)nc * sizeof(double), s>>>(nc, c->coarse_L, c->coarse_AinvT);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
   single_works(c);
   return cudaSuccess;
 }
@@ -1213,8 +1504,135 @@ __global__ void cg_p_kernel(size_t n, double* __restrict__ scal, const double* _
 }
 __global__ void cg_commit_kernel(double* scal) { scal[0] = scal[8]; }
 
-int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, int inner, hdg_solve_info* info,
-              cudaStream_t s) {
+// ---------------------------------------------------------------------------
+// Device-resident CG loop: the iterations of pcg_solve as the body of one
+// conditional WHILE node of a CUDA graph, so that a solve is one graph launch
+// with no host round trip per iteration. The body runs
+//   [zold = z]; z = V r; rz_new = r.z [, r.zold]; p = z (first pass) or
+//   z + beta p; rz = rz_new; q = A p; alpha = rz / p.q; x += alpha p;
+//   r -= alpha q; rr = r.r; check (breakdown, rel <= rtol, maxit)
+// -- the host loop's operations in its order (the host loop takes its first
+// V-cycle before the loop, the device loop in its first pass), so both give
+// the same iterates bit for bit. The graph reads only context buffers (its
+// iterate is cg_x), so one graph per inner precision serves every call;
+// rtol, |b| and maxit are device scalars set before each launch.
+// scal slots: 16 rtol, 17 |b|, 19 relres; ctl: [0] iterations, [1] status
+// (hdg_status, -1 while running), [2] maxit.
+__global__ void cgd_init_kernel(double* scal, int* ctl, double rtol, int maxit) {
+  scal[16] = rtol;
+  scal[17] = sqrt(scal[4]);
+  scal[19] = 1.0;
+  ctl[0] = 0;
+  ctl[1] = -1;
+  ctl[2] = maxit;
+}
+__global__ void cgd_p_kernel(size_t n, const double* __restrict__ scal, const int* __restrict__ ctl,
+                             const double* __restrict__ z, double* __restrict__ p, int flexible) {
+  const bool first = ctl[0] == 0;
+  double beta = 0.0;
+  if (!first) {
+    const double rz_new = scal[8];
+    beta = (flexible ? rz_new - scal[9] : rz_new) / scal[0];
+  }
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    p[t] = first ? z[t] : z[t] + beta * p[t];
+}
+__global__ void cgd_check_kernel(double* scal, int* ctl, double* hist, cudaGraphConditionalHandle h) {
+  const int it = ctl[0] + 1;
+  ctl[0] = it;
+  const double pq = scal[1];
+  int st = -1;
+  double rel = scal[19];
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    st = HDG_ERR_BREAKDOWN;
+  } else {
+    rel = sqrt(scal[2]) / scal[17];
+    if (it < 256) hist[it] = rel;
+    if (!isfinite(rel)) st = HDG_ERR_BREAKDOWN;
+    else if (rel <= scal[16]) st = HDG_OK;
+    else if (it >= ctl[2]) st = HDG_ERR_NOT_CONVERGED;
+  }
+  scal[19] = rel;
+  ctl[1] = st;
+  cudaGraphSetConditional(h, st < 0 ? 1u : 0u);
+}
+
+// z = V r for double r, z on the single-vector work, launched directly (no
+// graph of its own: it is captured into the CG loop's body)
+static cudaError_t vcycle_direct(Context* c, int prec, const double* r, double* z, cudaStream_t s) {
+  VWork& w = c->w1[prec_double(prec) ? 0 : 1];
+  const size_t n = (size_t)c->ndof;
+  const int g = grid_for(n);
+  if (prec_double(prec)) copy_convert_kernel<double, double><<<g, 256, 0, s>>>(n, r, (double*)w.pr[c->k]);
+  else copy_convert_kernel<double, float><<<g, 256, 0, s>>>(n, r, (float*)w.pr[c->k]);
+  HDG_CUDA_TRY(cudaGetLastError());
+  HDG_CUDA_TRY(vcycle_body_any(c, w, prec, s));
+  if (prec_double(prec)) copy_convert_kernel<double, double><<<g, 256, 0, s>>>(n, (const double*)w.px[c->k], z);
+  else copy_convert_kernel<float, double><<<g, 256, 0, s>>>(n, (const float*)w.px[c->k], z);
+  return cudaGetLastError();
+}
+
+// the loop body on capture stream s
+static cudaError_t cgd_body(Context* c, int inner, cudaGraphConditionalHandle h, cudaStream_t s) {
+  const size_t n = (size_t)c->ndof;
+  const int g = grid_for(n);
+  const bool flexible = inner != HDG_PREC_FP64;
+  const int outer = (inner == HDG_PREC_FP64) ? HDG_PREC_FP64 : HDG_PREC_F32X2;
+  double* sc = c->scal;
+  if (flexible) {
+    copy_convert_kernel<double, double><<<g, 256, 0, s>>>(n, c->cg_z, c->cg_zold);
+    HDG_CUDA_TRY(cudaGetLastError());
+  }
+  HDG_CUDA_TRY(vcycle_direct(c, inner, c->cg_r, c->cg_z, s));
+  if (flexible) HDG_CUDA_TRY(dots<double>(c, n, c->cg_r, c->cg_z, c->cg_r, c->cg_zold, nullptr, nullptr, sc + 8, s));
+  else HDG_CUDA_TRY(dots<double>(c, n, c->cg_r, c->cg_z, nullptr, nullptr, nullptr, nullptr, sc + 8, s));
+  cgd_p_kernel<<<g, 256, 0, s>>>(n, sc, c->cg_ctl, c->cg_z, c->cg_p, flexible ? 1 : 0);
+  HDG_CUDA_TRY(cudaGetLastError());
+  cg_commit_kernel<<<1, 1, 0, s>>>(sc);
+  HDG_CUDA_TRY(cudaGetLastError());
+  HDG_CUDA_TRY(launch_apply(c, c->k, 0, outer, c->cg_p, nullptr, c->cg_q, 1.0, 0.0, 1, s));
+  HDG_CUDA_TRY(dots<double>(c, n, c->cg_p, c->cg_q, nullptr, nullptr, nullptr, nullptr, sc + 1, s));
+  cg_xr_kernel<<<g, 256, 0, s>>>(n, sc, c->cg_p, c->cg_q, c->cg_x, c->cg_r);
+  HDG_CUDA_TRY(cudaGetLastError());
+  HDG_CUDA_TRY(dots<double>(c, n, c->cg_r, c->cg_r, nullptr, nullptr, nullptr, nullptr, sc + 2, s));
+  cgd_check_kernel<<<1, 1, 0, s>>>(sc, c->cg_ctl, c->cg_hist, h);
+  return cudaGetLastError();
+}
+
+// graph: one WHILE node whose body is cgd_body (condition initially 1)
+static cudaError_t build_cg_graph(Context* c, int inner, cudaGraphExec_t* out) {
+  cudaGraph_t G = nullptr;
+  HDG_CUDA_TRY(cudaGraphCreate(&G, 0));
+  cudaStream_t cs = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  cudaGraphNode_t wn;
+  if (e == cudaSuccess) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&wn, G, nullptr, nullptr, 0, &np);
+  }
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t eb = cgd_body(c, inner, h, cs);
+      const cudaError_t ee = cudaStreamEndCapture(cs, &body);
+      e = eb != cudaSuccess ? eb : ee;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, G, 0);
+  if (cs) cudaStreamDestroy(cs);
+  cudaGraphDestroy(G);
+  return e;
+}
+
+static int pcg_solve_impl(Context* c, const double* b, double* x, double rtol, int maxit, int inner,
+                          hdg_solve_info* info, cudaStream_t s) {
   const size_t n = (size_t)c->ndof;
   const int g = grid_for(n);
   double* r = c->cg_r;
@@ -1247,6 +1665,26 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
   if (!(bn > 0.0)) {
     if (info) info->relres = 0.0;
     return (bn == 0.0) ? HDG_OK : HDG_ERR_INVALID_ARG;
+  }
+  if (x == c->cg_x && c->cg_graph[inner]) {
+    // device-resident loop: one graph launch runs every iteration
+    cgd_init_kernel<<<1, 1, 0, s>>>(sc, c->cg_ctl, rtol, maxit);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(z, 0, n * sizeof(double), s));
+    CK(cudaGraphLaunch(c->cg_graph[inner], s));
+    double* hc = c->h_cg;
+    CK(cudaMemcpyAsync(hc, sc + 19, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hc + 1, c->cg_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hc + 8, c->cg_hist, 256 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int ctl[2];
+    std::memcpy(ctl, hc + 1, sizeof(ctl));
+    if (info) {
+      info->iterations = ctl[0];
+      info->relres = hc[0];
+      for (int i = 1; i < 256 && i <= ctl[0]; ++i) info->relres_history[i] = hc[8 + i];
+    }
+    return ctl[1] < 0 ? HDG_ERR_CUDA : ctl[1];
   }
   CK(vcycle_typed(c, c->w1[prec_double(inner) ? 0 : 1], inner, r, z, true, s));
   CK(dots<double>(c, n, r, z, nullptr, nullptr, nullptr, nullptr, sc + 0, s));
@@ -1281,6 +1719,30 @@ int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, in
   if (it > maxit) it = maxit;
   if (info) { info->iterations = it; info->relres = rel; }
   return status;
+}
+
+// One right-hand side: with CUDA graphs on, the device-resident loop (its
+// buffers made at set-up, its graph on first use per inner precision; the host
+// loop where conditional graph nodes are not available), iterating in cg_x and
+// copied to x at the end.
+int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, int inner, hdg_solve_info* info,
+              cudaStream_t s) {
+  if (!c->opt.use_graphs || c->cg_graph_failed || !c->cg_x || !c->h_cg)
+    return pcg_solve_impl(c, b, x, rtol, maxit, inner, info, s);
+  if (!c->cg_graph[inner]) {
+    const cudaError_t e = build_cg_graph(c, inner, &c->cg_graph[inner]);
+    if (e != cudaSuccess) {
+      // conditional nodes unavailable (driver): keep the host loop from now on
+      cudaGetLastError();
+      c->cg_graph[inner] = nullptr;
+      c->cg_graph_failed = true;
+      return pcg_solve_impl(c, b, x, rtol, maxit, inner, info, s);
+    }
+  }
+  const int st = pcg_solve_impl(c, b, c->cg_x, rtol, maxit, inner, info, s);
+  if (cudaMemcpyAsync(x, c->cg_x, (size_t)c->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return HDG_ERR_CUDA;
+  return st;
 }
 
 // ---------------------------------------------------------------------------

@@ -39,7 +39,8 @@ class hdg_options(ctypes.Structure):
                 ("tau_kappa", ctypes.c_int), ("smoother", ctypes.c_int), ("tensor_apply", ctypes.c_int),
                 ("fmg_start", ctypes.c_int),
                 ("max_device_bytes", ctypes.c_size_t),
-                ("wait_probe", ctypes.c_int)]
+                ("wait_probe", ctypes.c_int),
+                ("coarse_fuse", ctypes.c_int)]
 
 
 class hdg_info(ctypes.Structure):

@@ -24,7 +24,7 @@ def host(t):
 
 @pytest.mark.parametrize("reduced", [1, 0])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("f32x2", 1e-12), ("fp32", 3e-6), ("bf16", 1.2e-2)])
-@pytest.mark.parametrize("k,nb", [(0, 2), (1, 33), (3, 64), (5, 7), (7, 3)])
+@pytest.mark.parametrize("k,nb", [(0, 2), (1, 33), (3, 64), (2, 128), (5, 7), (7, 3)])
 def test_column_apply_vs_assembled(prec, tol, k, nb, reduced):
     """FP64 / F32X2: rounding of an 8(k+1)-term sum (~48 bits for F32X2); FP32 and
     BF16 blocks: entry rounding 2^-24 / 2^-9 with FP32 accumulation. Bound
