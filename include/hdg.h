@@ -164,6 +164,15 @@ typedef struct {
                                  most 1024 unknowns) are phases of one launch
                                  (default); 0: one launch per step on every
                                  level                                        */
+  int top_accum;              /* 1: FP32 / BF16 V-cycles keep the finest
+                                 level's correction as a double-float pair
+                                 (two floats, ~48 bits) and prolongate into it
+                                 in double-float arithmetic; every operator of
+                                 the cycle stays in float, BF16 cycles use the
+                                 FP32 blocks on the finest level and the BF16
+                                 blocks below: the iteration counts of FP64
+                                 cycles (default); 0: the correction in float,
+                                 BF16 blocks on every p-level                */
 } hdg_options;
 
 typedef struct {

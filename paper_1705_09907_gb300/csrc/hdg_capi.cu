@@ -51,7 +51,7 @@ void hdg_default_options(hdg_options* o) {
   o->nu1 = 2; o->nu2 = 2; o->coarse_n = 2; o->tau = 1.0; o->cheb_degree = 2; o->mixed = 1; o->use_graphs = 1;
   o->autotune = 1; o->reduced = 1; o->tau_kappa = 0;
   o->smoother = 0; o->tensor_apply = 1; o->fmg_start = 0; o->max_device_bytes = 0; o->wait_probe = 0;
-  o->coarse_fuse = 1;
+  o->coarse_fuse = 1; o->top_accum = 1;
 }
 
 const char* hdg_error_string(int s) {
@@ -183,6 +183,12 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
       const std::vector<float> Pp32(Pp.begin(), Pp.end());
       TRY(ctx_alloc(c, (void**)&L.Pp32, Pp.size() * sizeof(float)));
       TRY(cudaMemcpyAsync(L.Pp32, Pp32.data(), Pp.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+      // and the rest P - float(P) for the double-float prolongation into the
+      // finest level of a float cycle
+      std::vector<float> Pplo(Pp.size());
+      for (size_t q = 0; q < Pp.size(); ++q) Pplo[q] = (float)(Pp[q] - (double)Pp32[q]);
+      TRY(ctx_alloc(c, (void**)&L.Pplo, Pp.size() * sizeof(float)));
+      TRY(cudaMemcpyAsync(L.Pplo, Pplo.data(), Pp.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     }
   }
   TRY(launch_local_setup(c, s));
@@ -251,7 +257,7 @@ int hdg_setup(const hdg_mesh* mesh, int k, const double* kappa, const hdg_option
       o.cheb_degree < 1 || o.cheb_degree > 8 || o.reduced < 0 || o.reduced > 2 ||
       o.tau_kappa < 0 || o.tau_kappa > 1 || o.wait_probe < 0 || o.wait_probe > 64 || o.smoother < 0 ||
       o.smoother > 1 || o.fmg_start < 0 || o.fmg_start > 16 ||
-      o.tensor_apply < 0 || o.tensor_apply > 1 || o.coarse_fuse < 0 || o.coarse_fuse > 1)
+      o.tensor_apply < 0 || o.tensor_apply > 1 || o.coarse_fuse < 0 || o.coarse_fuse > 1 || o.top_accum < 0 || o.top_accum > 1)
     return HDG_ERR_INVALID_ARG;
   const long nel = (long)mesh->nx * mesh->ny;
   const long ne = (long)(mesh->nx + 1) * mesh->ny + (long)mesh->nx * (mesh->ny + 1);

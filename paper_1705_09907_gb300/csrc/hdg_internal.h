@@ -65,6 +65,7 @@ struct PLevel {
   double* Sdense = nullptr;                 // [nel][m][m] FP64 element blocks
   double* Pp = nullptr;                     // prolongation from p-1 [(p+1) x p] (device)
   float* Pp32 = nullptr;                    // the same in float (float V-cycles)
+  float* Pplo = nullptr;                    // Pp - Pp32 in float (double-float prolongation)
   // V-cycle work vectors, [ndof] each, per precision (d = double, f = float)
   double *r64 = nullptr, *x64 = nullptr, *t64 = nullptr, *d64 = nullptr;
   float *r32 = nullptr, *x32 = nullptr, *t32 = nullptr, *d32 = nullptr;
@@ -115,6 +116,11 @@ struct VWork {
   size_t own_bytes = 0;                     // their total size
   size_t cap = ~size_t(0);                  // most it may allocate (memory cap)
   void* red_z = nullptr;                    // batched reduced-apply scratch [4(k+1)][nel][nb]
+  // float cycles: low part of the finest level's correction (its high part is
+  // px[k]) and a float scratch of that level ([ndof][nb] each; null: the
+  // correction is accumulated in float)
+  float* top_lo = nullptr;
+  float* top_u = nullptr;
 };
 
 // Per-level vectors of the full multigrid cycle (double, one right-hand side):
@@ -154,6 +160,7 @@ struct Context {
   std::vector<HLevel> hlev;                 // finest Q1 first
   double* coarse_L = nullptr;               // dense FP64 Cholesky factor [nc][nc]
   double* coarse_AinvT = nullptr;           // its inverse, transposed (fused coarse cycle; nc <= 1024)
+  float *top_lo32 = nullptr, *top_u32 = nullptr;   // the single float work's top_lo, top_u
   int coarse_dim = 0;
   double* coarse_rhs = nullptr;             // [nc] FP64 scratch
   // CG / reduction scratch

@@ -40,7 +40,8 @@ class hdg_options(ctypes.Structure):
                 ("fmg_start", ctypes.c_int),
                 ("max_device_bytes", ctypes.c_size_t),
                 ("wait_probe", ctypes.c_int),
-                ("coarse_fuse", ctypes.c_int)]
+                ("coarse_fuse", ctypes.c_int),
+                ("top_accum", ctypes.c_int)]
 
 
 class hdg_info(ctypes.Structure):

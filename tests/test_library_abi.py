@@ -80,13 +80,13 @@ def test_options_validated_before_any_device_work(lib):
     d = hdg.default_options()
     assert (d.nu1, d.nu2, d.coarse_n, d.tau, d.cheb_degree, d.mixed, d.use_graphs, d.autotune, d.reduced,
             d.tau_kappa, d.smoother, d.tensor_apply, d.fmg_start, d.max_device_bytes, d.wait_probe,
-            d.coarse_fuse) == (2, 2, 2, 1.0, 2, 1, 1, 1, 1, 0, 0, 1, 0, 0, 0, 1)
+            d.coarse_fuse, d.top_accum) == (2, 2, 2, 1.0, 2, 1, 1, 1, 1, 0, 0, 1, 0, 0, 0, 1, 1)
     ctx = ctypes.c_void_p()
     m = hdg.hdg_mesh(4, 4, 0.0, 0.0, 1.0, 1.0)
     for bad in ({"reduced": 3}, {"reduced": -1}, {"tau_kappa": 2}, {"tau": 0.0}, {"nu1": 0},
                 {"cheb_degree": 9}, {"coarse_n": 1}, {"wait_probe": -1}, {"wait_probe": 65},
                 {"smoother": 2}, {"smoother": -1}, {"fmg_start": -1}, {"fmg_start": 17},
-                {"tensor_apply": 2}, {"coarse_fuse": -1}, {"coarse_fuse": 2}):
+                {"tensor_apply": 2}, {"coarse_fuse": -1}, {"coarse_fuse": 2}, {"top_accum": 2}):
         o = hdg.default_options(**bad)
         st = hdg.hdg_setup(ctypes.byref(m), 1, ctypes.c_void_p(16), ctypes.byref(o), None, ctypes.byref(ctx))
         assert st == hdg.HDG_ERR_INVALID_ARG, bad
@@ -99,4 +99,4 @@ def test_options_struct_matches_header(lib):
     o = hdg.hdg_options()
     ctypes.memset(ctypes.byref(o), 0xFF, ctypes.sizeof(o))
     lib.hdg_default_options(ctypes.byref(o))
-    assert o.max_device_bytes == 0 and o.wait_probe == 0 and o.tau_kappa == 0 and o.coarse_fuse == 1
+    assert o.max_device_bytes == 0 and o.wait_probe == 0 and o.tau_kappa == 0 and o.coarse_fuse == 1 and o.top_accum == 1
