@@ -307,7 +307,10 @@ def run_ours(args):
     fq_h = inputs.constant_f(N, k)
     kap_d = torch.as_tensor(kap, device="cuda")
     fq_d = torch.as_tensor(fq_h, device="cuda")
-    solver = hdg.HDGSolver(N, N, k, kap_d)
+    # a profiling run launches the CG loop from the host (use_graphs = 0: the
+    # same kernels, launched directly): profilers do not see the kernels of a
+    # conditional graph node's body
+    solver = hdg.HDGSolver(N, N, k, kap_d, use_graphs=0 if args.profile else 1)
     info = solver.info
     rtol = 1e-10
     u = torch.empty((solver.nel, (k + 1) ** 2), dtype=torch.float64, device="cuda")
@@ -370,7 +373,7 @@ def run_ours(args):
         torch.cuda.nvtx.range_pop()
         sbm.close()
         # the FP64 step with the FSAI smoother (NVTX range fsai_fp64_step)
-        sfs = hdg.HDGSolver(N, N, k, kap_d, smoother=1)
+        sfs = hdg.HDGSolver(N, N, k, kap_d, smoother=1, use_graphs=0)
         bf = sfs.condense_rhs(fq_d)
         sfs.solve(bf, rtol=rtol, maxit=200)
         torch.cuda.nvtx.range_push("fsai_fp64_step")
@@ -920,6 +923,44 @@ def run_profile_apply(args):
     print(json.dumps({"profile_apply": True, "n": N, "k": k, "prec": prec}))
 
 
+def run_profile_small(args):
+    """Small fixed launch sequences for kernel captures of the column apply and
+    the V-cycle (about 2 GB on the device): the column-batched apply of 64
+    Fourier right-hand sides at 256^2, k = 5, kappa = 1 in --prec (NVTX range
+    cols, after --warmup untimed ones), then V-cycles in --prec on a 256^2,
+    k = 2 lognormal-kappa context (NVTX range vcycle)."""
+    import torch
+
+    from paper_1705_09907_gb300 import hdg, inputs
+
+    prec = args.prec
+    dt = torch.float64 if prec in ("fp64", "f32x2") else torch.float32
+    sbm = hdg.HDGSolver(256, 256, 5, torch.ones(256 * 256, dtype=torch.float64, device="cuda"), autotune=0)
+    B = sbm.condense_rhs(torch.as_tensor(inputs.fourier_rhs(256, 5, 64, seed=3), device="cuda")).to(dt)
+    Y = torch.empty_like(B)
+    for _ in range(args.warmup):
+        sbm.apply(B, prec, out=Y)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("cols")
+    for _ in range(3):
+        sbm.apply(B, prec, out=Y)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    sbm.close()
+    s = hdg.HDGSolver(256, 256, 2, torch.as_tensor(inputs.lognormal_kappa(256, SEED), device="cuda"))
+    r = torch.as_tensor(inputs.random_trace(s.n_edges, 2, seed=1), device="cuda").to(dt)
+    for _ in range(args.warmup):
+        s.vcycle(r, prec=prec)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("vcycle")
+    for _ in range(3):
+        s.vcycle(r, prec=prec)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    s.close()
+    print(json.dumps({"profile_small": True, "prec": prec}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -933,6 +974,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="one solve step and 3 applies per precision, then exit")
     ap.add_argument("--profile-apply", action="store_true",
                     help="3 reduced and 3 dense condensed-block applies in --prec (kernel captures)")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="column applies (256^2, k = 5, 64 right-hand sides) and V-cycles (256^2, k = 2) in --prec")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16", "f32x2"])
     ap.add_argument("--clocks-log", default=None,
                     help="CSV path for the nvidia-smi clock samples (default: a temporary file)")
@@ -941,6 +984,8 @@ def main():
         run_reference(args)
     elif args.profile_apply:
         run_profile_apply(args)
+    elif args.profile_small:
+        run_profile_small(args)
     else:
         run_ours(args)
 

@@ -1764,8 +1764,33 @@ static cudaError_t build_cg_graph(Context* c, int inner, cudaGraphExec_t* out) {
     }
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(out, G, 0);
-  if (cs) cudaStreamDestroy(cs);
   cudaGraphDestroy(G);
+  if (e == cudaSuccess) {
+    // kernels of one V-cycle (hdg_info.vcycle_kernels): the cycle captured alone
+    cudaGraph_t Gv = nullptr;
+    VWork& w = c->w1[prec_double(inner) ? 0 : 1];
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t eb = vcycle_body_any(c, w, inner, cs);
+      const cudaError_t ee = cudaStreamEndCapture(cs, &Gv);
+      e = eb != cudaSuccess ? eb : ee;
+    }
+    size_t nn = 0;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(Gv, nullptr, &nn);
+    if (e == cudaSuccess) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      e = cudaGraphGetNodes(Gv, nodes.data(), &nn);
+      int nk = 0;
+      for (size_t q = 0; q < nn && e == cudaSuccess; ++q) {
+        cudaGraphNodeType ty;
+        e = cudaGraphNodeGetType(nodes[q], &ty);
+        if (ty == cudaGraphNodeTypeKernel) ++nk;
+      }
+      if (e == cudaSuccess) c->vcycle_kernels = nk;
+    }
+    if (Gv) cudaGraphDestroy(Gv);
+  }
+  if (cs) cudaStreamDestroy(cs);
   return e;
 }
 
