@@ -363,10 +363,15 @@ int hdg_solve(void* ctx, const double* b, double* lambda, int nrhs, double rtol,
  * n independent problems of uneven size solved together (1 <= n <= 64
  * contexts, e.g. from hdg_setup_batch, all on the current device, each at most
  * once): hdg_solve of context q on (b[q], lambda[q]) with the common rtol,
- * maxit and inner precision, each on a stream and host thread of its own, so
- * the instances share the GPU at the same time (small meshes fill the SMs that
- * large ones leave idle). Every instance runs the kernels of its own hdg_solve,
- * so each lambda[q] is bitwise what hdg_solve gives for it alone. The call
+ * maxit and inner precision. With use_graphs on in every context (and no
+ * fmg_start) all instances form one CUDA graph launched once: per instance a
+ * chain of its set-up kernels, a conditional WHILE node iterating its CG and
+ * the copy of its solution, the chains independent, so the instances share
+ * the GPU at the same time (small meshes fill the SMs that large ones leave
+ * idle) with no host round trip until all have finished; otherwise each runs
+ * on a stream and host thread of its own. Every instance runs the kernels of
+ * its own hdg_solve, so each lambda[q] is bitwise what hdg_solve gives for it
+ * alone. The call
  * orders itself after the work already issued on `stream`, makes `stream` wait
  * for every instance, and returns when all have finished. b[q], lambda[q]:
  * device [ndof_q] doubles. infos (host [n], may be NULL) and statuses (host

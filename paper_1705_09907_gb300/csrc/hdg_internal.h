@@ -256,6 +256,12 @@ cudaError_t build_hierarchy(Context* c, cudaStream_t s);
 cudaError_t vcycle(Context* c, int prec, const void* r, void* z, int nb, cudaStream_t s);
 int pcg_solve(Context* c, const double* b, double* x, double rtol, int maxit, int inner,
               hdg_solve_info* info, cudaStream_t s);
+// one graph for several contexts' one-right-hand-side solves (hdg_solve_multi):
+// add one instance's chain, then after the launch fetch and read its results
+cudaError_t cg_multi_add(Context* c, int inner, const double* b, double* lambda, double rtol, int maxit, cudaGraph_t G,
+                         cudaStream_t cs);
+cudaError_t cg_multi_fetch(Context* c, cudaStream_t s);
+int cg_multi_result(Context* c, hdg_solve_info* info);
 // CG on nb right-hand sides at once (b, x: [ndof][nb]), one V-cycle of all
 // columns per iteration, per-column step lengths; a column stops updating once
 // its residual meets rtol

@@ -30,12 +30,28 @@ __global__ void dots_kernel(size_t n, const T* __restrict__ a0, const T* __restr
                             const T* __restrict__ a1, const T* __restrict__ b1, const T* __restrict__ a2,
                             const T* __restrict__ b2, double* __restrict__ part) {
   __shared__ double sh[3][256];
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
-    s0 += (double)a0[t] * (double)b0[t];
-    if (a1) s1 += (double)a1[t] * (double)b1[t];
-    if (a2) s2 += (double)a2[t] * (double)b2[t];
+  // four independent partial sums per thread (loads of four strides in flight),
+  // combined in a fixed order
+  double p0[4] = {0.0, 0.0, 0.0, 0.0}, p1[4] = {0.0, 0.0, 0.0, 0.0}, p2[4] = {0.0, 0.0, 0.0, 0.0};
+  const size_t step = (size_t)gridDim.x * blockDim.x;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; t + 3 * step < n; t += 4 * step) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const size_t o = t + u * step;
+      p0[u] += (double)a0[o] * (double)b0[o];
+      if (a1) p1[u] += (double)a1[o] * (double)b1[o];
+      if (a2) p2[u] += (double)a2[o] * (double)b2[o];
+    }
   }
+  for (; t < n; t += step) {
+    p0[0] += (double)a0[t] * (double)b0[t];
+    if (a1) p1[0] += (double)a1[t] * (double)b1[t];
+    if (a2) p2[0] += (double)a2[t] * (double)b2[t];
+  }
+  const double s0 = (p0[0] + p0[1]) + (p0[2] + p0[3]);
+  const double s1 = (p1[0] + p1[1]) + (p1[2] + p1[3]);
+  const double s2 = (p2[0] + p2[1]) + (p2[2] + p2[3]);
   sh[0][threadIdx.x] = s0; sh[1][threadIdx.x] = s1; sh[2][threadIdx.x] = s2;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
@@ -1882,6 +1898,101 @@ static int pcg_solve_impl(Context* c, const double* b, double* x, double rtol, i
   if (it > maxit) it = maxit;
   if (info) { info->iterations = it; info->relres = rel; }
   return status;
+}
+
+// ---------------------------------------------------------------------------
+// Several contexts' solves as one graph (hdg_solve_multi): per instance a
+// chain prologue -> WHILE node (the body of the device-resident loop) ->
+// epilogue, the chains independent, so one launch solves every instance and
+// the GPU overlaps them. The prologue does on the device what pcg_solve's
+// host part does (|b|, x = 0, r = b, z = 0, the control words); a zero b stops
+// the loop before its first pass (condition 0, status OK, x = 0).
+__global__ void cgd_init_multi_kernel(double* scal, int* ctl, double rtol, int maxit, cudaGraphConditionalHandle h) {
+  const double bn = sqrt(scal[4]);
+  scal[16] = rtol;
+  scal[17] = bn;
+  scal[19] = bn > 0.0 ? 1.0 : 0.0;
+  ctl[0] = 0;
+  ctl[1] = bn > 0.0 ? -1 : (bn == 0.0 ? HDG_OK : HDG_ERR_INVALID_ARG);
+  ctl[2] = maxit;
+  cudaGraphSetConditional(h, bn > 0.0 ? 1u : 0u);
+}
+
+// Adds instance c's chain to G (capture stream cs); solution to lambda.
+cudaError_t cg_multi_add(Context* c, int inner, const double* b, double* lambda, double rtol, int maxit, cudaGraph_t G,
+                         cudaStream_t cs) {
+  if (!c->cg_x || !c->cg_ctl || !c->cg_hist || !c->h_cg) return cudaErrorInvalidValue;
+  const size_t n = (size_t)c->ndof;
+  const int g = grid_for(n);
+  cudaGraphConditionalHandle h;
+  HDG_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault));
+  // prologue
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = dots<double>(c, n, b, b, nullptr, nullptr, nullptr, nullptr, c->scal + 4, cs);
+  if (e == cudaSuccess) {
+    cgd_init_multi_kernel<<<1, 1, 0, cs>>>(c->scal, c->cg_ctl, rtol, maxit, h);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = vec_fill(c->cg_x, HDG_PREC_FP64, n, cs);
+  if (e == cudaSuccess) e = vec_fill(c->cg_z, HDG_PREC_FP64, n, cs);
+  if (e == cudaSuccess) {
+    copy_convert_kernel<double, double><<<g, 256, 0, cs>>>(n, b, c->cg_r);
+    e = cudaGetLastError();
+  }
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t ndeps = 0;
+  std::vector<cudaGraphNode_t> dv;
+  if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, &edata, &ndeps);
+  if (e == cudaSuccess) dv.assign(deps, deps + ndeps);
+  cudaGraph_t Gout = G;
+  const cudaError_t ee = cudaStreamEndCapture(cs, &Gout);
+  HDG_CUDA_TRY(e);
+  HDG_CUDA_TRY(ee);
+  // the loop
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t wn;
+  HDG_CUDA_TRY(cudaGraphAddNode(&wn, G, dv.data(), nullptr, dv.size(), &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  e = cgd_body(c, inner, h, cs);
+  const cudaError_t eb = cudaStreamEndCapture(cs, &body);
+  HDG_CUDA_TRY(e);
+  HDG_CUDA_TRY(eb);
+  // epilogue
+  HDG_CUDA_TRY(cudaStreamBeginCaptureToGraph(cs, G, &wn, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  copy_convert_kernel<double, double><<<g, 256, 0, cs>>>(n, c->cg_x, lambda);
+  e = cudaGetLastError();
+  Gout = G;
+  const cudaError_t e2 = cudaStreamEndCapture(cs, &Gout);
+  HDG_CUDA_TRY(e);
+  return e2;
+}
+
+// After the graph: copies of instance c's results to its pinned buffer (stream s)
+cudaError_t cg_multi_fetch(Context* c, cudaStream_t s) {
+  double* hc = c->h_cg;
+  HDG_CUDA_TRY(cudaMemcpyAsync(hc, c->scal + 19, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HDG_CUDA_TRY(cudaMemcpyAsync(hc + 1, c->cg_ctl, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  return cudaMemcpyAsync(hc + 8, c->cg_hist, 256 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+// ... and, once they have arrived, the status and the solve information
+int cg_multi_result(Context* c, hdg_solve_info* info) {
+  const double* hc = c->h_cg;
+  int ctl[2];
+  std::memcpy(ctl, hc + 1, sizeof(ctl));
+  if (info) {
+    info->iterations = ctl[0];
+    info->relres = hc[0];
+    info->relres_history[0] = 1.0;
+    for (int i = 1; i < 256 && i <= ctl[0]; ++i) info->relres_history[i] = hc[8 + i];
+  }
+  return ctl[1] < 0 ? HDG_ERR_CUDA : ctl[1];
 }
 
 // One right-hand side: with CUDA graphs on, the device-resident loop (its

@@ -67,3 +67,36 @@ def test_solve_multi_rejects_bad_arguments():
         hdg.solve_multi([s], [b], inner="fp32")
     assert e.value.status == hdg.HDG_ERR_UNSUPPORTED
     s.close()
+
+
+def test_solve_multi_one_graph_statuses_and_zero_rhs():
+    """The one-graph path: a zero right-hand side stops its loop before the first
+    pass (status OK, no iterations, lambda = 0); a small maxit leaves an
+    instance NOT_CONVERGED with exactly maxit iterations; the others converge as
+    in their own solves; a context without graphs sends the call down the
+    per-thread path with the same results."""
+    from paper_1705_09907_gb300 import hdg
+    probs = _problems([(16, 2), (32, 3), (24, 1)], 60)
+    sols = hdg.setup_batch([(N, N, k, torch.as_tensor(kap, device="cuda")) for N, k, kap, _ in probs])
+    bs = [s.condense_rhs(torch.as_tensor(fq, device="cuda")) for s, (_, _, _, fq) in zip(sols, probs)]
+    bs[2] = torch.zeros_like(bs[2])
+    lams, infos = hdg.solve_multi(sols, bs, rtol=1e-10, maxit=300, raise_on_error=False)
+    assert infos[2]["status"] == hdg.HDG_OK and infos[2]["iterations"] == 0
+    assert torch.count_nonzero(lams[2]) == 0
+    for q in (0, 1):
+        own, inf = sols[q].solve(bs[q], rtol=1e-10, maxit=300)
+        assert torch.equal(own, lams[q]) and infos[q]["iterations"] == inf["iterations"]
+    lams3, infos3 = hdg.solve_multi(sols[:2], bs[:2], rtol=1e-12, maxit=3, raise_on_error=False)
+    assert all(i["status"] == hdg.HDG_ERR_NOT_CONVERGED and i["iterations"] == 3 for i in infos3)
+    for s in sols:
+        s.close()
+    # a context with use_graphs = 0 among them: the per-thread path
+    N, k, kap, fq = probs[1]
+    a = hdg.HDGSolver(N, N, k, torch.as_tensor(kap, device="cuda"), autotune=0)
+    c = hdg.HDGSolver(N, N, k, torch.as_tensor(kap, device="cuda"), autotune=0, use_graphs=0)
+    b = a.condense_rhs(torch.as_tensor(fq, device="cuda"))
+    lm, im = hdg.solve_multi([a, c], [b, b.clone()], rtol=1e-10, maxit=300)
+    assert im[0]["iterations"] == im[1]["iterations"] and im[0]["status"] == hdg.HDG_OK
+    assert torch.equal(lm[0], lm[1])
+    a.close()
+    c.close()
