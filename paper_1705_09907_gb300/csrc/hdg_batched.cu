@@ -219,12 +219,14 @@ __device__ __forceinline__ void drain_item(const BatchedArgs& a, uint32_t tm, in
           so = (float)a.kappa[i + nx * j];
           sn = (float)a.kappa[type == 0 ? (i - 1) + nx * j : i + nx * (j - 1)];
         }
-        // fixed-trip loops over the tile's columns keep v in registers
+        // fixed-trip loops over the tile's columns keep v in registers; the
+        // face's rows are nrhs apart from one base address
+        float* yq = ybase + (size_t)eout * n1 * a.nrhs;
+        const size_t rs = (size_t)a.nrhs;
 #pragma unroll
         for (int q = 0; q < kTileN / 2; ++q)
           if (q < n1)
-            ybase[((size_t)eout * n1 + q) * a.nrhs] =
-                bndrow ? 0.0f : so * __uint_as_float(vt[q]) + sn * __uint_as_float(vt[kTileN / 2 + q]);
+            yq[q * rs] = bndrow ? 0.0f : so * __uint_as_float(vt[q]) + sn * __uint_as_float(vt[kTileN / 2 + q]);
         if (type == 0 && i == nx - 1) {
           const int eb = nx + (nx + 1) * j;
           for (int q = 0; q < n1; ++q) ybase[((size_t)eb * n1 + q) * a.nrhs] = 0.0f;
