@@ -844,7 +844,11 @@ def run_ours(args):
                          % (nel * q_red * 8 / 1e6, nel * 16 * n1 * n1 * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "setup_ms": info["setup_ms"], "device_bytes": info["device_bytes"],
-        "roofline": roof, "trace_apply": tra, "trace_apply_dense": trd, "local_ops_ms": local_ms, "mixed": mixed, "mixed_1024_k3": m3,
+        "roofline": roof, "trace_apply": tra, "trace_apply_dense": trd,
+        "paper_context": {"what": "the paper's matrix-free FP64 trace apply on a Xeon Phi KNL 7210 ran at about 80% of "
+                                  "its STREAM bandwidth (about 240 of 300 GB/s); context only, not a target",
+                          "this_gpu_fp64_dense_frac_hbm": trd.get("fp64", {}).get("frac_hbm")},
+        "local_ops_ms": local_ms, "mixed": mixed, "mixed_1024_k3": m3,
         "batched_solve": bs, "tau_kappa_variant": tk, "mixed_vs_oracle": mvo, "fsai_smoother": fsai,
         "config1_16x16_k1": c1, "adjoint_512_k2": adj, "fmg": fmg,
         "shared_batched_apply": sb, "multi_instance_apply": mi,
