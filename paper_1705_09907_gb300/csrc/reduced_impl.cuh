@@ -250,6 +250,15 @@ struct Form {
     if (cv) val = fma(be, cv[o], val);
     return val;
   }
+  // the same with the addend c already loaded (any value when cv is null)
+  __device__ __forceinline__ T with(T s, T c) const {
+    if (f == 0) return s;
+    if (f == 1) return c - s;
+    if (f == 2) return c + s;
+    T val = al * s;
+    if (cv) val = fma(be, c, val);
+    return val;
+  }
 };
 
 // Pass 1 of the two-launch form for element K: z_K = S_K v_K into the scratch.
@@ -307,14 +316,39 @@ __device__ __forceinline__ void face_body(const RedArgs& a, long K0, int t, T* s
   __syncthreads();
   const Form<T> form(a);
   const int cnt = (int)((nel - K0) < kFaceThreads ? (nel - K0) : kFaceThreads);
-  for (int idx = t; idx < cnt * N1; idx += kFaceThreads) {
-    const int tt = idx / N1, q = idx - tt * N1;
-    const long Kt = K0 + tt;
-    const int i = (int)(Kt % nx), j = (int)(Kt / nx);
-    const size_t ow = (size_t)(i + (long)(nx + 1) * j) * N1 + q;
-    const size_t os = (size_t)(nv + i + (long)nx * j) * N1 + q;
-    y[ow] = i > 0 ? form(sw[idx], ow) : T(0);
-    y[os] = j > 0 ? form(ss[idx], os) : T(0);
+  // every thread has at most N1 outputs of each face type: their addends are
+  // all loaded before the first store, so the loads overlap
+  size_t ow[N1], os[N1];
+  bool hw[N1], hs[N1];
+  T cw[N1], cs[N1];
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int idx = t + u * kFaceThreads;
+    hw[u] = false;
+    hs[u] = false;
+    ow[u] = os[u] = 0;
+    cw[u] = cs[u] = T(0);
+    if (idx < cnt * N1) {
+      const int tt = idx / N1, q = idx - tt * N1;
+      const long Kt = K0 + tt;
+      const int i = (int)(Kt % nx), j = (int)(Kt / nx);
+      ow[u] = (size_t)(i + (long)(nx + 1) * j) * N1 + q;
+      os[u] = (size_t)(nv + i + (long)nx * j) * N1 + q;
+      hw[u] = i > 0;
+      hs[u] = j > 0;
+      if (form.cv) {
+        cw[u] = form.cv[ow[u]];
+        cs[u] = form.cv[os[u]];
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int idx = t + u * kFaceThreads;
+    if (idx < cnt * N1) {
+      y[ow[u]] = hw[u] ? form.with(sw[idx], cw[u]) : T(0);
+      y[os[u]] = hs[u] ? form.with(ss[idx], cs[u]) : T(0);
+    }
   }
 }
 
