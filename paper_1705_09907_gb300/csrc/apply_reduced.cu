@@ -69,6 +69,13 @@ __global__ void __launch_bounds__(kFaceThreads) reduced_face_kernel(const RedArg
 // both forms give identical results.
 constexpr int kTileWarps = 2, kRowsPerWarp = 4, kTileRows = kTileWarps * kRowsPerWarp;
 
+// the value of the lane to the left (lane 0 keeps its own)
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ dd shfl_up1(dd v) {
+  return dd(__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1));
+}
+
 template <int N1, typename TS, typename T, bool DIFF>
 __global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const RedArgs a) {
   __shared__ T north[kTileWarps][N1][32];
@@ -80,9 +87,10 @@ __global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const Red
   const int i = bx * 32 + lane;
   const int j0 = by * kTileRows + w * kRowsPerWarp;
   const bool col = i < nx;
+  using VT = typename VecT<T>::type;
   T* __restrict__ z = (T*)a.z;
-  T* __restrict__ y = (T*)a.y;
-  const Form<T> form(a);
+  VT* __restrict__ y = (VT*)a.y;
+  const Form<VT> form(a);
   const long nv = (long)(nx + 1) * ny;
   T zn_prev[N1], zs_first[N1];
 #pragma unroll
@@ -103,19 +111,19 @@ __global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const Red
     }
     T ew[N1];                                             // E output of the element to the left
 #pragma unroll
-    for (int q = 0; q < N1; ++q) ew[q] = __shfl_up_sync(0xffffffffu, ze[q], 1);
+    for (int q = 0; q < N1; ++q) ew[q] = shfl_up1(ze[q]);
     if (col) {
       const long eW = i + (long)(nx + 1) * j, eS = nv + i + (long)nx * j;
       // W face
       if (i == 0) {
 #pragma unroll
-        for (int q = 0; q < N1; ++q) y[eW * N1 + q] = T(0);
+        for (int q = 0; q < N1; ++q) y[eW * N1 + q] = VT(0);
       } else if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < N1; ++q) z[(size_t)(0 * N1 + q) * nel + K] = zw[q];
       } else {
 #pragma unroll
-        for (int q = 0; q < N1; ++q) y[eW * N1 + q] = form(zw[q] + ew[q], (size_t)eW * N1 + q);
+        for (int q = 0; q < N1; ++q) y[eW * N1 + q] = form(to_vec(zw[q] + ew[q]), (size_t)eW * N1 + q);
       }
       if (lane == 31 && i < nx - 1) {
 #pragma unroll
@@ -123,15 +131,15 @@ __global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const Red
       }
       if (i == nx - 1) {
 #pragma unroll
-        for (int q = 0; q < N1; ++q) y[(eW + 1) * N1 + q] = T(0);
+        for (int q = 0; q < N1; ++q) y[(eW + 1) * N1 + q] = VT(0);
       }
       // S face
       if (j == 0) {
 #pragma unroll
-        for (int q = 0; q < N1; ++q) y[eS * N1 + q] = T(0);
+        for (int q = 0; q < N1; ++q) y[eS * N1 + q] = VT(0);
       } else if (r > 0) {
 #pragma unroll
-        for (int q = 0; q < N1; ++q) y[eS * N1 + q] = form(zs[q] + zn_prev[q], (size_t)eS * N1 + q);
+        for (int q = 0; q < N1; ++q) y[eS * N1 + q] = form(to_vec(zs[q] + zn_prev[q]), (size_t)eS * N1 + q);
       } else if (w > 0) {
 #pragma unroll
         for (int q = 0; q < N1; ++q) zs_first[q] = zs[q];
@@ -141,7 +149,7 @@ __global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const Red
       }
       if (j == ny - 1) {
 #pragma unroll
-        for (int q = 0; q < N1; ++q) y[(eS + nx) * N1 + q] = T(0);
+        for (int q = 0; q < N1; ++q) y[(eS + nx) * N1 + q] = VT(0);
       } else if (w == kTileWarps - 1 && r == kRowsPerWarp - 1) {
 #pragma unroll
         for (int q = 0; q < N1; ++q) z[(size_t)(3 * N1 + q) * nel + K] = zn[q];
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(32 * kTileWarps) reduced_tile_kernel(const Red
   if (w > 0 && rows > 0 && col && j0 > 0) {
     const long eS = nv + i + (long)nx * j0;
 #pragma unroll
-    for (int q = 0; q < N1; ++q) y[eS * N1 + q] = form(zs_first[q] + north[w - 1][q][lane], (size_t)eS * N1 + q);
+    for (int q = 0; q < N1; ++q) y[eS * N1 + q] = form(to_vec(zs_first[q] + north[w - 1][q][lane]), (size_t)eS * N1 + q);
   }
 }
 
@@ -173,9 +181,10 @@ __global__ void __launch_bounds__(256) reduced_fix_kernel(const RedArgs a) {
   const long nvert = (long)(tiles_x - 1) * ny, total = nvert + (long)(tiles_y - 1) * nx;
   const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (t >= total) return;
+  using VT = typename VecT<T>::type;
   const T* __restrict__ z = (const T*)a.z;
-  T* __restrict__ y = (T*)a.y;
-  const Form<T> form(a);
+  VT* __restrict__ y = (VT*)a.y;
+  const Form<VT> form(a);
   long e, K, Kn;
   int fo;
   if (t < nvert) {
@@ -190,7 +199,7 @@ __global__ void __launch_bounds__(256) reduced_fix_kernel(const RedArgs a) {
   }
 #pragma unroll
   for (int q = 0; q < N1; ++q)
-    y[e * N1 + q] = form(z[(size_t)(fo * N1 + q) * nel + K] + z[(size_t)((fo + 1) * N1 + q) * nel + Kn],
+    y[e * N1 + q] = form(to_vec(z[(size_t)(fo * N1 + q) * nel + K] + z[(size_t)((fo + 1) * N1 + q) * nel + Kn]),
                          (size_t)e * N1 + q);
 }
 
@@ -272,7 +281,7 @@ __device__ Coord coord_of(int n1, int b, int idx) {
 }
 
 __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict__ Sd, double* __restrict__ R64,
-                                      float* __restrict__ R32) {
+                                      float* __restrict__ R32, float2* __restrict__ R2) {
   const int h = n1 / 2, se = h + (n1 & 1), so = h;
   const int d[4] = {2 * se, so + se, se + so, 2 * so};
   int Q = 0;
@@ -296,6 +305,10 @@ __global__ void reduced_blocks_kernel(long nel, int n1, const double* __restrict
     const double val = acc / (double)(ci.cnt * cj.cnt);
     R64[red_base(K, Q) + (size_t)q * 32] = val;
     if (R32) R32[red_index32(K, Q, q)] = (float)val;
+    if (R2) {
+      const float hi = (float)val;
+      R2[red_base(K, Q) + (size_t)q * 32] = make_float2(hi, (float)(val - (double)hi));
+    }
   }
 }
 
@@ -370,6 +383,10 @@ cudaError_t launch_reduced_cols(Context* c, int p, int prec, const void* v, cons
   a.v = v; a.cvec = cvec; a.y = y; a.z = z;
   a.alpha = alpha; a.beta = beta;
   a.nx = c->mesh.nx; a.ny = c->mesh.ny;
+  if (prec == HDG_PREC_F32X2 && L.R2) {   // double-float product on the FP32 pipe
+    a.R = L.R2;
+    return red_cols_dispatch<float2, dd, false>(L.n1, a, c->nel, nb, s);
+  }
   if (prec_double(prec)) {
     if (!L.R64) return cudaErrorInvalidValue;
     a.R = L.R64;
@@ -416,7 +433,7 @@ cudaError_t launch_reduced_blocks(Context* c, int p, cudaStream_t s) {
   const long total = (long)c->nel * reduced_entries(L.n1);
   int blocks = (int)((total + 255) / 256);
   if (blocks > c->num_sms * 32) blocks = c->num_sms * 32;
-  reduced_blocks_kernel<<<blocks, 256, 0, s>>>(c->nel, L.n1, L.Sdense, L.R64, L.R32);
+  reduced_blocks_kernel<<<blocks, 256, 0, s>>>(c->nel, L.n1, L.Sdense, L.R64, L.R32, L.R2);
   return cudaGetLastError();
 }
 
@@ -428,7 +445,11 @@ cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, con
   a.alpha = alpha; a.beta = beta;
   a.nx = c->mesh.nx; a.ny = c->mesh.ny;
   const long nel = c->nel;
-  if (prec_double(prec)) {   // FP64 (and the double-vector F32X2 cycles): FP64 blocks
+  if (prec == HDG_PREC_F32X2 && L.R2) {   // double-float product on the FP32 pipe
+    a.R = L.R2;
+    return red_dispatch<float2, dd, false>(L.n1, a, nel, c->opt.reduced, s);
+  }
+  if (prec_double(prec)) {   // FP64 (and F32X2 without the float2 blocks): FP64 blocks
     if (!L.R64) return cudaErrorInvalidValue;
     a.R = L.R64;
     return red_dispatch<double, double, false>(L.n1, a, nel, c->opt.reduced, s);

@@ -160,7 +160,10 @@ static int setup_impl(Context* c, const double* kappa, cudaStream_t s) {
       const size_t ep = ((size_t)c->nel + 31) / 32 * 32;                     // warp chunks
       const size_t Q = (size_t)reduced_entries(L.n1);
       TRY(ctx_alloc(c, (void**)&L.R64, Q * ep * sizeof(double)));
-      if (mixed && c->opt.reduced) TRY(ctx_alloc(c, (void**)&L.R32, (Q + 3) / 4 * 4 * ep * sizeof(float)));
+      if (mixed && c->opt.reduced) {
+        TRY(ctx_alloc(c, (void**)&L.R32, (Q + 3) / 4 * 4 * ep * sizeof(float)));
+        TRY(ctx_alloc(c, (void**)&L.R2, Q * ep * sizeof(float2)));
+      }
     }
     if (mixed) {
       TRY(ctx_alloc(c, (void**)&L.S32, L.rec_entries * sizeof(float)));

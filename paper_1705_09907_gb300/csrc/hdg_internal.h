@@ -62,6 +62,7 @@ struct PLevel {
   // condensed blocks reduced by the element's reflection symmetry: packed
   // upper triangles of the four character blocks, [Q][nel] (apply_reduced.cu)
   double* R64 = nullptr; float* R32 = nullptr;
+  float2* R2 = nullptr;                     // reduced blocks as (hi, lo) float pairs (F32X2 applies)
   double* Sdense = nullptr;                 // [nel][m][m] FP64 element blocks
   double* Pp = nullptr;                     // prolongation from p-1 [(p+1) x p] (device)
   float* Pp32 = nullptr;                    // the same in float (float V-cycles)

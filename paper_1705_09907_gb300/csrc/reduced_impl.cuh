@@ -2,10 +2,65 @@
 // (apply_reduced.cu, where the method is described) and the one-launch apply
 // over several meshes (apply_multi.cu).
 #pragma once
-#include "hdg_internal.h"
+#include "apply_impl.cuh"
 
 namespace hdg {
 namespace red {
+
+// Double-float arithmetic for the reduced product of the double-vector
+// (F32X2) applies: a value is hi + lo (two floats, lo below half an ulp of hi
+// after every operation), products are split exactly by an FMA and sums by
+// Knuth's two-sum, so the element product keeps about 46 significant bits on
+// the FP32 pipe (the FP64 pipe of this GPU is ~60x slower). Blocks are float2
+// pairs (hi, lo) of the FP64 reduced blocks; vectors stay double.
+struct dd {
+  float hi, lo;
+  __device__ __forceinline__ dd() {}
+  __device__ __forceinline__ explicit dd(int v) : hi((float)v), lo(0.0f) {}
+  __device__ __forceinline__ explicit dd(float v) : hi(v), lo(0.0f) {}
+  __device__ __forceinline__ dd(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ dd(float2 v) : hi(v.x), lo(v.y) {}
+};
+__device__ __forceinline__ dd dd_norm(float s, float l) {
+  const float h = __fadd_rn(s, l);
+  return dd(h, __fsub_rn(l, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bv = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bv)), __fsub_rn(b.hi, bv));
+  return dd_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + dd(-b.hi, -b.lo); }
+// u + b t in each arithmetic (named apart from fma so that double and float
+// calls inside this namespace never meet the double-float overload)
+__device__ __forceinline__ double madd(double b, double t, double u) { return ::fma(b, t, u); }
+__device__ __forceinline__ float madd(float b, float t, float u) { return fmaf(b, t, u); }
+__device__ __forceinline__ dd madd(dd b, dd t, dd u) {
+  const float p = __fmul_rn(b.hi, t.hi);
+  float e = __fmaf_rn(b.hi, t.hi, -p);
+  e = __fmaf_rn(b.hi, t.lo, e);
+  e = __fmaf_rn(b.lo, t.hi, e);
+  const float s = __fadd_rn(u.hi, p);
+  const float bv = __fsub_rn(s, u.hi);
+  const float e2 = __fadd_rn(__fsub_rn(u.hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+  return dd_norm(s, __fadd_rn(u.lo, __fadd_rn(e, e2)));
+}
+// vector entries in the arithmetic type: double vectors are split into
+// (hi, lo) with integer operations for the double-float product
+template <typename T>
+__device__ __forceinline__ T vload(const void* v, size_t i) { return __ldg((const T*)v + i); }
+template <>
+__device__ __forceinline__ dd vload<dd>(const void* v, size_t i) {
+  const dfloat f = split_double(__ldg((const double*)v + i));
+  return dd(f.hi, f.lo);
+}
+// the vector type of an arithmetic type, and the conversion of a result
+template <typename T> struct VecT { using type = T; };
+template <> struct VecT<dd> { using type = double; };
+template <typename T>
+__device__ __forceinline__ T to_vec(T a) { return a; }
+__device__ __forceinline__ double to_vec(dd a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
 template <int N1>
 struct Red {
@@ -43,10 +98,10 @@ __device__ __forceinline__ void sym_block_reg(const float* bq, const T (&t)[D > 
     for (int j = i; j < D; ++j, ++q) {
       const T b = (T)bq[q];
       if (j == i) {
-        u[i] = fma(b, t[i], u[i]);
+        u[i] = madd(b, t[i], u[i]);
       } else {
-        u[i] = fma(b, t[j], u[i]);
-        u[j] = fma(b, t[i], u[j]);
+        u[i] = madd(b, t[j], u[i]);
+        u[j] = madd(b, t[i], u[j]);
       }
     }
   }
@@ -66,10 +121,10 @@ __device__ __forceinline__ void sym_block(const TS* __restrict__ R, int qoff, si
     for (int j = i; j < D; ++j, ++q) {
       const T b = (T)__ldcs(R + base + (size_t)q * 32);
       if (j == i) {
-        u[i] = fma(b, t[i], u[i]);
+        u[i] = madd(b, t[i], u[i]);
       } else {
-        u[i] = fma(b, t[j], u[i]);
-        u[j] = fma(b, t[i], u[j]);
+        u[i] = madd(b, t[j], u[i]);
+        u[j] = madd(b, t[i], u[j]);
       }
     }
   }
@@ -121,7 +176,7 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
   constexpr bool kVec = sizeof(TS) == 4;
   constexpr int G = kVec ? red_groups(RD::Q) : 1;
   float bq[4 * G];
-  if (kVec) {
+  if constexpr (kVec) {
     const float4* __restrict__ R4 = (const float4*)a.R;
     const size_t g0 = ((size_t)(K >> 5) * G) * 32 + (K & 31);
 #pragma unroll
@@ -131,18 +186,18 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
     }
   }
   const int nx = a.nx, ny = a.ny;
-  const T* __restrict__ v = (const T*)a.v;
+  const void* v = a.v;
   const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
   const bool hW = i > 0, hE = i < nx - 1, hS = j > 0, hN = j < ny - 1;
   T xw[N1], xe[N1], xs[N1], xn[N1];
 #pragma unroll
   for (int q = 0; q < N1; ++q) {
-    xw[q] = hW ? v[(eW * N1 + q) * nb + col] : T(0);
-    xe[q] = hE ? v[((eW + 1) * N1 + q) * nb + col] : T(0);
-    xs[q] = hS ? v[(eS * N1 + q) * nb + col] : T(0);
-    xn[q] = hN ? v[((eS + nx) * N1 + q) * nb + col] : T(0);
+    xw[q] = hW ? vload<T>(v, (eW * N1 + q) * nb + col) : T(0);
+    xe[q] = hE ? vload<T>(v, ((eW + 1) * N1 + q) * nb + col) : T(0);
+    xs[q] = hS ? vload<T>(v, (eS * N1 + q) * nb + col) : T(0);
+    xn[q] = hN ? vload<T>(v, ((eS + nx) * N1 + q) * nb + col) : T(0);
   }
-  if (DIFF) {   // S_K has zero row sums: apply it to v_K - mean(v_K)
+  if constexpr (DIFF) {   // S_K has zero row sums: apply it to v_K - mean(v_K)
     T sum = T(0);
 #pragma unroll
     for (int q = 0; q < N1; ++q) sum += (xw[q] + xe[q]) + (xs[q] + xn[q]);
@@ -185,7 +240,7 @@ __device__ __forceinline__ void elem_product(const RedArgs& a, long nel, long K,
   const TS* __restrict__ R = (const TS*)a.R;
   T u0[RD::d0 > 0 ? RD::d0 : 1], u1[RD::d1 > 0 ? RD::d1 : 1], u2[RD::d2 > 0 ? RD::d2 : 1],
       u3[RD::d3 > 0 ? RD::d3 : 1];
-  if (kVec) {
+  if constexpr (kVec) {
     sym_block_reg<RD::d0, T>(bq + RD::q0, t0, u0);
     sym_block_reg<RD::d1, T>(bq + RD::q1, t1, u1);
     sym_block_reg<RD::d2, T>(bq + RD::q2, t2, u2);
@@ -293,8 +348,9 @@ __device__ __forceinline__ void face_body(const RedArgs& a, long K0, int t, T* s
   const int nx = a.nx, ny = a.ny;
   const long nel = (long)nx * ny;
   const long K = K0 + t;
+  using VT = typename VecT<T>::type;
   const T* __restrict__ z = (const T*)a.z;
-  T* __restrict__ y = (T*)a.y;
+  VT* __restrict__ y = (VT*)a.y;
   const long nv = (long)(nx + 1) * ny;
   if (K < nel) {
     const int i = (int)(K % nx), j = (int)(K / nx);
@@ -306,28 +362,28 @@ __device__ __forceinline__ void face_body(const RedArgs& a, long K0, int t, T* s
     // the E / N domain-boundary edges have no owner element: zero them here
     if (i == nx - 1) {
 #pragma unroll
-      for (int q = 0; q < N1; ++q) y[(i + 1 + (long)(nx + 1) * j) * N1 + q] = T(0);
+      for (int q = 0; q < N1; ++q) y[(i + 1 + (long)(nx + 1) * j) * N1 + q] = VT(0);
     }
     if (j == ny - 1) {
 #pragma unroll
-      for (int q = 0; q < N1; ++q) y[(nv + i + (long)nx * (j + 1)) * N1 + q] = T(0);
+      for (int q = 0; q < N1; ++q) y[(nv + i + (long)nx * (j + 1)) * N1 + q] = VT(0);
     }
   }
   __syncthreads();
-  const Form<T> form(a);
+  const Form<VT> form(a);
   const int cnt = (int)((nel - K0) < kFaceThreads ? (nel - K0) : kFaceThreads);
   // every thread has at most N1 outputs of each face type: their addends are
   // all loaded before the first store, so the loads overlap
   size_t ow[N1], os[N1];
   bool hw[N1], hs[N1];
-  T cw[N1], cs[N1];
+  VT cw[N1], cs[N1];
 #pragma unroll
   for (int u = 0; u < N1; ++u) {
     const int idx = t + u * kFaceThreads;
     hw[u] = false;
     hs[u] = false;
     ow[u] = os[u] = 0;
-    cw[u] = cs[u] = T(0);
+    cw[u] = cs[u] = VT(0);
     if (idx < cnt * N1) {
       const int tt = idx / N1, q = idx - tt * N1;
       const long Kt = K0 + tt;
@@ -346,8 +402,8 @@ __device__ __forceinline__ void face_body(const RedArgs& a, long K0, int t, T* s
   for (int u = 0; u < N1; ++u) {
     const int idx = t + u * kFaceThreads;
     if (idx < cnt * N1) {
-      y[ow[u]] = hw[u] ? form.with(sw[idx], cw[u]) : T(0);
-      y[os[u]] = hs[u] ? form.with(ss[idx], cs[u]) : T(0);
+      y[ow[u]] = hw[u] ? form.with(to_vec(sw[idx]), cw[u]) : VT(0);
+      y[os[u]] = hs[u] ? form.with(to_vec(ss[idx]), cs[u]) : VT(0);
     }
   }
 }
@@ -380,22 +436,23 @@ __device__ __forceinline__ void cols_face_body(const RedArgs& a, long K, int nb,
   const long nel = (long)nx * ny;
   if (K >= nel || col >= nb) return;
   const int i = (int)(K % nx), j = (int)(K / nx);
+  using VT = typename VecT<T>::type;
   const T* __restrict__ z = (const T*)a.z;
-  T* __restrict__ y = (T*)a.y;
-  const Form<T> form(a);
+  VT* __restrict__ y = (VT*)a.y;
+  const Form<VT> form(a);
   const long nv = (long)(nx + 1) * ny;
   const long eW = i + (long)(nx + 1) * j, eS = nv + i + (long)nx * j;
 #pragma unroll
   for (int q = 0; q < N1; ++q) {
     const size_t ow = (size_t)(eW * N1 + q) * nb + col, os = (size_t)(eS * N1 + q) * nb + col;
-    y[ow] = i > 0 ? form(z[((size_t)(0 * N1 + q) * nel + K) * nb + col] +
-                         z[((size_t)(1 * N1 + q) * nel + K - 1) * nb + col], ow)
-                  : T(0);
-    y[os] = j > 0 ? form(z[((size_t)(2 * N1 + q) * nel + K) * nb + col] +
-                         z[((size_t)(3 * N1 + q) * nel + K - nx) * nb + col], os)
-                  : T(0);
-    if (i == nx - 1) y[((eW + 1) * N1 + q) * nb + col] = T(0);
-    if (j == ny - 1) y[((eS + nx) * N1 + q) * nb + col] = T(0);
+    y[ow] = i > 0 ? form(to_vec(z[((size_t)(0 * N1 + q) * nel + K) * nb + col] +
+                                z[((size_t)(1 * N1 + q) * nel + K - 1) * nb + col]), ow)
+                  : VT(0);
+    y[os] = j > 0 ? form(to_vec(z[((size_t)(2 * N1 + q) * nel + K) * nb + col] +
+                                z[((size_t)(3 * N1 + q) * nel + K - nx) * nb + col]), os)
+                  : VT(0);
+    if (i == nx - 1) y[((eW + 1) * N1 + q) * nb + col] = VT(0);
+    if (j == ny - 1) y[((eS + nx) * N1 + q) * nb + col] = VT(0);
   }
 }
 
