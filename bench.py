@@ -793,7 +793,10 @@ def run_ours(args):
                    "frac_hbm": gbs / peaks["hbm_gbs"], "algorithmic_bytes": algo,
                    "scratch_bytes": 2 * nel * 4 * n1 * red_w[p_],
                    "dense_equivalent_GBps": dense_eq / (ms * 1e-3) / 1e9,
-                   "fp64_ops_per_element": {"fma": red_fma, "add": red_add} if p_ in ("fp64", "f32x2") else None}
+                   "fp64_ops_per_element": {"fma": red_fma, "add": red_add} if p_ == "fp64" else None}
+        if p_ == "f32x2":
+            tra[p_]["kernels"] += "; float2 (hi, lo) blocks, double-float arithmetic on the FP32 pipe"
+            tra[p_]["double_float_ops_per_element"] = {"fma": red_fma, "add": red_add}
     tra["fp64"]["fp64_pipe_frac"] = nel * (red_fma + red_add) / (apply_ms["fp64"] * 1e-3) / (1.25e12 / 2)
     trd = {}
     for p_, ms in dense_ms.items():
