@@ -374,6 +374,63 @@ __global__ void __launch_bounds__(kElemThreads) reduced_theta_kernel(const RedAr
   dth[K] = -d;
 }
 
+// ---------------------------------------------------------------------------
+// Schwarz blocks of the float cycles, packed. A weighted patch inverse
+// M_K = W A_patch^-1 W is symmetric but has none of the reflection symmetry of
+// S_K (the patch takes the neighbours' face blocks, whose coefficients differ),
+// so it is stored as one packed upper triangle per element (m(m+1)/2 of its m^2
+// entries, m = 4(k+1): 210 of 400 at k = 4) in the warp chunks of the reduced
+// blocks, and applied like them: an element pass u_K = M_K x_K (each stored
+// entry used for both of its positions) into the scratch, then the face pass of
+// the reduced apply. The owner-record apply streams all m^2 entries; the float
+// Schwarz applies are bandwidth bound, so this halves their block bytes.
+__global__ void sym_pack_kernel(long nel, int m, const double* __restrict__ Md, float* __restrict__ Mp) {
+  const int Q = m * (m + 1) / 2;
+  const long total = nel * Q;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / nel);
+    const long K = t % nel;
+    int i = 0, r = q;
+    while (r >= m - i) { r -= m - i; ++i; }
+    const int j = i + r;
+    const double* M = Md + (size_t)K * m * m;
+    Mp[red_base(K, Q) + (size_t)q * 32] = (float)(0.5 * (M[i * m + j] + M[j * m + i]));
+  }
+}
+
+template <int N1>
+__global__ void __launch_bounds__(kElemThreads) sym_elem_kernel(const RedArgs a) {
+  constexpr int D = 4 * N1, Q = D * (D + 1) / 2;
+  const int nx = a.nx, ny = a.ny;
+  const long nel = (long)nx * ny;
+  const long K = blockIdx.x * (long)kElemThreads + threadIdx.x;
+  if (K >= nel) return;
+  const int i = (int)(K % nx), j = (int)(K / nx);
+  const float* __restrict__ v = (const float*)a.v;
+  const long eW = i + (long)(nx + 1) * j, eS = (long)(nx + 1) * ny + i + (long)nx * j;
+  const bool has[4] = {i > 0, i < nx - 1, j > 0, j < ny - 1};
+  const long ed[4] = {eW, eW + 1, eS, eS + nx};
+  float x[D], u[D];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int q = 0; q < N1; ++q) x[f * N1 + q] = has[f] ? __ldg(v + ed[f] * N1 + q) : 0.0f;
+  sym_block<D, float, float>((const float*)a.R, 0, red_base(K, Q), x, u);
+  float* __restrict__ z = (float*)a.z;
+#pragma unroll
+  for (int r = 0; r < D; ++r) z[(size_t)r * nel + K] = u[r];
+}
+
+template <int N1>
+cudaError_t sym_launch(const RedArgs& a, long nel, cudaStream_t s) {
+  const unsigned g1 = (unsigned)((nel + kElemThreads - 1) / kElemThreads),
+                 g2 = (unsigned)((nel + kFaceThreads - 1) / kFaceThreads);
+  sym_elem_kernel<N1><<<g1, kElemThreads, 0, s>>>(a);
+  HDG_CUDA_TRY(cudaGetLastError());
+  reduced_face_kernel<N1, float><<<g2, kFaceThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_reduced_cols(Context* c, int p, int prec, const void* v, const void* cvec, void* y, double alpha,
@@ -437,6 +494,35 @@ cudaError_t launch_reduced_blocks(Context* c, int p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_sym_pack(Context* c, int p, const double* Md, cudaStream_t s) {
+  PLevel& L = c->plev[p];
+  if (!L.Mp32) return cudaErrorInvalidValue;
+  const long total = (long)c->nel * L.m * (L.m + 1) / 2;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > c->num_sms * 32) blocks = c->num_sms * 32;
+  sym_pack_kernel<<<blocks, 256, 0, s>>>(c->nel, L.m, Md, L.Mp32);
+  return cudaGetLastError();
+}
+cudaError_t launch_sym_schwarz(Context* c, int p, const void* v, const void* cvec, void* y, double alpha,
+                               double beta, cudaStream_t s) {
+  PLevel& L = c->plev[p];
+  if (!L.Mp32 || !c->red_z) return cudaErrorInvalidValue;
+  RedArgs a{};
+  a.R = L.Mp32; a.v = v; a.cvec = cvec; a.y = y; a.z = c->red_z;
+  a.alpha = alpha; a.beta = beta;
+  a.nx = c->mesh.nx; a.ny = c->mesh.ny;
+  switch (L.n1) {
+    case 1: return sym_launch<1>(a, c->nel, s);
+    case 2: return sym_launch<2>(a, c->nel, s);
+    case 3: return sym_launch<3>(a, c->nel, s);
+    case 4: return sym_launch<4>(a, c->nel, s);
+    case 5: return sym_launch<5>(a, c->nel, s);
+    case 6: return sym_launch<6>(a, c->nel, s);
+    case 7: return sym_launch<7>(a, c->nel, s);
+    case 8: return sym_launch<8>(a, c->nel, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 cudaError_t launch_reduced_apply(Context* c, int p, int prec, const void* v, const void* cvec, void* y,
                                  double alpha, double beta, cudaStream_t s) {
   PLevel& L = c->plev[p];

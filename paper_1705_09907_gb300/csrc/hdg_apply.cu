@@ -8,6 +8,9 @@ cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, 
   PLevel& L = c->plev[p];
   if (which == 0 && nrhs == 1 && c->opt.reduced)
     return launch_reduced_apply(c, p, prec, v, cvec, y, alpha, beta, s);
+  // float Schwarz applies of one vector: the packed symmetric blocks
+  if (which == 1 && nrhs == 1 && prec == HDG_PREC_FP32 && L.Mp32 && c->red_z)
+    return launch_sym_schwarz(c, p, v, cvec, y, alpha, beta, s);
   // columns with double vectors: the reduced column kernels (FP64-pipe bound,
   // 2x fewer operations); float columns keep the dense column kernel, which
   // reads the blocks once for all columns and beats the reduced form's scratch

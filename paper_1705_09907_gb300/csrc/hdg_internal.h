@@ -58,6 +58,7 @@ struct PLevel {
   size_t rec_entries = 0;                   // nseg * R * 16
   double* S64 = nullptr; float* S32 = nullptr; __nv_bfloat16* S16 = nullptr;
   double* M64 = nullptr; float* M32 = nullptr; __nv_bfloat16* M16 = nullptr;
+  float* Mp32 = nullptr;                    // Schwarz blocks as packed upper triangles (float cycles)
   float2* S2 = nullptr; float2* M2 = nullptr;   // double-float (hi, lo) copies
   // condensed blocks reduced by the element's reflection symmetry: packed
   // upper triangles of the four character blocks, [Q][nel] (apply_reduced.cu)
@@ -248,6 +249,11 @@ cudaError_t launch_reduced_theta(Context* c, const double* lam, const double* ps
 // Trace-operator apply on the record layout of level p:
 //   y = beta * cvec + alpha * (B v), B = S (which = 0) or Schwarz M (which = 1)
 // vectors in double (prec FP64) or float (FP32/BF16); cvec may be null.
+// Schwarz blocks of the float cycles as packed upper triangles (from the dense
+// per-element blocks Md at set-up), and their apply y = beta c + alpha M v
+cudaError_t launch_sym_pack(Context* c, int p, const double* Md, cudaStream_t s);
+cudaError_t launch_sym_schwarz(Context* c, int p, const void* v, const void* cvec, void* y, double alpha,
+                               double beta, cudaStream_t s);
 cudaError_t launch_apply(Context* c, int p, int which, int prec, const void* v, const void* cvec,
                          void* y, double alpha, double beta, int nrhs, cudaStream_t s);
 

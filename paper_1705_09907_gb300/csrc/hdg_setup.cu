@@ -334,6 +334,11 @@ cudaError_t launch_asm_blocks(Context* c, int p, cudaStream_t s) {
   asm_kernel<<<blocks, 32 * wpb, smem, s>>>(c->mesh.nx, c->mesh.ny, L.n1, L.Sdense, Md, c->err_flag);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = write_records(c, p, Md, L.M64, L.M32, L.M16, L.M2, s);
+  if (e == cudaSuccess && L.M32 && c->red_z) {   // packed copy for the float cycles' one-vector applies
+    const size_t ep = ((size_t)c->nel + 31) / 32 * 32;
+    e = ctx_alloc(c, (void**)&L.Mp32, (size_t)L.m * (L.m + 1) / 2 * ep * sizeof(float));
+    if (e == cudaSuccess) e = launch_sym_pack(c, p, Md, s);
+  }
   cudaError_t e2 = cudaFreeAsync(Md, s);
   return e != cudaSuccess ? e : e2;
 }
