@@ -221,3 +221,28 @@ def test_invalid_arguments(H):
         s.apply(x, prec="fp32")
     assert e.value.status == H.HDG_ERR_UNSUPPORTED
     s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16", 5e-2)])
+@pytest.mark.parametrize("k,nx,ny", [(5, 12, 10), (6, 9, 8), (7, 8, 6)])
+def test_vcycle_low_precision_high_degree(H, prec, tol, k, nx, ny):
+    """Float V-cycles at the high degrees (the packed Schwarz blocks of 24..32
+    face dofs, the double-float finest correction) against the oracle's FP64
+    V-cycle; and the mixed-precision CG reaches the direct solution."""
+    m = omesh.Mesh(nx, ny)
+    kap = np.exp(inputs.gaussian_field(nx, seed=3, corr_len=0.3, ny=ny))
+    G = ogmg.NestedGMG(m, k, kap)
+    top = G.plevels[k]
+    r = np.zeros(top.ndof)
+    r[top.idx] = np.random.default_rng(14).normal(size=len(top.idx))
+    z_ref = G.vcycle(r)
+    s = H.HDGSolver(nx, ny, k, cuda(kap))
+    z = host(s.vcycle(cuda(r, torch.float32), prec=prec)).astype(np.float64)
+    assert np.linalg.norm(z - z_ref) <= tol * np.linalg.norm(z_ref)
+    prob = G.plevels[k].prob
+    fq = np.random.default_rng(15).normal(size=(m.nel, k + 2, k + 2))
+    lam_ref = prob.solve_direct(prob.condense_rhs(fq))
+    lam, info = s.solve(s.condense_rhs(cuda(fq)), rtol=1e-12, maxit=200, inner=prec)
+    assert info["relres"] <= 1e-12
+    assert np.linalg.norm(host(lam) - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref)
+    s.close()
