@@ -601,7 +601,7 @@ __global__ void coarse_inverse_kernel(int n, const double* __restrict__ L, doubl
 // (its 2n dependent substitution steps would cost more than the whole cycle).
 constexpr int kHfMaxLevels = 8;
 constexpr int kHfMaxCoef = 7;         // cheb_degree <= 8
-constexpr int kHfThreads = 1024;
+constexpr int kHfThreads = 512;
 constexpr int kHfMaxCoarse = 1024;    // largest coarsest system solved through its inverse
 
 // one fused level: global sources of its read-only data, offsets (in entries
