@@ -112,7 +112,12 @@ typedef struct {
                                  with one CTA per 32 x 8 element tile plus a
                                  small launch for the faces on tile edges;
                                  0: the dense owner records (kernel chosen by
-                                 `autotune`)                                 */
+                                 `autotune`). With 1 or 2, double vectors in
+                                 F32X2 use the reduced blocks as float pairs
+                                 in double-float arithmetic, and one-vector
+                                 FP32 Schwarz applies use the Schwarz blocks
+                                 packed as symmetric upper triangles (element
+                                 pass + face pass)                          */
   int tau_kappa;              /* 1: tau_K = kappa_K on the faces of element K
                                  (tau piecewise constant per element, Sec. 3;
                                  `tau` is unused): every local equation then
