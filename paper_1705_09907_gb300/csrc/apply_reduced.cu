@@ -415,7 +415,27 @@ __global__ void __launch_bounds__(kElemThreads) sym_elem_kernel(const RedArgs a)
   for (int f = 0; f < 4; ++f)
 #pragma unroll
     for (int q = 0; q < N1; ++q) x[f * N1 + q] = has[f] ? __ldg(v + ed[f] * N1 + q) : 0.0f;
-  sym_block<D, float, float>((const float*)a.R, 0, red_base(K, Q), x, u);
+  // u = M x row by row of the packed triangle: a row's entries are loaded
+  // together before its multiply-adds, so they are in flight at once (the
+  // products and their order are those of sym_block)
+  {
+    const float* __restrict__ R = (const float*)a.R + red_base(K, Q);
+#pragma unroll
+    for (int r = 0; r < D; ++r) u[r] = 0.0f;
+    int q = 0;
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      float e[D];
+#pragma unroll
+      for (int c = r; c < D; ++c) e[c] = __ldcs(R + (size_t)(q + c - r) * 32);
+#pragma unroll
+      for (int c = r; c < D; ++c) {
+        u[r] = fmaf(e[c], x[c], u[r]);
+        if (c != r) u[c] = fmaf(e[c], x[r], u[c]);
+      }
+      q += D - r;
+    }
+  }
   float* __restrict__ z = (float*)a.z;
 #pragma unroll
   for (int r = 0; r < D; ++r) z[(size_t)r * nel + K] = u[r];
